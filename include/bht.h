@@ -1,0 +1,162 @@
+/*
+ * bht.h — C ABI of the GB300 batch hierarchical Tucker library (libbht.so).
+ *
+ * The library compresses a stream of tensor batches into the batch
+ * hierarchical Tucker (batch-HT) format of arXiv 2412.16544:
+ *   - bht_l2r        : one-shot leaves-to-root decomposition of a first batch
+ *                      (Algorithm 1, "BHT-l2r"; Problem 1, Section 1);
+ *   - htrise_update  : incremental update with a new batch, never storing or
+ *                      rebuilding the accumulation (Algorithm 2, "HT-RISE";
+ *                      Problem 2, Section 1);
+ *   - ht_reconstruct : root-to-leaves decoding of stored items
+ *                      (eq. htucker_reconstruction, Section 2.3);
+ *   - ht_encode      : latent representation of unseen items on the current
+ *                      cores (Step 1 of Algorithm 2, used for the relative
+ *                      test error of eq. generalization_performance).
+ *
+ * Conventions shared by every call
+ *   - Every function returns bht_status; BHT_OK (0) on success. Nothing is
+ *     thrown across the ABI. bht_last_error() returns a thread-local message
+ *     describing the last failure of the calling thread.
+ *   - Batches are item-major, C-order: element (m, i_1, ..., i_d) of an
+ *     N-item batch with modes n_1..n_d sits at offset
+ *     ((m * n_1 + i_1) * n_2 + i_2) ... * n_d + i_d. The paper keeps the batch
+ *     last; its Section 3.1 footnote states the batch position does not matter.
+ *   - Data pointers may be device pointers or host pointers (pinned or
+ *     pageable); the library detects which (cudaPointerGetAttributes) and
+ *     copies host data through its own device staging buffer on `stream`.
+ *     The caller keeps ownership of every pointer it passes and must keep
+ *     it valid until the call returns (host data) or until `stream` has
+ *     passed the call (device data).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that decide ranks synchronise `stream` before they return.
+ *   - The dimension tree is the balanced binary tree over modes 1..d whose
+ *     first child of a node with m modes takes ceil(m/2) of them (Fig. 2,
+ *     Section 2.3); the batch is not a tree node, it rides on the root
+ *     (Section 3.1). Node order everywhere is breadth-first, left to right:
+ *     node 0 is the root, nodes 1 and 2 are its successors, ...
+ *   - Cores (Section 2.3): a leaf core is U in R^{n x r}, row-major [n][r];
+ *     a transfer core is G in R^{r_l x r_r x r}, C-order [r_l][r_r][r]
+ *     (the merged row index is i_l * r_r + i_r); the root is stored item-major
+ *     [N_total][r_11][r_12].
+ *   - Errors: on any error inside htrise_update the state is left exactly as
+ *     it was before the call (updates are built in fresh buffers and
+ *     committed only at the end).
+ */
+#ifndef BHT_H_
+#define BHT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BHT_OK = 0,
+  BHT_EINVAL = 1,        /* invalid argument (null pointer, bad size, d < 2, eps <= 0) */
+  BHT_ENOMEM = 2,        /* device or host allocation failed */
+  BHT_ECAPACITY = 3,     /* a size exceeds a documented maximum */
+  BHT_ECUDA = 4,         /* a CUDA runtime call failed; see bht_last_error() */
+  BHT_ENUMERIC = 5,      /* non-finite values in the input or in an intermediate */
+  BHT_ETIMEOUT = 6,      /* a bounded device-side wait gave up; results are invalid */
+  BHT_EUNSUPPORTED = 7   /* a valid request this build does not implement */
+} bht_status;
+
+/* Element type of a batch or of an output buffer. */
+typedef enum { BHT_F32 = 0, BHT_F64 = 1 } bht_dtype;
+
+/* Arithmetic of the path.
+ *   BHT_PREC_FP64 : every contraction, Gram matrix, eigensolve and norm in FP64
+ *                   (the plain GPU form of the method).
+ *   BHT_PREC_MIXED: the full-data contractions (Gram matrices and mode
+ *                   products over the batch) on tcgen05 tensor cores in TF32
+ *                   with FP32 accumulation (split-precision 3xTF32 when
+ *                   eps_rel < 5e-3); node eigensolves, re-orthogonalisation,
+ *                   norms and the skip test stay in FP64. */
+typedef enum { BHT_PREC_FP64 = 0, BHT_PREC_MIXED = 1 } bht_precision;
+
+typedef struct {
+  int32_t precision;      /* bht_precision */
+  int32_t reserved0;
+  int64_t reserved1;
+} bht_opts;
+
+typedef struct bht_tree bht_tree;
+typedef struct bht_state bht_state;
+
+/* Outcome of one htrise_update call. */
+typedef struct {
+  int32_t skipped;        /* 1: projection error <= eps_des, only the root grew (Algorithm 2) */
+  int32_t reserved;
+  double eps_proj;        /* sqrt(max(||Y||^2 - ||C_1||^2, 0)), eq. relative_error_threshold */
+  double eps_des;         /* eps_rel * ||Y||_F of the new batch */
+  double norm_y;          /* ||Y||_F of the new batch */
+  int64_t n_items_total;  /* items in the accumulation after the call */
+} bht_update_info;
+
+/* Balanced binary dimension tree over d >= 2 modes of sizes dims[0..d-1]
+ * (Section 2.3, Fig. 2). `out` receives a host object owned by the caller,
+ * released with bht_tree_destroy. d <= 16 and every dims[i] in [1, 4096]. */
+bht_status bht_tree_create_balanced(int32_t d, const int64_t* dims, bht_tree** out);
+bht_status bht_tree_destroy(bht_tree* tree);
+/* Depth p and number of nodes 2d-1 of a tree. */
+bht_status bht_tree_info(const bht_tree* tree, int32_t* depth, int32_t* num_nodes);
+
+/* BHT-l2r (Algorithm 1): compress a first batch Y of N items into a new state.
+ *   Y      : [N][n_1]..[n_d] item-major, element type `dtype`, device or host.
+ *   eps_rel: relative tolerance; the result satisfies ||Y - Y~|| <= eps_rel ||Y||
+ *            (Corollary bht_leaves_to_root) up to the arithmetic of `opts`.
+ *   opts   : may be NULL (= BHT_PREC_FP64).
+ *   out    : receives a state owned by the caller (bht_state_destroy). The
+ *            state keeps its own copy of the tree. */
+bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N,
+                   double eps_rel, const bht_opts* opts, void* stream, bht_state** out);
+
+/* HT-RISE (Algorithm 2): update `state` with a new batch of N items.
+ *   Projects Y onto the current cores; if the projection error is <= eps_rel ||Y||
+ *   only the root grows, otherwise residuals are truncated node by node, the
+ *   bases expanded and re-orthogonalised, parents zero-padded and the batch
+ *   re-projected. `info` may be NULL. */
+bht_status htrise_update(bht_state* state, const void* Y, int32_t dtype, int64_t N,
+                         double eps_rel, const bht_opts* opts, void* stream,
+                         bht_update_info* info);
+
+/* Root-to-leaves reconstruction (eq. htucker_reconstruction) of stored items
+ * first .. first+count-1 into `out` ([count][n_1]..[n_d], element type `dtype`,
+ * device or host). Never modifies the state. */
+bht_status ht_reconstruct(const bht_state* state, int64_t first, int64_t count,
+                          void* out, int32_t dtype, void* stream);
+
+/* Latent representation of N unseen items on the current cores (Step 1 of
+ * Algorithm 2), written item-major [N][r_11][r_12] as FP64 into `out`
+ * (device or host). Never modifies the state. */
+bht_status ht_encode(const bht_state* state, const void* Y, int32_t dtype, int64_t N,
+                     double* out, void* stream);
+
+/* Getters. Ranks: ranks[0] = items in the accumulation, ranks[i] = rank of
+ * node i (breadth-first) for i = 1 .. 2d-2; `cap` is the length of `ranks`. */
+bht_status bht_get_ranks(const bht_state* state, int64_t* ranks, int64_t cap);
+bht_status bht_get_dims(const bht_state* state, int32_t* d, int64_t* dims, int64_t cap);
+/* Copy core `node` (1 .. 2d-2) to host FP64 in the layout above; `cap` is the
+ * capacity of `host_out` in elements; `numel` receives the element count. */
+bht_status bht_get_core(const bht_state* state, int32_t node, double* host_out,
+                        int64_t cap, int64_t* numel);
+/* Copy root slices first .. first+count-1 to host FP64, [count][r_11][r_12]. */
+bht_status bht_get_root(const bht_state* state, int64_t first, int64_t count,
+                        double* host_out, int64_t cap);
+/* Elements of all cores (denominator of the compression ratio, eq. compression_ratio). */
+bht_status bht_num_elements(const bht_state* state, int64_t* cores_total);
+bht_status bht_state_destroy(bht_state* state);
+
+/* Device kernels launched by the calling thread's library calls since the
+ * last reset (a plain counter kept by the host side of the library). */
+bht_status bht_launch_count(int64_t* count, int32_t reset);
+
+const char* bht_last_error(void);
+const char* bht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BHT_H_ */

@@ -1,0 +1,274 @@
+"""Python binding of libbht (batch hierarchical Tucker on GB300).
+
+Argument marshalling only: every step of BHT-l2r, HT-RISE and the
+reconstruction runs inside libbht.so (include/bht.h). The binding turns
+tensors into pointers, sizes and a stream handle, calls the C entry point of
+the same name and raises on a non-zero status. There is no CPU fallback: if
+the shared library is missing, importing this package raises.
+
+Batches may be torch tensors (CUDA or CPU) or numpy arrays, float32 or
+float64, C-contiguous, item-major [N, n_1, ..., n_d].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbht.so")
+
+BHT_OK = 0
+BHT_F32, BHT_F64 = 0, 1
+BHT_PREC_FP64, BHT_PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "BHT_OK", 1: "BHT_EINVAL", 2: "BHT_ENOMEM", 3: "BHT_ECAPACITY", 4: "BHT_ECUDA",
+                5: "BHT_ENUMERIC", 6: "BHT_ETIMEOUT", 7: "BHT_EUNSUPPORTED"}
+
+
+class BHTError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("skipped", ctypes.c_int32), ("reserved", ctypes.c_int32), ("eps_proj", ctypes.c_double),
+                ("eps_des", ctypes.c_double), ("norm_y", ctypes.c_double), ("n_items_total", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2412_16544_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "bht_tree_create_balanced": [i32, P(i64), P(vp)],
+        "bht_tree_destroy": [vp],
+        "bht_tree_info": [vp, P(i32), P(i32)],
+        "bht_l2r": [vp, vp, i32, i64, dbl, P(_Opts), vp, P(vp)],
+        "htrise_update": [vp, vp, i32, i64, dbl, P(_Opts), vp, P(_Info)],
+        "ht_reconstruct": [vp, i64, i64, vp, i32, vp],
+        "ht_encode": [vp, vp, i32, i64, vp, vp],
+        "bht_get_ranks": [vp, P(i64), i64],
+        "bht_get_dims": [vp, P(i32), P(i64), i64],
+        "bht_get_core": [vp, i32, vp, i64, P(i64)],
+        "bht_get_root": [vp, i64, i64, vp, i64],
+        "bht_num_elements": [vp, P(i64)],
+        "bht_state_destroy": [vp],
+        "bht_launch_count": [P(i64), i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.bht_last_error.restype = ctypes.c_char_p
+    lib.bht_last_error.argtypes = []
+    lib.bht_version.restype = ctypes.c_char_p
+    lib.bht_version.argtypes = []
+    return lib
+
+
+_lib = _load()
+EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
+            "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
+            "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version"]
+
+
+def _check(status: int, where: str):
+    if status != BHT_OK:
+        raise BHTError(status, where, _lib.bht_last_error().decode(errors="replace"))
+
+
+def lib():
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _buffer(x):
+    """(pointer, dtype code, shape, keepalive) of a torch tensor or numpy array."""
+    torch = _torch()
+    if torch is not None and isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("batch must be C-contiguous")
+        if x.dtype == torch.float32:
+            code = BHT_F32
+        elif x.dtype == torch.float64:
+            code = BHT_F64
+        else:
+            raise TypeError("batch must be float32 or float64")
+        return ctypes.c_void_p(x.data_ptr()), code, tuple(x.shape), x
+    a = np.asarray(x)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("batch must be C-contiguous")
+    if a.dtype == np.float32:
+        code = BHT_F32
+    elif a.dtype == np.float64:
+        code = BHT_F64
+    else:
+        raise TypeError("batch must be float32 or float64")
+    return ctypes.c_void_p(a.ctypes.data), code, a.shape, a
+
+
+def _stream(stream):
+    if stream is None:
+        torch = _torch()
+        if torch is not None and torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _opts(precision):
+    if precision is None:
+        return None
+    code = {"fp64": BHT_PREC_FP64, "mixed": BHT_PREC_MIXED}.get(precision, precision)
+    return ctypes.byref(_Opts(int(code), 0, 0))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class UpdateInfo:
+    skipped: bool
+    eps_proj: float
+    eps_des: float
+    norm_y: float
+    n_items_total: int
+
+
+def bht_tree_create_balanced(dims) -> ctypes.c_void_p:
+    arr = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    h = ctypes.c_void_p()
+    _check(_lib.bht_tree_create_balanced(len(dims), arr, ctypes.byref(h)), "bht_tree_create_balanced")
+    return h
+
+
+def bht_tree_destroy(tree) -> None:
+    _check(_lib.bht_tree_destroy(tree), "bht_tree_destroy")
+
+
+def bht_tree_info(tree):
+    depth, nodes = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.bht_tree_info(tree, ctypes.byref(depth), ctypes.byref(nodes)), "bht_tree_info")
+    return depth.value, nodes.value
+
+
+def bht_l2r(tree, Y, eps_rel: float, precision=None, stream=None) -> ctypes.c_void_p:
+    ptr, code, shape, keep = _buffer(Y)
+    h = ctypes.c_void_p()
+    _check(_lib.bht_l2r(tree, ptr, code, int(shape[0]), float(eps_rel), _opts(precision), _stream(stream),
+                        ctypes.byref(h)), "bht_l2r")
+    del keep
+    return h
+
+
+def htrise_update(state, Y, eps_rel: float, precision=None, stream=None) -> UpdateInfo:
+    ptr, code, shape, keep = _buffer(Y)
+    info = _Info()
+    _check(_lib.htrise_update(state, ptr, code, int(shape[0]), float(eps_rel), _opts(precision),
+                              _stream(stream), ctypes.byref(info)), "htrise_update")
+    del keep
+    return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total)
+
+
+def bht_get_dims(state):
+    d = ctypes.c_int32()
+    dims = (ctypes.c_int64 * 16)()
+    _check(_lib.bht_get_dims(state, ctypes.byref(d), dims, 16), "bht_get_dims")
+    return [dims[i] for i in range(d.value)]
+
+
+def bht_get_ranks(state):
+    dims = bht_get_dims(state)
+    n = 2 * len(dims) - 1
+    out = (ctypes.c_int64 * n)()
+    _check(_lib.bht_get_ranks(state, out, n), "bht_get_ranks")
+    return [out[i] for i in range(n)]
+
+
+def ht_reconstruct(state, first: int, count: int, out=None, dtype="float32", stream=None):
+    """Decode items first..first+count-1 into `out` (allocated on the current CUDA device when None)."""
+    dims = bht_get_dims(state)
+    if out is None:
+        torch = _torch()
+        tdt = torch.float32 if dtype in ("float32", BHT_F32) else torch.float64
+        out = torch.empty((count, *dims), dtype=tdt, device="cuda")
+    ptr, code, _, keep = _buffer(out)
+    _check(_lib.ht_reconstruct(state, int(first), int(count), ptr, code, _stream(stream)), "ht_reconstruct")
+    return out
+
+
+def ht_encode(state, Y, out=None, stream=None):
+    ranks = bht_get_ranks(state)
+    ptr, code, shape, keep = _buffer(Y)
+    if out is None:
+        out = np.empty((shape[0], ranks[1], ranks[2]), dtype=np.float64)
+    optr, ocode, _, okeep = _buffer(out)
+    if ocode != BHT_F64:
+        raise TypeError("ht_encode writes float64")
+    _check(_lib.ht_encode(state, ptr, code, int(shape[0]), optr, _stream(stream)), "ht_encode")
+    return out
+
+
+def bht_get_core(state, node: int) -> np.ndarray:
+    n = ctypes.c_int64()
+    _check(_lib.bht_get_core(state, int(node), None, 0, ctypes.byref(n)), "bht_get_core")
+    buf = np.empty(n.value, dtype=np.float64)
+    _check(_lib.bht_get_core(state, int(node), ctypes.c_void_p(buf.ctypes.data), n.value, ctypes.byref(n)),
+           "bht_get_core")
+    return buf
+
+
+def bht_get_root(state, first: int, count: int) -> np.ndarray:
+    ranks = bht_get_ranks(state)
+    out = np.empty((count, ranks[1], ranks[2]), dtype=np.float64)
+    _check(_lib.bht_get_root(state, int(first), int(count), ctypes.c_void_p(out.ctypes.data), out.size),
+           "bht_get_root")
+    return out
+
+
+def bht_num_elements(state) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.bht_num_elements(state, ctypes.byref(n)), "bht_num_elements")
+    return n.value
+
+
+def bht_state_destroy(state) -> None:
+    _check(_lib.bht_state_destroy(state), "bht_state_destroy")
+
+
+def bht_launch_count(reset: bool = False) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.bht_launch_count(ctypes.byref(n), 1 if reset else 0), "bht_launch_count")
+    return n.value
+
+
+def bht_version() -> str:
+    return _lib.bht_version().decode()
+
+
+def bht_last_error() -> str:
+    return _lib.bht_last_error().decode(errors="replace")

@@ -1,0 +1,894 @@
+// api.cu — host side of libbht: dimension tree, device state, orchestration
+// of BHT-l2r (Algorithm 1) and HT-RISE (Algorithm 2), reconstruction
+// (eq. htucker_reconstruction) and the C ABI of include/bht.h.
+//
+// Layout of a layer intermediate ("layer tensor"): item-major
+// [N][I_1]..[I_m], one axis per node of the layer (eq.
+// ht_index_set_construction with the batch appended, Section 3.1). The
+// unfolding of axis j is the view [A][I_j][B], A = N * prod_{i<j} I_i,
+// B = prod_{i>j} I_i; merging two children's axes into their parent's axis is
+// a C-order reshape and moves no data.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bht.h"
+#include "internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors, launch counter
+// ---------------------------------------------------------------------------
+namespace {
+thread_local std::string g_err;
+thread_local int64_t g_launches = 0;
+
+struct Fail {
+  bht_status st;
+};
+
+[[noreturn]] void fail(bht_status st, const std::string& msg) {
+  g_err = msg;
+  throw Fail{st};
+}
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? BHT_ENOMEM : BHT_ECUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+}  // namespace
+
+namespace bht {
+void note_launch(int n) { g_launches += n; }
+}  // namespace bht
+
+using namespace bht;
+
+// ---------------------------------------------------------------------------
+// dimension tree (Section 2.3, Fig. 2)
+// ---------------------------------------------------------------------------
+struct TNode {
+  int id = 0, layer = 0, parent = -1, slot = -1;
+  int child[2] = {-1, -1};
+  int mode = -1;              // leaf: its mode
+  int first = 0, count = 0;   // modes covered: first .. first+count-1
+  bool leaf() const { return child[0] < 0; }
+};
+
+struct bht_tree {
+  int d = 0;
+  std::vector<int64_t> dims;
+  std::vector<TNode> nodes;                 // breadth-first, root = 0
+  std::vector<std::vector<int>> layers;     // node ids per layer, left to right
+  int p = 0;
+  std::vector<int> leaf_of_mode;
+};
+
+static void build_tree(bht_tree& t, int d, const int64_t* dims) {
+  t.d = d;
+  t.dims.assign(dims, dims + d);
+  t.nodes.clear();
+  t.layers.clear();
+  TNode root;
+  root.id = 0;
+  root.first = 0;
+  root.count = d;
+  t.nodes.push_back(root);
+  std::vector<int> frontier = {0};
+  while (!frontier.empty()) {
+    t.layers.push_back(frontier);
+    std::vector<int> next;
+    for (int id : frontier) {
+      const int m = t.nodes[id].count;
+      if (m == 1) {
+        t.nodes[id].mode = t.nodes[id].first;
+        continue;
+      }
+      const int h = (m + 1) / 2;  // the first successor takes ceil(m/2) modes
+      for (int slot = 0; slot < 2; ++slot) {
+        TNode c;
+        c.id = (int)t.nodes.size();
+        c.layer = t.nodes[id].layer + 1;
+        c.parent = id;
+        c.slot = slot;
+        c.first = t.nodes[id].first + (slot ? h : 0);
+        c.count = slot ? m - h : h;
+        t.nodes[id].child[slot] = c.id;
+        t.nodes.push_back(c);
+        next.push_back(c.id);
+      }
+    }
+    frontier = next;
+  }
+  t.p = (int)t.layers.size() - 1;
+  t.leaf_of_mode.assign(d, -1);
+  for (auto& nd : t.nodes)
+    if (nd.leaf()) t.leaf_of_mode[nd.mode] = nd.id;
+}
+
+// ---------------------------------------------------------------------------
+// device memory helpers (stream-ordered pool allocations)
+// ---------------------------------------------------------------------------
+namespace {
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  ck(cudaMallocAsync(&p, bytes, s), "cudaMallocAsync");
+  return p;
+}
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+struct DBuf {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(size_t bytes, cudaStream_t st) : p(dalloc(bytes, st)), s(st) {}
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), s(o.s) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      dfree(p, s);
+      p = o.p;
+      s = o.s;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~DBuf() { dfree(p, s); }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+  void* release() {
+    void* q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t dtype_size(int dt) { return dt == BHT_F64 ? 8 : 4; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// state
+// ---------------------------------------------------------------------------
+struct bht_state {
+  bht_tree tree;
+  int precision = BHT_PREC_FP64;
+  std::vector<int64_t> rank;    // per node id; rank[0] unused
+  std::vector<double*> U;       // per node id: orthonormal matrix form [rows][rank], FP64, device
+  double* root = nullptr;       // [root_cap][r11][r12], FP64, device
+  int64_t root_cap = 0;
+  int64_t n_items = 0;
+  int* d_status = nullptr;      // device status word of bounded waits
+
+  int64_t rows(int id) const {  // alpha of eq. compute_residual; n for a leaf
+    const TNode& nd = tree.nodes[id];
+    if (nd.leaf()) return tree.dims[nd.mode];
+    return rank[nd.child[0]] * rank[nd.child[1]];
+  }
+  int64_t r11() const { return rank[tree.nodes[0].child[0]]; }
+  int64_t r12() const { return rank[tree.nodes[0].child[1]]; }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// layer tensors
+// ---------------------------------------------------------------------------
+struct LTensor {
+  const void* ptr = nullptr;
+  int dtype = BHT_F64;
+  int64_t N = 0;
+  std::vector<int64_t> dims;   // per axis
+  std::vector<int> node;       // node id carried by each axis
+  DBuf own;                    // owns ptr when the library created it
+
+  int64_t numel() const {
+    int64_t n = N;
+    for (auto v : dims) n *= v;
+    return n;
+  }
+  int axis_of(int id) const {
+    for (size_t i = 0; i < node.size(); ++i)
+      if (node[i] == id) return (int)i;
+    fail(BHT_EINVAL, "internal: node not on an axis");
+  }
+  void view(int axis, int64_t& A, int64_t& I, int64_t& B) const {
+    A = N;
+    for (int i = 0; i < axis; ++i) A *= dims[i];
+    I = dims[axis];
+    B = 1;
+    for (size_t i = axis + 1; i < dims.size(); ++i) B *= dims[i];
+  }
+};
+
+LTensor input_tensor(const bht_tree& t, const void* Y, int dtype, int64_t N) {
+  LTensor C;
+  C.ptr = Y;
+  C.dtype = dtype;
+  C.N = N;
+  C.dims = t.dims;
+  for (int m = 0; m < t.d; ++m) C.node.push_back(t.leaf_of_mode[m]);
+  return C;
+}
+
+// Merge the axes of layer+1 into the index set of `layer` (eq. ht_index_set_construction):
+// a transfer node's two successors are adjacent axes, merged in C-order.
+void reshape_to_layer(const bht_tree& t, LTensor& C, int layer) {
+  std::vector<int64_t> dims;
+  std::vector<int> node;
+  size_t pos = 0;
+  for (int id : t.layers[layer]) {
+    const TNode& nd = t.nodes[id];
+    if (nd.leaf()) {
+      if (pos >= C.node.size() || C.node[pos] != id) fail(BHT_EINVAL, "internal: reshape (leaf)");
+      dims.push_back(C.dims[pos]);
+      pos += 1;
+    } else {
+      if (pos + 1 >= C.node.size() + 1 || C.node[pos] != nd.child[0] || C.node[pos + 1] != nd.child[1])
+        fail(BHT_EINVAL, "internal: reshape (transfer)");
+      dims.push_back(C.dims[pos] * C.dims[pos + 1]);
+      pos += 2;
+    }
+    node.push_back(id);
+  }
+  C.dims = dims;
+  C.node = node;
+}
+
+// Order of contractions over several axes of one layer minimising FP work.
+// ops: (axis, new size). Exhaustive for <= 6 operations.
+std::vector<int> best_order(const std::vector<int64_t>& dims, const std::vector<std::pair<int, int64_t>>& ops) {
+  std::vector<int> perm(ops.size());
+  for (size_t i = 0; i < perm.size(); ++i) perm[i] = (int)i;
+  auto cost = [&](const std::vector<int>& pr) {
+    std::vector<double> d(dims.begin(), dims.end());
+    double c = 0.0;
+    for (int k : pr) {
+      double prod = 1.0;
+      for (size_t i = 0; i < d.size(); ++i) prod *= d[i];
+      c += prod * (double)ops[k].second;  // 2 * I * S * rest, up to the factor 2
+      d[ops[k].first] = (double)ops[k].second;
+    }
+    return c;
+  };
+  if (ops.size() <= 1) return perm;
+  std::vector<int> best = perm;
+  double bc = cost(perm);
+  if (ops.size() <= 6) {
+    while (std::next_permutation(perm.begin(), perm.end())) {
+      const double c = cost(perm);
+      if (c < bc) {
+        bc = c;
+        best = perm;
+      }
+    }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 building blocks
+// ---------------------------------------------------------------------------
+void gram64(const LTensor& C, int axis, double* G, cudaStream_t s) {
+  int64_t A, I, B;
+  C.view(axis, A, I, B);
+  ck(cudaMemsetAsync(G, 0, sizeof(double) * I * I, s), "memset gram");
+  if (C.dtype == BHT_F32)
+    ck(launch_gram_f64<float>(static_cast<const float*>(C.ptr), G, A, I, B, s), "gram");
+  else
+    ck(launch_gram_f64<double>(static_cast<const double*>(C.ptr), G, A, I, B, s), "gram");
+}
+
+// C x_axis M with M(s, t) = M[s * ms + t * mt]; the result is FP64 and owned.
+LTensor ttm64(const LTensor& C, int axis, const double* M, int64_t ms, int64_t mt, int64_t S, cudaStream_t s) {
+  int64_t A, T, B;
+  C.view(axis, A, T, B);
+  LTensor out;
+  out.dtype = BHT_F64;
+  out.N = C.N;
+  out.dims = C.dims;
+  out.dims[axis] = S;
+  out.node = C.node;
+  out.own = DBuf(sizeof(double) * (size_t)std::max<int64_t>(out.numel(), 1), s);
+  out.ptr = out.own.p;
+  if (C.dtype == BHT_F32)
+    ck(launch_ttm_f64<float, double>(static_cast<const float*>(C.ptr), out.own.as<double>(), M, ms, mt, A, T, B, S, s),
+       "ttm");
+  else
+    ck(launch_ttm_f64<double, double>(static_cast<const double*>(C.ptr), out.own.as<double>(), M, ms, mt, A, T, B,
+                                      S, s),
+       "ttm");
+  return out;
+}
+
+// Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j].
+LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
+                      const std::vector<int64_t>& rs, cudaStream_t s) {
+  std::vector<std::pair<int, int64_t>> ops;
+  for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
+  for (int k : best_order(C.dims, ops)) {
+    const int ax = ops[k].first;
+    LTensor nxt = ttm64(C, ax, Us[k], 1, rs[k], rs[k], s);
+    C = std::move(nxt);
+  }
+  return C;
+}
+
+struct EigOut {
+  DBuf V, lam;
+  int64_t n = 0;
+  std::vector<double> h_lam;
+};
+
+// Eigendecomposition of the symmetric FP64 matrix G (destroyed).
+void eig64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
+  out.n = n;
+  out.V = DBuf(sizeof(double) * n * n, s);
+  out.lam = DBuf(sizeof(double) * n, s);
+  DBuf work(eig_workspace_bytes(n), s);
+  ck(launch_eig_sym(G, n, out.lam.as<double>(), out.V.as<double>(), work.p, d_status, s), "eigensolver");
+}
+
+// smallest r >= rmin with sum_{i>=r} max(lam_i, 0) <= eps_nw2 (lam descending); capped at rmax
+int64_t tail_rank(const std::vector<double>& lam, double eps_nw2, int64_t rmin, int64_t rmax) {
+  const int64_t n = (int64_t)lam.size();
+  std::vector<double> tail(n + 1, 0.0);
+  for (int64_t i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + std::max(lam[i], 0.0);
+  int64_t r = n;
+  for (int64_t i = 0; i <= n; ++i)
+    if (tail[i] <= eps_nw2) {
+      r = i;
+      break;
+    }
+  r = std::max(r, rmin);
+  r = std::min(r, std::min(rmax, n));
+  return r;
+}
+
+void check_status(bht_state* st, cudaStream_t s) {
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (h != 0) {
+    cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
+    fail((bht_status)h, "a bounded device-side wait gave up (eigensolver barrier)");
+  }
+}
+
+// Stage host data to the device when needed.
+const void* stage_input(const void* Y, int dtype, int64_t numel, DBuf& staging, cudaStream_t s) {
+  if (is_device_ptr(Y)) return Y;
+  staging = DBuf(dtype_size(dtype) * (size_t)numel, s);
+  ck(cudaMemcpyAsync(staging.p, Y, dtype_size(dtype) * (size_t)numel, cudaMemcpyHostToDevice, s), "H2D batch");
+  return staging.p;
+}
+
+double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_t s) {
+  ck(cudaMemsetAsync(d_acc, 0, sizeof(double), s), "memset");
+  if (dtype == BHT_F32)
+    ck(launch_sqnorm<float>(static_cast<const float*>(x), n, d_acc, s), "sqnorm");
+  else
+    ck(launch_sqnorm<double>(static_cast<const double*>(x), n, d_acc, s), "sqnorm");
+  return 0.0;
+}
+
+// Step 1 of Algorithm 2: project a batch through every layer with the current cores.
+LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, cudaStream_t s) {
+  const bht_tree& t = st->tree;
+  LTensor C = input_tensor(t, Y, dtype, N);
+  for (int layer = t.p; layer >= 1; --layer) {
+    if (layer < t.p) reshape_to_layer(t, C, layer);
+    std::vector<int> ids;
+    std::vector<const double*> Us;
+    std::vector<int64_t> rs;
+    for (int id : t.layers[layer]) {
+      ids.push_back(id);
+      Us.push_back(st->U[id]);
+      rs.push_back(st->rank[id]);
+    }
+    C = project_layer(std::move(C), ids, Us, rs, s);
+  }
+  return C;  // [N][r11][r12]
+}
+
+void validate_opts(const bht_opts* o) {
+  if (o && o->precision != BHT_PREC_FP64 && o->precision != BHT_PREC_MIXED)
+    fail(BHT_EINVAL, "opts.precision must be BHT_PREC_FP64 or BHT_PREC_MIXED");
+  if (o && o->precision == BHT_PREC_MIXED) fail(BHT_EUNSUPPORTED, "mixed precision path not built yet");
+}
+
+// Root buffer with room for `cap` items of r11 x r12, old items zero-padded (eq. incremental_zero_padding1).
+void grow_root(bht_state* st, int64_t r11_old, int64_t r12_old, int64_t r11, int64_t r12, int64_t need,
+               cudaStream_t s) {
+  const bool reshape = (r11 != r11_old || r12 != r12_old);
+  if (!reshape && need <= st->root_cap) return;
+  int64_t cap = std::max<int64_t>(st->root_cap, 16);
+  while (cap < need) cap *= 2;
+  DBuf nr(sizeof(double) * cap * r11 * r12, s);
+  if (st->n_items > 0)
+    ck(launch_copy_pad3<double, double>(st->root, st->n_items, r11_old, r12_old, nr.as<double>(), st->n_items, r11,
+                                        r12, s),
+       "root re-layout");
+  dfree(st->root, s);
+  st->root = static_cast<double*>(nr.release());
+  st->root_cap = cap;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define BHT_API_BEGIN try {
+#define BHT_API_END                                     \
+  return BHT_OK;                                        \
+  }                                                     \
+  catch (const Fail& f) {                               \
+    return f.st;                                        \
+  }                                                     \
+  catch (const std::bad_alloc&) {                       \
+    g_err = "host allocation failed";                   \
+    return BHT_ENOMEM;                                  \
+  }                                                     \
+  catch (...) {                                         \
+    g_err = "unexpected host exception";                \
+    return BHT_ECUDA;                                   \
+  }
+
+extern "C" {
+
+const char* bht_last_error(void) { return g_err.c_str(); }
+const char* bht_version(void) { return "bht-gb300 0.1 (sm_103a)"; }
+
+bht_status bht_launch_count(int64_t* count, int32_t reset) {
+  if (!count) return BHT_EINVAL;
+  *count = g_launches;
+  if (reset) g_launches = 0;
+  return BHT_OK;
+}
+
+bht_status bht_tree_create_balanced(int32_t d, const int64_t* dims, bht_tree** out) {
+  BHT_API_BEGIN
+  if (!out || !dims) fail(BHT_EINVAL, "null argument");
+  if (d < 2 || d > 16) fail(BHT_EINVAL, "d must be in [2, 16]");
+  for (int i = 0; i < d; ++i)
+    if (dims[i] < 1 || dims[i] > 4096) fail(BHT_EINVAL, "every mode size must be in [1, 4096]");
+  bht_tree* t = new bht_tree();
+  build_tree(*t, d, dims);
+  *out = t;
+  BHT_API_END
+}
+
+bht_status bht_tree_destroy(bht_tree* tree) {
+  delete tree;
+  return BHT_OK;
+}
+
+bht_status bht_tree_info(const bht_tree* tree, int32_t* depth, int32_t* num_nodes) {
+  if (!tree) return BHT_EINVAL;
+  if (depth) *depth = tree->p;
+  if (num_nodes) *num_nodes = (int32_t)tree->nodes.size();
+  return BHT_OK;
+}
+
+bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                   const bht_opts* opts, void* stream, bht_state** out) {
+  BHT_API_BEGIN
+  if (!tree || !Y || !out) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bht_tree& t = *tree;
+  int64_t item = 1;
+  for (auto v : t.dims) item *= v;
+  DBuf staging;
+  const void* dY = stage_input(Y, dtype, N * item, staging, s);
+
+  bht_state* st = new bht_state();
+  st->tree = t;
+  st->precision = opts ? opts->precision : BHT_PREC_FP64;
+  st->rank.assign(t.nodes.size(), 0);
+  st->U.assign(t.nodes.size(), nullptr);
+  try {
+    ck(cudaMalloc(&st->d_status, sizeof(int)), "cudaMalloc status");
+    ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
+    DBuf acc(sizeof(double) * 2, s);
+    sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
+    double normY2 = 0.0;
+    ck(cudaMemcpyAsync(&normY2, acc.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norm");
+    ck(cudaStreamSynchronize(s), "sync");
+    if (!std::isfinite(normY2)) fail(BHT_ENUMERIC, "the batch holds non-finite values");
+    // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1)
+    const double eps_nw2 = eps_rel * eps_rel * normY2 / (2.0 * t.d - 2.0);
+
+    LTensor C = input_tensor(t, dY, dtype, N);
+    for (int layer = t.p; layer >= 1; --layer) {
+      if (layer < t.p) reshape_to_layer(t, C, layer);
+      const auto& ids = t.layers[layer];
+      // HOSVD of the layer: every node from the same intermediate
+      std::vector<EigOut> eo(ids.size());
+      for (size_t k = 0; k < ids.size(); ++k) {
+        const int ax = C.axis_of(ids[k]);
+        const int64_t I = C.dims[ax];
+        DBuf G(sizeof(double) * I * I, s);
+        gram64(C, ax, G.as<double>(), s);
+        eig64(G.as<double>(), I, eo[k], st->d_status, s);
+      }
+      for (auto& e : eo) {
+        e.h_lam.resize(e.n);
+        ck(cudaMemcpyAsync(e.h_lam.data(), e.lam.p, sizeof(double) * e.n, cudaMemcpyDeviceToHost, s), "D2H lam");
+      }
+      check_status(st, s);
+      std::vector<const double*> Us;
+      std::vector<int64_t> rs;
+      for (size_t k = 0; k < ids.size(); ++k) {
+        const int64_t n = eo[k].n;
+        const int64_t r = tail_rank(eo[k].h_lam, eps_nw2, 1, n);  // eq. ht_leaf_svd, r >= 1
+        double* U = static_cast<double*>(dalloc(sizeof(double) * n * r, s));
+        ck(launch_copy_cols(eo[k].V.as<double>(), n, n, r, U, r, s), "extract basis");
+        st->U[ids[k]] = U;
+        st->rank[ids[k]] = r;
+        Us.push_back(U);
+        rs.push_back(r);
+      }
+      C = project_layer(std::move(C), ids, Us, rs, s);
+    }
+    // G_0 = reshape(C, [r11, r12, N]) stored item-major
+    grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), N, s);
+    ck(cudaMemcpyAsync(st->root, C.ptr, sizeof(double) * C.numel(), cudaMemcpyDeviceToDevice, s), "root");
+    st->n_items = N;
+    ck(cudaStreamSynchronize(s), "sync");
+    *out = st;
+  } catch (...) {
+    bht_state_destroy(st);
+    throw;
+  }
+  BHT_API_END
+}
+
+bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                         const bht_opts* opts, void* stream, bht_update_info* info) {
+  BHT_API_BEGIN
+  if (!st || !Y) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bht_tree& t = st->tree;
+  int64_t item = 1;
+  for (auto v : t.dims) item *= v;
+  DBuf staging;
+  const void* dY = stage_input(Y, dtype, N * item, staging, s);
+
+  // Step 1: project onto the existing cores; ||Y||^2 and ||C||^2 in FP64
+  DBuf acc(sizeof(double) * 2, s);
+  sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
+  LTensor Cbar = project_all(st, dY, dtype, N, s);
+  sqnorm_of(Cbar.ptr, BHT_F64, Cbar.numel(), acc.as<double>() + 1, s);
+  double h[2];
+  ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H norms");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (!std::isfinite(h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
+  const double eps_des = eps_rel * std::sqrt(h[0]);
+  const double eps_proj = std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold
+  const int64_t r11_old = st->r11(), r12_old = st->r12();
+  if (eps_proj <= eps_des) {
+    grow_root(st, r11_old, r12_old, r11_old, r12_old, st->n_items + N, s);
+    ck(cudaMemcpyAsync(st->root + st->n_items * r11_old * r12_old, Cbar.ptr, sizeof(double) * Cbar.numel(),
+                       cudaMemcpyDeviceToDevice, s),
+       "root append");
+    st->n_items += N;
+    ck(cudaStreamSynchronize(s), "sync");
+    if (info) *info = bht_update_info{1, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items};
+    return BHT_OK;
+  }
+  Cbar = LTensor();
+
+  // Steps 2-3 layer by layer; the new cores live in a shadow copy until commit
+  const double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
+  std::vector<int64_t> rank = st->rank;
+  std::vector<double*> U = st->U;
+  std::vector<double*> fresh;  // buffers created by this call
+  auto own = [&](double* p) { fresh.push_back(p); return p; };
+  try {
+    LTensor C = input_tensor(t, dY, dtype, N);
+    for (int layer = t.p; layer >= 1; --layer) {
+      if (layer < t.p) reshape_to_layer(t, C, layer);
+      const auto& ids = t.layers[layer];
+      std::vector<EigOut> eo(ids.size());
+      std::vector<int64_t> alpha(ids.size()), rold(ids.size());
+      for (size_t k = 0; k < ids.size(); ++k) {
+        const int ax = C.axis_of(ids[k]);
+        const int64_t a = C.dims[ax];
+        alpha[k] = a;
+        rold[k] = rank[ids[k]];
+        // residual Gram R R^T = Pi G Pi with Pi = I - U U^T (eq. compute_residual)
+        DBuf G(sizeof(double) * a * a, s), Pi(sizeof(double) * a * a, s), H(sizeof(double) * a * a, s);
+        gram64(C, ax, G.as<double>(), s);
+        ck(launch_fill_identity(Pi.as<double>(), a, s), "identity");
+        ck(launch_gemm_f64(a, a, rold[k], -1.0, U[ids[k]], rold[k], 1, U[ids[k]], 1, rold[k], 1.0, Pi.as<double>(),
+                           a, 1, s),
+           "Pi = I - U U^T");
+        ck(launch_gemm_f64(a, a, a, 1.0, Pi.as<double>(), a, 1, G.as<double>(), a, 1, 0.0, H.as<double>(), a, 1, s),
+           "Pi G");
+        ck(launch_gemm_f64(a, a, a, 1.0, H.as<double>(), a, 1, Pi.as<double>(), a, 1, 0.0, G.as<double>(), a, 1, s),
+           "Pi G Pi");
+        eig64(G.as<double>(), a, eo[k], st->d_status, s);
+      }
+      for (auto& e : eo) {
+        e.h_lam.resize(e.n);
+        ck(cudaMemcpyAsync(e.h_lam.data(), e.lam.p, sizeof(double) * e.n, cudaMemcpyDeviceToHost, s), "D2H lam");
+      }
+      check_status(st, s);
+      std::vector<int> grown_parents;
+      for (size_t k = 0; k < ids.size(); ++k) {
+        const int id = ids[k];
+        const int64_t a = alpha[k], r0 = rold[k];
+        // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
+        const int64_t rR = tail_rank(eo[k].h_lam, eps_nw2, 0, std::max<int64_t>(a - r0, 0));
+        if (rR == 0) continue;
+        DBuf UR(sizeof(double) * a * rR, s), W(sizeof(double) * r0 * rR + 8, s);
+        ck(launch_copy_cols(eo[k].V.as<double>(), a, a, rR, UR.as<double>(), rR, s), "U_R");
+        // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)
+        for (int pass = 0; pass < 2 && r0 > 0; ++pass) {
+          ck(launch_gemm_f64(r0, rR, a, 1.0, U[id], 1, r0, UR.as<double>(), rR, 1, 0.0, W.as<double>(), rR, 1, s),
+             "U^T U_R");
+          ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, s),
+             "U_R -= U W");
+        }
+        // symmetric orthonormalisation U_R <- U_R S^{-1/2}, S = U_R^T U_R
+        {
+          DBuf S(sizeof(double) * rR * rR, s), Wm(sizeof(double) * rR * rR, s), T(sizeof(double) * a * rR, s);
+          ck(launch_gemm_f64(rR, rR, a, 1.0, UR.as<double>(), 1, rR, UR.as<double>(), rR, 1, 0.0, S.as<double>(), rR,
+                             1, s),
+             "S");
+          EigOut se;
+          eig64(S.as<double>(), rR, se, st->d_status, s);
+          // Wm = V diag(mu^-1/2) V^T
+          DBuf Vs(sizeof(double) * rR * rR, s);
+          ck(cudaMemcpyAsync(Vs.p, se.V.p, sizeof(double) * rR * rR, cudaMemcpyDeviceToDevice, s), "copy");
+          ck(launch_scale_cols_invsqrt(Vs.as<double>(), rR, se.lam.as<double>(), s), "scale");
+          ck(launch_gemm_f64(rR, rR, rR, 1.0, Vs.as<double>(), rR, 1, se.V.as<double>(), 1, rR, 0.0, Wm.as<double>(),
+                             rR, 1, s),
+             "S^-1/2");
+          ck(launch_gemm_f64(a, rR, rR, 1.0, UR.as<double>(), rR, 1, Wm.as<double>(), rR, 1, 0.0, T.as<double>(), rR,
+                             1, s),
+             "U_R S^-1/2");
+          ck(cudaMemcpyAsync(UR.p, T.p, sizeof(double) * a * rR, cudaMemcpyDeviceToDevice, s), "copy");
+          check_status(st, s);
+        }
+        // expandCore: U^k = [U^{k-1}, U_R] (eq. concatenating_orthonormal_vectors)
+        const int64_t rn = r0 + rR;
+        double* Un = own(static_cast<double*>(dalloc(sizeof(double) * a * rn, s)));
+        if (r0 > 0) ck(launch_copy_cols(U[id], r0, a, r0, Un, rn, s), "expand old");
+        ck(launch_copy_cols(UR.as<double>(), rR, a, rR, Un + r0, rn, s), "expand new");
+        U[id] = Un;
+        rank[id] = rn;
+        const int par = t.nodes[id].parent;
+        if (par > 0 && std::find(grown_parents.begin(), grown_parents.end(), par) == grown_parents.end())
+          grown_parents.push_back(par);
+      }
+      // padWithZeros of every parent whose successor grew (eq. incremental_zero_padding1)
+      for (int par : grown_parents) {
+        const TNode& pn = t.nodes[par];
+        const int c0 = pn.child[0], c1 = pn.child[1];
+        // child ranks before this layer's expansion
+        int64_t ra0 = rank[c0], rb0 = rank[c1];
+        for (size_t k = 0; k < ids.size(); ++k) {
+          if (ids[k] == c0) ra0 = rold[k];
+          if (ids[k] == c1) rb0 = rold[k];
+        }
+        const int64_t rp = rank[par];
+        double* Pn = own(static_cast<double*>(dalloc(sizeof(double) * rank[c0] * rank[c1] * rp, s)));
+        ck(launch_copy_pad3<double, double>(U[par], ra0, rb0, rp, Pn, rank[c0], rank[c1], rp, s), "pad parent");
+        U[par] = Pn;
+      }
+      // Step 1 revisited: project onto the updated cores of the layer
+      std::vector<const double*> Us;
+      std::vector<int64_t> rs;
+      for (int id : ids) {
+        Us.push_back(U[id]);
+        rs.push_back(rank[id]);
+      }
+      C = project_layer(std::move(C), ids, Us, rs, s);
+    }
+    // eq. incremental_root_concatenate with the root zero-padded in modes 1, 2
+    const int64_t r11 = rank[t.nodes[0].child[0]], r12 = rank[t.nodes[0].child[1]];
+    grow_root(st, r11_old, r12_old, r11, r12, st->n_items + N, s);
+    ck(cudaMemcpyAsync(st->root + st->n_items * r11 * r12, C.ptr, sizeof(double) * C.numel(),
+                       cudaMemcpyDeviceToDevice, s),
+       "root append");
+    ck(cudaStreamSynchronize(s), "sync");
+  } catch (...) {
+    for (double* p : fresh) dfree(p, s);
+    cudaStreamSynchronize(s);
+    throw;
+  }
+  // commit: release the replaced cores and any intermediate core superseded within this call
+  for (size_t id = 1; id < U.size(); ++id)
+    if (U[id] != st->U[id]) dfree(st->U[id], s);
+  for (double* p : fresh)
+    if (std::find(U.begin(), U.end(), p) == U.end()) dfree(p, s);
+  st->U = U;
+  st->rank = rank;
+  st->n_items += N;
+  ck(cudaStreamSynchronize(s), "sync");
+  if (info) *info = bht_update_info{0, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items};
+  BHT_API_END
+}
+
+bht_status ht_reconstruct(const bht_state* st, int64_t first, int64_t count, void* out, int32_t dtype,
+                          void* stream) {
+  BHT_API_BEGIN
+  if (!st || !out) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (first < 0 || count < 0 || first + count > st->n_items) fail(BHT_EINVAL, "item range outside the accumulation");
+  if (count == 0) return BHT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bht_tree& t = st->tree;
+  LTensor C;
+  C.dtype = BHT_F64;
+  C.N = count;
+  C.dims = {st->r11(), st->r12()};
+  C.node = {t.nodes[0].child[0], t.nodes[0].child[1]};
+  C.ptr = st->root + first * st->r11() * st->r12();
+  for (int layer = 1; layer <= t.p; ++layer) {
+    // expand every node of this layer: axis r -> rows (eq. htucker_reconstruction)
+    std::vector<std::pair<int, int64_t>> ops;
+    std::vector<int> ids;
+    for (int id : t.layers[layer]) {
+      ids.push_back(id);
+      ops.push_back({C.axis_of(id), st->rows(id)});
+    }
+    for (int k : best_order(C.dims, ops)) {
+      const int id = ids[k];
+      const int ax = C.axis_of(id);
+      const int64_t r = st->rank[id], a = st->rows(id);
+      LTensor nxt = ttm64(C, ax, st->U[id], r, 1, a, s);
+      C = std::move(nxt);
+    }
+    // split transfer axes into their successors' axes (C-order)
+    std::vector<int64_t> dims;
+    std::vector<int> node;
+    for (size_t i = 0; i < C.node.size(); ++i) {
+      const TNode& nd = t.nodes[C.node[i]];
+      if (nd.layer == layer && !nd.leaf()) {
+        dims.push_back(st->rank[nd.child[0]]);
+        dims.push_back(st->rank[nd.child[1]]);
+        node.push_back(nd.child[0]);
+        node.push_back(nd.child[1]);
+      } else {
+        dims.push_back(C.dims[i]);
+        node.push_back(C.node[i]);
+      }
+    }
+    C.dims = dims;
+    C.node = node;
+  }
+  const int64_t n = C.numel();
+  const bool dev = is_device_ptr(out);
+  if (dtype == BHT_F64) {
+    ck(cudaMemcpyAsync(out, C.ptr, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "copy out");
+  } else {
+    DBuf tmp;
+    float* dst = static_cast<float*>(out);
+    if (!dev) {
+      tmp = DBuf(sizeof(float) * n, s);
+      dst = tmp.as<float>();
+    }
+    ck(launch_cast<double, float>(static_cast<const double*>(C.ptr), dst, n, s), "cast");
+    if (!dev) ck(cudaMemcpyAsync(out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "D2H");
+    ck(cudaStreamSynchronize(s), "sync");
+  }
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t N, double* out, void* stream) {
+  BHT_API_BEGIN
+  if (!st || !Y || !out) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t item = 1;
+  for (auto v : st->tree.dims) item *= v;
+  DBuf staging;
+  const void* dY = stage_input(Y, dtype, N * item, staging, s);
+  LTensor C = project_all(st, dY, dtype, N, s);
+  const bool dev = is_device_ptr(out);
+  ck(cudaMemcpyAsync(out, C.ptr, sizeof(double) * C.numel(), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     s),
+     "copy out");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_get_ranks(const bht_state* st, int64_t* ranks, int64_t cap) {
+  if (!st || !ranks) return BHT_EINVAL;
+  const int64_t nn = (int64_t)st->tree.nodes.size();
+  if (cap < nn) return BHT_ECAPACITY;
+  ranks[0] = st->n_items;
+  for (int64_t i = 1; i < nn; ++i) ranks[i] = st->rank[i];
+  return BHT_OK;
+}
+
+bht_status bht_get_dims(const bht_state* st, int32_t* d, int64_t* dims, int64_t cap) {
+  if (!st) return BHT_EINVAL;
+  if (d) *d = st->tree.d;
+  if (dims) {
+    if (cap < st->tree.d) return BHT_ECAPACITY;
+    for (int i = 0; i < st->tree.d; ++i) dims[i] = st->tree.dims[i];
+  }
+  return BHT_OK;
+}
+
+bht_status bht_get_core(const bht_state* st, int32_t node, double* host_out, int64_t cap, int64_t* numel) {
+  BHT_API_BEGIN
+  if (!st) fail(BHT_EINVAL, "null state");
+  if (node < 1 || node >= (int32_t)st->tree.nodes.size()) fail(BHT_EINVAL, "node must be in [1, 2d-2]");
+  const int64_t n = st->rows(node) * st->rank[node];
+  if (numel) *numel = n;
+  if (host_out) {
+    if (cap < n) fail(BHT_ECAPACITY, "output too small");
+    ck(cudaMemcpy(host_out, st->U[node], sizeof(double) * n, cudaMemcpyDeviceToHost), "D2H core");
+  }
+  BHT_API_END
+}
+
+bht_status bht_get_root(const bht_state* st, int64_t first, int64_t count, double* host_out, int64_t cap) {
+  BHT_API_BEGIN
+  if (!st || !host_out) fail(BHT_EINVAL, "null argument");
+  if (first < 0 || count < 0 || first + count > st->n_items) fail(BHT_EINVAL, "item range outside the accumulation");
+  const int64_t per = st->r11() * st->r12();
+  if (cap < per * count) fail(BHT_ECAPACITY, "output too small");
+  if (count)
+    ck(cudaMemcpy(host_out, st->root + first * per, sizeof(double) * per * count, cudaMemcpyDeviceToHost),
+       "D2H root");
+  BHT_API_END
+}
+
+bht_status bht_num_elements(const bht_state* st, int64_t* cores_total) {
+  if (!st || !cores_total) return BHT_EINVAL;
+  int64_t n = 0;
+  for (size_t id = 1; id < st->tree.nodes.size(); ++id) n += st->rows((int)id) * st->rank[id];
+  n += st->n_items * st->r11() * st->r12();
+  *cores_total = n;
+  return BHT_OK;
+}
+
+bht_status bht_state_destroy(bht_state* st) {
+  if (!st) return BHT_OK;
+  cudaDeviceSynchronize();
+  for (double* p : st->U)
+    if (p) cudaFreeAsync(p, nullptr);
+  if (st->root) cudaFreeAsync(st->root, nullptr);
+  cudaDeviceSynchronize();
+  if (st->d_status) cudaFree(st->d_status);
+  delete st;
+  return BHT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,463 @@
+// dense.cu — FP64 SIMT kernels of the plain path: Gram matrices of mode
+// unfoldings, mode products (TTM), norms, small FP64 GEMMs and copies.
+//
+// Every full-data contraction of BHT-l2r (Algorithm 1) and HT-RISE
+// (Algorithm 2) is one of two shapes over a view [A][I][B] of a layer
+// intermediate (Section 2.1 unfolding of the node's index I):
+//   Gram : G = X_(I) X_(I)^T                      (the SVD of eq. ht_leaf_svd
+//          is taken through the eigenvectors of this Gram matrix)
+//   TTM  : X x_I M, M = U^T to project (eq. ht_leaf_contraction) or M = U to
+//          expand (eq. htucker_reconstruction).
+// GB300 has few FP64 units (≈1/64 of the FP32 rate), so these kernels are
+// FP64-ALU bound; they are the reference GPU form the mixed path is measured
+// against.
+#include "internal.cuh"
+
+namespace bht {
+
+namespace {
+
+constexpr int TILE = 64;   // output tile edge
+constexpr int BK = 16;     // depth of one shared-memory stage
+constexpr int NT = 256;    // threads per CTA (16 x 16, each 4 x 4 outputs)
+
+template <typename T>
+__device__ __forceinline__ double ld_as_double(const T* p) { return static_cast<double>(*p); }
+
+// ---------------------------------------------------------------------------
+// Gram of the middle index of X[A][I][B]
+// grid.x: upper-triangular tile pairs (ti <= tj), grid.y: chunks of the
+// flattened column index k = a * B + b.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, double* __restrict__ G,
+                                                      int64_t A, int64_t I, int64_t B,
+                                                      int64_t kchunk, int ntiles) {
+  __shared__ double Xi[BK][TILE + 1];
+  __shared__ double Xj[BK][TILE + 1];
+  // decode the tile pair (ti, tj), ti <= tj, from blockIdx.x
+  int pid = blockIdx.x, ti = 0;
+  while (pid >= ntiles - ti) { pid -= ntiles - ti; ++ti; }
+  const int tj = ti + pid;
+  const int64_t i0 = (int64_t)ti * TILE, j0 = (int64_t)tj * TILE;
+  const int64_t K = A * B;
+  const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+  const int64_t kend = min(K, kbeg + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool along_k = B >= 8;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    // load BK x TILE slabs of rows i0.. and j0..
+    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+      int kk, ii;
+      if (along_k) { kk = e % BK; ii = e / BK; } else { ii = e % TILE; kk = e / TILE; }
+      const int64_t k = k0 + kk;
+      double vi = 0.0, vj = 0.0;
+      if (k < kend) {
+        const int64_t a = k / B, b = k - a * B;
+        const int64_t base = a * I * B + b;
+        if (i0 + ii < I) vi = ld_as_double(X + base + (i0 + ii) * B);
+        if (ti != tj && j0 + ii < I) vj = ld_as_double(X + base + (j0 + ii) * B);
+      }
+      Xi[kk][ii] = vi;
+      if (ti != tj) Xj[kk][ii] = vj;
+    }
+    __syncthreads();
+    const double (*Bj)[TILE + 1] = (ti == tj) ? Xi : Xj;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Xi[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bj[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = i0 + ty + 16 * u;
+    if (i >= I) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t j = j0 + tx + 16 * v;
+      if (j >= I) continue;
+      if (ti == tj) {
+        atomicAdd(G + i * I + j, acc[u][v]);
+      } else {
+        atomicAdd(G + i * I + j, acc[u][v]);
+        atomicAdd(G + j * I + i, acc[u][v]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TTM: out[a][s][b] = sum_t M(s,t) X[a][t][b]
+// grid.x: tiles of the flattened column c = a * B + b, grid.y: tiles of s.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(NT) ttm_f64_kernel(const Tin* __restrict__ X, Tout* __restrict__ out,
+                                                     const double* __restrict__ M, int64_t ms, int64_t mt,
+                                                     int64_t A, int64_t T, int64_t B, int64_t S) {
+  __shared__ double Ms[BK][TILE + 1];
+  __shared__ double Xs[BK][TILE + 1];
+  const int64_t c0 = (int64_t)blockIdx.x * TILE;
+  const int64_t s0 = (int64_t)blockIdx.y * TILE;
+  const int64_t AB = A * B;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool m_along_s = (ms == 1);
+  const bool x_along_c = B >= 8;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+  for (int64_t t0 = 0; t0 < T; t0 += BK) {
+    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+      int kk, ss;
+      if (m_along_s) { ss = e % TILE; kk = e / TILE; } else { kk = e % BK; ss = e / BK; }
+      const int64_t t = t0 + kk, sidx = s0 + ss;
+      Ms[kk][ss] = (t < T && sidx < S) ? M[sidx * ms + t * mt] : 0.0;
+    }
+    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+      int kk, cc;
+      if (x_along_c) { cc = e % TILE; kk = e / TILE; } else { kk = e % BK; cc = e / BK; }
+      const int64_t t = t0 + kk, c = c0 + cc;
+      double v = 0.0;
+      if (t < T && c < AB) {
+        const int64_t a = c / B, b = c - a * B;
+        v = ld_as_double(X + (a * T + t) * B + b);
+      }
+      Xs[kk][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Ms[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Xs[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = c0 + tx + 16 * v;
+    if (c >= AB) continue;
+    const int64_t a = c / B, b = c - a * B;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t sidx = s0 + ty + 16 * u;
+      if (sidx < S) out[(a * S + sidx) * B + b] = static_cast<Tout>(acc[u][v]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generic small FP64 GEMM with strided operands
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                      const double* __restrict__ Am, int64_t a_rs, int64_t a_cs,
+                                                      const double* __restrict__ Bm, int64_t b_rs, int64_t b_cs,
+                                                      double beta, double* __restrict__ C, int64_t c_rs,
+                                                      int64_t c_cs) {
+  __shared__ double As[BK][TILE + 1];
+  __shared__ double Bs[BK][TILE + 1];
+  const int64_t m0 = (int64_t)blockIdx.y * TILE, n0 = (int64_t)blockIdx.x * TILE;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  const bool a_along_m = (a_rs == 1);
+  const bool b_along_n = (b_cs == 1);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+      int kk, mm;
+      if (a_along_m) { mm = e % TILE; kk = e / TILE; } else { kk = e % BK; mm = e / BK; }
+      const int64_t k = k0 + kk, m = m0 + mm;
+      As[kk][mm] = (k < K && m < M) ? Am[m * a_rs + k * a_cs] : 0.0;
+    }
+    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+      int kk, nn;
+      if (b_along_n) { nn = e % TILE; kk = e / TILE; } else { kk = e % BK; nn = e / BK; }
+      const int64_t k = k0 + kk, n = n0 + nn;
+      Bs[kk][nn] = (k < K && n < N) ? Bm[k * b_rs + n * b_cs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t m = m0 + ty + 16 * u;
+    if (m >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t n = n0 + tx + 16 * v;
+      if (n >= N) continue;
+      double* cp = C + m * c_rs + n * c_cs;
+      *cp = (beta == 0.0) ? alpha * acc[u][v] : alpha * acc[u][v] + beta * (*cp);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions and copies
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void sqnorm_kernel(const T* __restrict__ x, int64_t n, double* __restrict__ acc) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = static_cast<double>(x[i]);
+    s = fma(v, v, s);
+  }
+  __shared__ double red[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+  }
+}
+
+__global__ void trace_kernel(const double* __restrict__ G, int64_t n, double* __restrict__ acc) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += G[i * n + i];
+  __shared__ double red[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+  }
+}
+
+template <typename Tin, typename Tout>
+__global__ void copy_pad3_kernel(const Tin* __restrict__ in, int64_t A1, int64_t B1, int64_t C1,
+                                 Tout* __restrict__ out, int64_t A2, int64_t B2, int64_t C2) {
+  const int64_t total = A2 * B2 * C2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e % C2;
+    const int64_t ab = e / C2;
+    const int64_t b = ab % B2, a = ab / B2;
+    Tout v = Tout(0);
+    if (a < A1 && b < B1 && c < C1) v = static_cast<Tout>(in[(a * B1 + b) * C1 + c]);
+    out[e] = v;
+  }
+}
+
+__global__ void copy_cols_kernel(const double* __restrict__ in, int64_t ld_in, int64_t rows, int64_t cols,
+                                 double* __restrict__ out, int64_t ld_out) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    out[i * ld_out + j] = in[i * ld_in + j];
+  }
+}
+
+template <typename Tin, typename Tout>
+__global__ void cast_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = static_cast<Tout>(in[i]);
+}
+
+__global__ void scale_cols_invsqrt_kernel(double* __restrict__ W, int64_t k, const double* __restrict__ lam) {
+  const int64_t total = k * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e % k;
+    W[e] *= rsqrt(fmax(lam[j], 1e-300));
+  }
+}
+
+__global__ void fill_identity_kernel(double* __restrict__ A, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    A[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+template <typename T>
+__global__ void check_finite_kernel(const T* __restrict__ x, int64_t n, int* __restrict__ flag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(static_cast<double>(x[i]));
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+}
+
+int grid_for(int64_t n, int threads = 256, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
+  if (A <= 0 || I <= 0 || B <= 0) return cudaSuccess;
+  const int ntiles = (int)((I + TILE - 1) / TILE);
+  const int pairs = ntiles * (ntiles + 1) / 2;
+  const int64_t K = A * B;
+  // enough CTAs to fill the GPU several times, each with at least 256 columns
+  int64_t want = (4 * 152 + pairs - 1) / pairs;
+  int64_t chunks = (K + 255) / 256;
+  if (chunks > want) chunks = want;
+  if (chunks < 1) chunks = 1;
+  int64_t kchunk = (K + chunks - 1) / chunks;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  chunks = (K + kchunk - 1) / kchunk;
+  dim3 grid(pairs, (unsigned)chunks);
+  gram_f64_kernel<T><<<grid, NT, 0, s>>>(X, G, A, I, B, kchunk, ntiles);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_ttm_f64(const Tin* X, Tout* out, const double* M, int64_t ms, int64_t mt, int64_t A,
+                           int64_t T, int64_t B, int64_t S, cudaStream_t s) {
+  if (A <= 0 || B <= 0 || S <= 0) return cudaSuccess;
+  const int64_t AB = A * B;
+  dim3 grid((unsigned)((AB + TILE - 1) / TILE), (unsigned)((S + TILE - 1) / TILE));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  ttm_f64_kernel<Tin, Tout><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sqnorm(const T* x, int64_t n, double* acc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  sqnorm_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, acc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const double* G, int64_t n, double* acc, cudaStream_t s) {
+  trace_kernel<<<1, 256, 0, s>>>(G, n, acc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
+                            int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
+                            int64_t c_rs, int64_t c_cs, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((M + TILE - 1) / TILE));
+  gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_copy_pad3(const Tin* in, int64_t A1, int64_t B1, int64_t C1, Tout* out, int64_t A2,
+                             int64_t B2, int64_t C2, cudaStream_t s) {
+  const int64_t total = A2 * B2 * C2;
+  if (total <= 0) return cudaSuccess;
+  copy_pad3_kernel<Tin, Tout><<<grid_for(total), 256, 0, s>>>(in, A1, B1, C1, out, A2, B2, C2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t rows, int64_t cols, double* out,
+                             int64_t ld_out, cudaStream_t s) {
+  if (rows * cols <= 0) return cudaSuccess;
+  copy_cols_kernel<<<grid_for(rows * cols), 256, 0, s>>>(in, ld_in, rows, cols, out, ld_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cast_kernel<Tin, Tout><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols_invsqrt(double* W, int64_t k, const double* lam, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  scale_cols_invsqrt_kernel<<<grid_for(k * k), 256, 0, s>>>(W, k, lam);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fill_identity_kernel<<<grid_for(n * n), 256, 0, s>>>(A, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_finite_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, flag);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t launch_gram_f64<float>(const float*, double*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_gram_f64<double>(const double*, double*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f64<float, double>(const float*, double*, const double*, int64_t, int64_t, int64_t,
+                                                   int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f64<double, double>(const double*, double*, const double*, int64_t, int64_t,
+                                                    int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f64<double, float>(const double*, float*, const double*, int64_t, int64_t,
+                                                   int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_sqnorm<float>(const float*, int64_t, double*, cudaStream_t);
+template cudaError_t launch_sqnorm<double>(const double*, int64_t, double*, cudaStream_t);
+template cudaError_t launch_copy_pad3<double, double>(const double*, int64_t, int64_t, int64_t, double*, int64_t,
+                                                      int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_copy_pad3<float, float>(const float*, int64_t, int64_t, int64_t, float*, int64_t,
+                                                    int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_copy_pad3<double, float>(const double*, int64_t, int64_t, int64_t, float*, int64_t,
+                                                     int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_cast<float, double>(const float*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);
+template cudaError_t launch_check_finite<double>(const double*, int64_t, int*, cudaStream_t);
+
+}  // namespace bht
