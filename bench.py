@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Throughput of the batch hierarchical Tucker hot path (BHT-l2r + HT-RISE) on GB300.
+
+One step = one pass of the whole path over one synthetic stream: BHT-l2r
+(Algorithm 1) on the first increment, HT-RISE (Algorithm 2) on each later
+increment. Default workload: the 64^3 advected spectral field, 20 increments of
+32 snapshots (671 MB of fp32), eps_rel = 1e-2, inputs resident in HBM when the
+timed region starts. The metric is GB/s of fp32 stream compressed.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s of tensor stream compressed (BHT-l2r+HT-RISE) at rel err<=eps, fast vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=os.environ.get("BHT_BENCH_PRECISION", "fp64"))
+    ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--increments", type=int, default=20)
+    ap.add_argument("--items", type=int, default=32)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"advected spectral field {a.n}^3 (|k|<=16, |k|^-5/3), {a.increments} increments x {a.items} "
+            f"snapshots, eps_rel={a.eps:g}")
+
+
+def gen_stream(a, seed):
+    import bht_synth
+    Y = bht_synth.spectral_field(seed, 0, a.increments * a.items, n=a.n)
+    return Y.reshape(a.increments, a.items, a.n, a.n, a.n)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the FP64 CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(Yhost, eps, seconds):
+    """BHT-l2r on increment 1, then HT-RISE while the budget lasts. Returns (bytes, s, increments, state)."""
+    import oracle
+    t0 = time.perf_counter()
+    st = oracle.bht_l2r(Yhost[0], eps)
+    done = 1
+    while done < len(Yhost) and time.perf_counter() - t0 < seconds:
+        oracle.htrise_update(st, Yhost[done], eps)
+        done += 1
+    dt = time.perf_counter() - t0
+    return done * Yhost[0].nbytes, dt, done, st
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    Y = gen_stream(a, 0)
+    nthreads = os.cpu_count()
+    for _ in range(a.warmup):
+        oracle_sample(Y, a.eps, 1.0)  # BHT-l2r on increment 1 at least
+    times, nbytes, incs = [], 0, 0
+    for _ in range(a.steps):
+        b, dt, done, _ = oracle_sample(Y, a.eps, min(a.cpu_seconds, 8.0))
+        times.append(dt)
+        nbytes, incs = b, done
+    ms = 1000.0 * statistics.mean(times)
+    gbs = nbytes / (ms / 1000.0) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "sample": f"first {incs} of {a.increments} increments per step"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"BHT-l2r on increment 1 + HT-RISE on increments 2..{incs} (numpy FP64)"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+# algorithmic work per kernel class, see the design doc (roofline section)
+PEAK_FP64_TFLOPS = 1.25  # FP64 nominal of the profiling recipe table (no measured FP64 peak is provided)
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_2412_16544_gb300 as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    Yh = gen_stream(a, seed=rank)                  # each rank compresses its own independent stream
+    Yd = torch.from_numpy(Yh).to(dev)              # resident in HBM before the timed region
+    bytes_per_step = Yh.nbytes
+    tree = B.bht_tree_create_balanced([a.n] * 3)
+    stream = torch.cuda.current_stream()
+
+    def one_pass(prec, src):
+        st = B.bht_l2r(tree, src[0], a.eps, precision=prec)
+        skips = 0
+        for k in range(1, a.increments):
+            info = B.htrise_update(st, src[k], a.eps, precision=prec)
+            skips += int(info.skipped)
+        return st, skips
+
+    def timed(prec, steps, warmup, profile_mask=0):
+        for _ in range(warmup):
+            st, _ = one_pass(prec, Yd)
+            B.bht_state_destroy(st)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        B.bht_launch_count(reset=True)
+        B.bht_profile_read(reset=True)
+        B.bht_profile_enable(profile_mask)
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        states = []
+        e0.record(stream)
+        for _ in range(steps):
+            st, skips = one_pass(prec, Yd)
+            states.append((st, skips))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        B.bht_profile_enable(0)
+        launches = B.bht_launch_count(reset=True)
+        prof = B.bht_profile_read(reset=True, work=True)
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, launches / steps, prof, clocks, states
+
+    # profiled pass: which kernel class dominates (all classes timed)
+    B.bht_profile_read(reset=True)
+    B.bht_profile_enable((1 << B.KERNEL_CLASSES) - 1)
+    st, _ = one_pass(a.precision, Yd)
+    torch.cuda.synchronize()
+    B.bht_profile_enable(0)
+    breakdown = B.bht_profile_read(reset=True)
+    B.bht_state_destroy(st)
+    dom_name = max(breakdown, key=lambda k: breakdown[k][0])
+    dom_cls = [B.bht_kernel_class_name(i) for i in range(B.KERNEL_CLASSES)].index(dom_name)
+
+    ms, launches, prof, clocks, states = timed(a.precision, a.steps, a.warmup, profile_mask=1 << dom_cls)
+    value = bytes_per_step * world / (ms / 1000.0) / 1e9
+
+    # accuracy of the last timed pass: per-increment relative error of the reconstruction
+    st, skips = states[-1]
+    ranks = B.bht_get_ranks(st)
+    errs = []
+    for k in sorted({0, 1, a.increments // 2, a.increments - 1}):
+        rec = B.ht_reconstruct(st, k * a.items, a.items, dtype="float32")
+        errs.append(float(torch.linalg.vector_norm(rec - Yd[k]) / torch.linalg.vector_norm(Yd[k])))
+    cores = B.bht_num_elements(st)
+    cr = a.increments * a.items * a.n ** 3 / cores
+    for s_, _ in states:
+        B.bht_state_destroy(s_)
+
+    # the plain FP64 GPU arm, for the fast-vs-plain comparison
+    plain = None
+    if a.precision != "fp64" and not a.no_fp64_arm:
+        ms64, _, _, _, st64 = timed("fp64", 1, 1)
+        for s_, _ in st64:
+            B.bht_state_destroy(s_)
+        plain = {"value": bytes_per_step * world / (ms64 / 1000.0) / 1e9, "unit": "GB/s", "ms_per_step": ms64}
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not a.no_e2e:
+        Yp = torch.from_numpy(Yh).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st_e, _ = one_pass(a.precision, Yp)
+        root = B.bht_get_root(st_e, 0, a.increments * a.items)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": bytes_per_step / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(Yh.nbytes),
+               "d2h_bytes_per_step": int(root.nbytes)}
+        B.bht_state_destroy(st_e)
+
+    # CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    oracle_diff = None
+    if rank == 0 and not a.no_cpu_baseline:
+        nb, dt, incs, ost = oracle_sample(Yh, a.eps, a.cpu_seconds)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"BHT-l2r on increment 1 + HT-RISE on increments 2..{incs} of the same stream "
+                         f"({nb / 1e6:.0f} MB, numpy FP64)"}
+        import oracle
+        st1 = B.bht_l2r(tree, Yd[0], a.eps, precision=a.precision)
+        r_gpu = B.ht_reconstruct(st1, 0, a.items, dtype="float64").cpu().numpy()
+        r_or = oracle.reconstruct(ost, 0, a.items)
+        oracle_diff = float(np.linalg.norm(r_gpu - r_or) / np.linalg.norm(Yh[0]))
+        B.bht_state_destroy(st1)
+
+    # roofline of the dominant kernel class (algorithmic work accumulated by the library)
+    dom_ms, dom_n, flops, nbytes = prof.get(dom_name, (0.0, 0, 0.0, 0.0))
+    roof = None
+    if dom_n:
+        if dom_name in ("ttm_tc", "gram_f32", "copy", "norm"):
+            ach = nbytes / dom_n / (dom_ms / dom_n / 1000.0) / 1e9
+            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+                if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "kernel": dom_name, "launches_per_step": dom_n / a.steps}
+        else:
+            ach = flops / dom_n / (dom_ms / dom_n / 1000.0) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / PEAK_FP64_TFLOPS, "traffic": None, "kernel": dom_name,
+                    "launches_per_step": dom_n / a.steps,
+                    "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)"}
+
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32" if a.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "precision": a.precision, "items_per_step": a.increments * a.items,
+                   "bytes_per_step": bytes_per_step, "parallelism": f"{world} independent streams",
+                   "l2": "inputs (671 MB per stream) larger than L2 (129 MB); no flush"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+        "plain_fp64": plain,
+        "accuracy": {"max_rel_err_per_increment": max(errs), "eps_rel": a.eps,
+                     "rel_diff_vs_oracle_increment1": oracle_diff},
+        "stream": {"ranks": ranks, "skipped_updates": skips, "updates": a.increments - 1, "compression_ratio": cr},
+        "kernel_breakdown_ms": {k: round(v[0], 4) for k, v in breakdown.items() if v[1]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank)
+        return
+    run_ours(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,18 @@ bht_status bht_state_destroy(bht_state* state);
  * last reset (a plain counter kept by the host side of the library). */
 bht_status bht_launch_count(int64_t* count, int32_t reset);
 
+/* Optional kernel timing. With bit c of class_mask set, every launch of
+ * kernel class c made by the calling thread is bracketed by a CUDA event pair
+ * recorded on its launch stream. bht_profile_read() waits for the recorded
+ * events and returns, per class c < n (n >= 10), the summed durations in ms,
+ * the launch counts and the algorithmic work of the timed launches (flops and
+ * bytes the mathematics of each launch requires); reset != 0 clears them.
+ * Any output pointer may be NULL. Class names come from bht_kernel_class_name(c). */
+bht_status bht_profile_enable(uint32_t class_mask);
+bht_status bht_profile_read(double* ms, int64_t* launches, double* flops, double* bytes, int32_t n,
+                            int32_t reset);
+const char* bht_kernel_class_name(int32_t cls);
+
 const char* bht_last_error(void);
 const char* bht_version(void);
 

@@ -64,6 +64,8 @@ def _load():
         "bht_num_elements": [vp, P(i64)],
         "bht_state_destroy": [vp],
         "bht_launch_count": [P(i64), i32],
+        "bht_profile_enable": [ctypes.c_uint32],
+        "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -73,13 +75,17 @@ def _load():
     lib.bht_last_error.argtypes = []
     lib.bht_version.restype = ctypes.c_char_p
     lib.bht_version.argtypes = []
+    lib.bht_kernel_class_name.restype = ctypes.c_char_p
+    lib.bht_kernel_class_name.argtypes = [i32]
     return lib
 
 
 _lib = _load()
 EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
-            "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version"]
+            "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name"]
+KERNEL_CLASSES = 10
 
 
 def _check(status: int, where: str):
@@ -264,6 +270,26 @@ def bht_launch_count(reset: bool = False) -> int:
     n = ctypes.c_int64()
     _check(_lib.bht_launch_count(ctypes.byref(n), 1 if reset else 0), "bht_launch_count")
     return n.value
+
+
+def bht_profile_enable(class_mask: int) -> None:
+    _check(_lib.bht_profile_enable(int(class_mask)), "bht_profile_enable")
+
+
+def bht_profile_read(reset: bool = False, work: bool = False) -> dict:
+    """Per kernel class: (ms, launches) or, with work=True, (ms, launches, flops, bytes)."""
+    ms = (ctypes.c_double * KERNEL_CLASSES)()
+    n = (ctypes.c_int64 * KERNEL_CLASSES)()
+    fl = (ctypes.c_double * KERNEL_CLASSES)()
+    by = (ctypes.c_double * KERNEL_CLASSES)()
+    _check(_lib.bht_profile_read(ms, n, fl, by, KERNEL_CLASSES, 1 if reset else 0), "bht_profile_read")
+    if work:
+        return {bht_kernel_class_name(i): (ms[i], n[i], fl[i], by[i]) for i in range(KERNEL_CLASSES)}
+    return {bht_kernel_class_name(i): (ms[i], n[i]) for i in range(KERNEL_CLASSES)}
+
+
+def bht_kernel_class_name(cls: int) -> str:
+    return _lib.bht_kernel_class_name(int(cls)).decode()
 
 
 def bht_version() -> str:

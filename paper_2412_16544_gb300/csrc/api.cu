@@ -43,8 +43,75 @@ void ck(cudaError_t e, const char* what) {
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// optional per-launch CUDA-event profiler (per kernel class, per host thread)
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+thread_local uint32_t g_prof_mask = 0;
+thread_local std::vector<ProfRec> g_prof_pending;
+thread_local std::vector<cudaEvent_t> g_prof_pool;
+thread_local double g_prof_ms[bht::K_NUM_CLASSES] = {};
+thread_local int64_t g_prof_n[bht::K_NUM_CLASSES] = {};
+thread_local double g_prof_flops[bht::K_NUM_CLASSES] = {};
+thread_local double g_prof_bytes[bht::K_NUM_CLASSES] = {};
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_resolve() {
+  for (auto& r : g_prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_prof_ms[r.cls] += ms;
+      g_prof_n[r.cls] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+}
+}  // namespace
+
 namespace bht {
 void note_launch(int n) { g_launches += n; }
+
+const char* kernel_class_name(int cls) {
+  static const char* names[K_NUM_CLASSES] = {"gram_f64", "ttm_f64", "eig_small_f64", "eig_coop_f64", "gemm_f64",
+                                             "norm", "copy", "ttm_tc", "gram_f32", "other"};
+  return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
+}
+
+ProfScope::ProfScope(int cls, cudaStream_t s, double flops, double bytes)
+    : cls_(cls), s_(s), on_(((g_prof_mask >> cls) & 1u) != 0) {
+  if (on_) {
+    g_prof_flops[cls] += flops;
+    g_prof_bytes[cls] += bytes;
+    e0_ = prof_event();
+    cudaEventRecord(e0_, s_);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (on_) {
+    cudaEvent_t e1 = prof_event();
+    cudaEventRecord(e1, s_);
+    g_prof_pending.push_back({cls_, e0_, e1});
+  }
+}
 }  // namespace bht
 
 using namespace bht;
@@ -458,6 +525,32 @@ extern "C" {
 
 const char* bht_last_error(void) { return g_err.c_str(); }
 const char* bht_version(void) { return "bht-gb300 0.1 (sm_103a)"; }
+
+bht_status bht_profile_enable(uint32_t class_mask) {
+  g_prof_mask = class_mask;
+  return BHT_OK;
+}
+
+bht_status bht_profile_read(double* ms, int64_t* launches, double* flops, double* bytes, int32_t n,
+                            int32_t reset) {
+  if (n < K_NUM_CLASSES) return BHT_ECAPACITY;
+  prof_resolve();
+  for (int i = 0; i < K_NUM_CLASSES; ++i) {
+    if (ms) ms[i] = g_prof_ms[i];
+    if (launches) launches[i] = g_prof_n[i];
+    if (flops) flops[i] = g_prof_flops[i];
+    if (bytes) bytes[i] = g_prof_bytes[i];
+    if (reset) {
+      g_prof_ms[i] = 0.0;
+      g_prof_n[i] = 0;
+      g_prof_flops[i] = 0.0;
+      g_prof_bytes[i] = 0.0;
+    }
+  }
+  return BHT_OK;
+}
+
+const char* bht_kernel_class_name(int32_t cls) { return kernel_class_name(cls); }
 
 bht_status bht_launch_count(int64_t* count, int32_t reset) {
   if (!count) return BHT_EINVAL;

@@ -349,6 +349,8 @@ cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   chunks = (K + kchunk - 1) / kchunk;
   dim3 grid(pairs, (unsigned)chunks);
+  ProfScope prof(K_GRAM_F64, s, (double)I * (double)(I + 1) * (double)K,
+                 (double)sizeof(T) * (double)K * (double)I + 8.0 * (double)I * (double)I);
   gram_f64_kernel<T><<<grid, NT, 0, s>>>(X, G, A, I, B, kchunk, ntiles);
   note_launch();
   return cudaGetLastError();
@@ -361,6 +363,8 @@ cudaError_t launch_ttm_f64(const Tin* X, Tout* out, const double* M, int64_t ms,
   const int64_t AB = A * B;
   dim3 grid((unsigned)((AB + TILE - 1) / TILE), (unsigned)((S + TILE - 1) / TILE));
   if (grid.y > 65535) return cudaErrorInvalidValue;
+  ProfScope prof(K_TTM_F64, s, 2.0 * (double)S * (double)T * (double)AB,
+                 (double)sizeof(Tin) * (double)AB * (double)T + (double)sizeof(Tout) * (double)AB * (double)S);
   ttm_f64_kernel<Tin, Tout><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S);
   note_launch();
   return cudaGetLastError();
@@ -369,12 +373,14 @@ cudaError_t launch_ttm_f64(const Tin* X, Tout* out, const double* M, int64_t ms,
 template <typename T>
 cudaError_t launch_sqnorm(const T* x, int64_t n, double* acc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_NORM, s, 2.0 * (double)n, (double)sizeof(T) * (double)n);
   sqnorm_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, acc);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const double* G, int64_t n, double* acc, cudaStream_t s) {
+  ProfScope prof(K_NORM, s);
   trace_kernel<<<1, 256, 0, s>>>(G, n, acc);
   note_launch();
   return cudaGetLastError();
@@ -385,6 +391,8 @@ cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const
                             int64_t c_rs, int64_t c_cs, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((M + TILE - 1) / TILE));
+  ProfScope prof(K_GEMM_F64, s, 2.0 * (double)M * (double)N * (double)K,
+                 8.0 * ((double)M * (double)K + (double)K * (double)N + (double)M * (double)N));
   gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs);
   note_launch();
   return cudaGetLastError();
@@ -395,6 +403,7 @@ cudaError_t launch_copy_pad3(const Tin* in, int64_t A1, int64_t B1, int64_t C1, 
                              int64_t B2, int64_t C2, cudaStream_t s) {
   const int64_t total = A2 * B2 * C2;
   if (total <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s, 0.0, (double)(sizeof(Tin) * A1 * B1 * C1 + sizeof(Tout) * total));
   copy_pad3_kernel<Tin, Tout><<<grid_for(total), 256, 0, s>>>(in, A1, B1, C1, out, A2, B2, C2);
   note_launch();
   return cudaGetLastError();
@@ -403,6 +412,7 @@ cudaError_t launch_copy_pad3(const Tin* in, int64_t A1, int64_t B1, int64_t C1, 
 cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t rows, int64_t cols, double* out,
                              int64_t ld_out, cudaStream_t s) {
   if (rows * cols <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
   copy_cols_kernel<<<grid_for(rows * cols), 256, 0, s>>>(in, ld_in, rows, cols, out, ld_out);
   note_launch();
   return cudaGetLastError();
@@ -411,6 +421,7 @@ cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t rows, int6
 template <typename Tin, typename Tout>
 cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
   cast_kernel<Tin, Tout><<<grid_for(n), 256, 0, s>>>(in, out, n);
   note_launch();
   return cudaGetLastError();
@@ -418,6 +429,7 @@ cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
 
 cudaError_t launch_scale_cols_invsqrt(double* W, int64_t k, const double* lam, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
   scale_cols_invsqrt_kernel<<<grid_for(k * k), 256, 0, s>>>(W, k, lam);
   note_launch();
   return cudaGetLastError();
@@ -425,6 +437,7 @@ cudaError_t launch_scale_cols_invsqrt(double* W, int64_t k, const double* lam, c
 
 cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
   fill_identity_kernel<<<grid_for(n * n), 256, 0, s>>>(A, n);
   note_launch();
   return cudaGetLastError();
@@ -433,6 +446,7 @@ cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_NORM, s);
   check_finite_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, flag);
   note_launch();
   return cudaGetLastError();

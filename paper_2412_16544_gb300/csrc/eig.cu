@@ -393,6 +393,7 @@ cudaError_t launch_eig_sym(double* G, int64_t n, double* lam, double* V, void* w
       cudaFuncSetAttribute(eig_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_set = true;
     }
+    ProfScope prof(K_EIG_SMALL, s, 9.0 * (double)n * (double)n * (double)n, 24.0 * (double)n * (double)n);
     eig_small_kernel<<<1, EIG_THREADS, sm, s>>>(G, (int)n, lam, V, VT);
     note_launch();
     return cudaGetLastError();
@@ -400,7 +401,10 @@ cudaError_t launch_eig_sym(double* G, int64_t n, double* lam, double* V, void* w
   // Frobenius norm for the absolute rotation threshold, read back to the host
   cudaError_t e = cudaMemsetAsync(nrm, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
-  fro_norm_kernel<<<152, 256, 0, s>>>(G, n * n, nrm);
+  {
+    ProfScope prof(K_NORM, s);
+    fro_norm_kernel<<<152, 256, 0, s>>>(G, n * n, nrm);
+  }
   note_launch();
   double h_nrm = 0.0;
   e = cudaMemcpyAsync(&h_nrm, nrm, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -427,7 +431,10 @@ cudaError_t launch_eig_sym(double* G, int64_t n, double* lam, double* V, void* w
   int blocks = nsm * (per_sm > 2 ? 2 : per_sm);
   int nn = (int)n;
   void* args[] = {&G, &nn, &lam, &V, &VT, &bar, &status, &h_nrm, &diagv, &offv};
-  e = cudaLaunchCooperativeKernel((void*)eig_coop_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
+  {
+    ProfScope prof(K_EIG_COOP, s, 9.0 * (double)n * (double)n * (double)n, 24.0 * (double)n * (double)n);
+    e = cudaLaunchCooperativeKernel((void*)eig_coop_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
+  }
   note_launch();
   return e;
 }

@@ -10,6 +10,34 @@ namespace bht {
 // Launch counter (kernels launched by the library on the calling thread).
 void note_launch(int n = 1);
 
+// Kernel classes timed by the optional per-launch CUDA-event profiler.
+enum KernelClass {
+  K_GRAM_F64 = 0,
+  K_TTM_F64 = 1,
+  K_EIG_SMALL = 2,
+  K_EIG_COOP = 3,
+  K_GEMM_F64 = 4,
+  K_NORM = 5,
+  K_COPY = 6,
+  K_TTM_TC = 7,
+  K_GRAM_F32 = 8,
+  K_OTHER = 9,
+  K_NUM_CLASSES = 10
+};
+const char* kernel_class_name(int cls);
+
+// Records a CUDA event pair around one launch on `s` when the class is enabled.
+// `flops` and `bytes` are the algorithmic work of the launch (what the math
+// requires, not what the kernel happens to do), summed per class.
+struct ProfScope {
+  ProfScope(int cls, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
+  ~ProfScope();
+  int cls_;
+  cudaStream_t s_;
+  bool on_;
+  cudaEvent_t e0_ = nullptr;
+};
+
 // Status word written by kernels that can fail on the device (bounded waits,
 // non-finite data). 0 = fine; otherwise a bht_status code.
 struct DevStatus {
