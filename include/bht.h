@@ -69,10 +69,11 @@ typedef enum { BHT_F32 = 0, BHT_F64 = 1 } bht_dtype;
 /* Arithmetic of the path.
  *   BHT_PREC_FP64 : every contraction, Gram matrix, eigensolve and norm in FP64
  *                   (the plain GPU form of the method).
- *   BHT_PREC_MIXED: the full-data contractions (Gram matrices and mode
- *                   products over the batch) on tcgen05 tensor cores in TF32
- *                   with FP32 accumulation (split-precision 3xTF32 when
- *                   eps_rel < 5e-3); node eigensolves, re-orthogonalisation,
+ *   BHT_PREC_MIXED: mode products of an innermost axis on tcgen05 tensor
+ *                   cores (split TF32: three TF32 products, FP32
+ *                   accumulation), other mode products in FP32, Gram matrices
+ *                   with FP32 products summed in FP64 (FP64 Grams when
+ *                   eps_rel < 1e-3); node eigensolves, re-orthogonalisation,
  *                   norms and the skip test stay in FP64. */
 typedef enum { BHT_PREC_FP64 = 0, BHT_PREC_MIXED = 1 } bht_precision;
 
@@ -133,6 +134,27 @@ bht_status ht_reconstruct(const bht_state* state, int64_t first, int64_t count,
  * (device or host). Never modifies the state. */
 bht_status ht_encode(const bht_state* state, const void* Y, int32_t dtype, int64_t N,
                      double* out, void* stream);
+
+/* One mode product over the innermost axis (eq. ht_leaf_contraction for that
+ * axis, Section 2.1 contraction with U^T):
+ *     out[(o * S + s) * R2 + i] = sum_k X[(o * R2 + i) * K + k] * U[k * S + s]
+ * X: fp32 device [rows][K]; U: FP64 device basis [K][S] (row-major, the
+ * layout of a leaf core); out: fp32 device. R2 places the new axis: R2 = 1
+ * keeps it innermost, R2 = rows / (item count) moves it in front of the other
+ * axes. precision BHT_PREC_MIXED runs the tcgen05 tensor-core kernel (split
+ * TF32: x = x_hi + x_lo, U = U_hi + U_lo, three TF32 products, FP32
+ * accumulation; K % 4 == 0); BHT_PREC_FP64 the FP64 SIMT kernel (R2 = 1).
+ * norms (nullable, device, 2 doubles) receives ||X||^2 and ||out||^2 added
+ * in FP64 (mixed only). Synchronises `stream`. */
+bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S,
+                            int32_t precision, float* out, int64_t R2, double* norms, void* stream);
+
+/* Node eigensolver (the error-truncated SVD of eq. ht_leaf_svd taken through
+ * the Gram matrix of the unfolding): G is a symmetric FP64 device matrix
+ * [n][n] (overwritten); lam receives all n eigenvalues in descending order;
+ * U ([n][r] row-major, device) the orthonormal eigenvectors of the r largest
+ * ones. n <= 4096. Synchronises `stream`. */
+bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, void* stream);
 
 /* Getters. Ranks: ranks[0] = items in the accumulation, ranks[i] = rank of
  * node i (breadth-first) for i = 1 .. 2d-2; `cap` is the length of `ranks`. */

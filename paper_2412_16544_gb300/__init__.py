@@ -65,6 +65,8 @@ def _load():
         "bht_state_destroy": [vp],
         "bht_launch_count": [P(i64), i32],
         "bht_profile_enable": [ctypes.c_uint32],
+        "bht_mode_product": [vp, i64, i64, vp, i64, i32, vp, i64, vp, vp],
+        "bht_sym_eig": [vp, i64, vp, vp, i64, vp],
         "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
     }
     for name, args in sig.items():
@@ -84,8 +86,8 @@ _lib = _load()
 EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
-            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name"]
-KERNEL_CLASSES = 10
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig"]
+KERNEL_CLASSES = 16
 
 
 def _check(status: int, where: str):
@@ -272,6 +274,31 @@ def bht_launch_count(reset: bool = False) -> int:
     return n.value
 
 
+def bht_mode_product(X, U, S: int, precision="mixed", R2: int = 1, out=None, norms=None, stream=None):
+    """out[(o S + s) R2 + i] = sum_k X[o R2 + i, k] U[k, s] on device tensors (X fp32 [rows, K], U fp64 [K, S])."""
+    torch = _torch()
+    rows, K = X.shape
+    if out is None:
+        out = torch.empty(rows * S, dtype=torch.float32, device=X.device)
+    code = {"fp64": BHT_PREC_FP64, "mixed": BHT_PREC_MIXED}.get(precision, precision)
+    nptr = ctypes.c_void_p(norms.data_ptr()) if norms is not None else None
+    _check(_lib.bht_mode_product(ctypes.c_void_p(X.data_ptr()), rows, K, ctypes.c_void_p(U.data_ptr()), int(S),
+                                 int(code), ctypes.c_void_p(out.data_ptr()), int(R2), nptr, _stream(stream)),
+           "bht_mode_product")
+    return out
+
+
+def bht_sym_eig(G, r: int, stream=None):
+    """Eigenvalues (descending) and the r leading eigenvectors of a symmetric fp64 CUDA tensor G (overwritten)."""
+    torch = _torch()
+    n = G.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=G.device)
+    U = torch.empty((n, max(r, 1)), dtype=torch.float64, device=G.device)
+    _check(_lib.bht_sym_eig(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
+                            ctypes.c_void_p(U.data_ptr()), int(r), _stream(stream)), "bht_sym_eig")
+    return lam, U[:, :r]
+
+
 def bht_profile_enable(class_mask: int) -> None:
     _check(_lib.bht_profile_enable(int(class_mask)), "bht_profile_enable")
 
@@ -283,9 +310,10 @@ def bht_profile_read(reset: bool = False, work: bool = False) -> dict:
     fl = (ctypes.c_double * KERNEL_CLASSES)()
     by = (ctypes.c_double * KERNEL_CLASSES)()
     _check(_lib.bht_profile_read(ms, n, fl, by, KERNEL_CLASSES, 1 if reset else 0), "bht_profile_read")
+    names = [bht_kernel_class_name(i) for i in range(KERNEL_CLASSES)]
     if work:
-        return {bht_kernel_class_name(i): (ms[i], n[i], fl[i], by[i]) for i in range(KERNEL_CLASSES)}
-    return {bht_kernel_class_name(i): (ms[i], n[i]) for i in range(KERNEL_CLASSES)}
+        return {names[i]: (ms[i], n[i], fl[i], by[i]) for i in range(KERNEL_CLASSES) if names[i] != "?"}
+    return {names[i]: (ms[i], n[i]) for i in range(KERNEL_CLASSES) if names[i] != "?"}
 
 
 def bht_kernel_class_name(cls: int) -> str:

@@ -90,8 +90,10 @@ namespace bht {
 void note_launch(int n) { g_launches += n; }
 
 const char* kernel_class_name(int cls) {
-  static const char* names[K_NUM_CLASSES] = {"gram_f64", "ttm_f64", "eig_small_f64", "eig_coop_f64", "gemm_f64",
-                                             "norm", "copy", "ttm_tc", "gram_f32", "other"};
+  static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
+                                             "gemm_f64",       "norm",           "copy",            "ttm_tc",
+                                             "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
+                                             "other"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -353,66 +355,140 @@ std::vector<int> best_order(const std::vector<int64_t>& dims, const std::vector<
 }
 
 // ---------------------------------------------------------------------------
-// FP64 building blocks
+// Arithmetic of one call
+//   FP64 : every contraction, Gram, norm and eigensolve in FP64.
+//   mixed: full-data contractions of an innermost axis on tcgen05 tensor cores
+//          (split TF32, FP32 accumulation), other contractions in FP32 SIMT,
+//          Grams with FP32 products promoted to FP64 every 16 columns; node
+//          eigensolves, orthogonalisation and norms in FP64. At tight
+//          tolerances (eps_rel < 1e-3) the Grams stay FP64 and the basis
+//          enters the tensor cores with its TF32 remainder (three products).
 // ---------------------------------------------------------------------------
-void gram64(const LTensor& C, int axis, double* G, cudaStream_t s) {
+struct Arith {
+  bool mixed = false;
+  bool tight = false;
+  int* d_status = nullptr;
+};
+
+void gram_any(const LTensor& C, int axis, double* G, const Arith& ar, cudaStream_t s) {
   int64_t A, I, B;
   C.view(axis, A, I, B);
   ck(cudaMemsetAsync(G, 0, sizeof(double) * I * I, s), "memset gram");
-  if (C.dtype == BHT_F32)
+  if (C.dtype == BHT_F32 && ar.mixed && !ar.tight)
+    ck(launch_gram_f32(static_cast<const float*>(C.ptr), G, A, I, B, s), "gram");
+  else if (C.dtype == BHT_F32)
     ck(launch_gram_f64<float>(static_cast<const float*>(C.ptr), G, A, I, B, s), "gram");
   else
     ck(launch_gram_f64<double>(static_cast<const double*>(C.ptr), G, A, I, B, s), "gram");
 }
 
-// C x_axis M with M(s, t) = M[s * ms + t * mt]; the result is FP64 and owned.
-LTensor ttm64(const LTensor& C, int axis, const double* M, int64_t ms, int64_t mt, int64_t S, cudaStream_t s) {
+// Mode product of axis `axis`: the axis (size T) becomes size S, new(s) = sum_t M(s, t) old(t),
+// M(s, t) = U[s * ms + t * mt] (projection: U [T][S], ms = 1, mt = S; expansion: U [S][T], ms = T, mt = 1).
+// rotate: only for the innermost axis, the new axis moves to the front (right after the items).
+// norm_in (nullable, device double): ||C||^2 added in FP64 when the tensor-core kernel runs.
+LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t mt, int64_t S, bool rotate,
+                const Arith& ar, cudaStream_t s, double* norm_in = nullptr, bool* used_norm = nullptr) {
   int64_t A, T, B;
   C.view(axis, A, T, B);
+  if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
   LTensor out;
-  out.dtype = BHT_F64;
   out.N = C.N;
   out.dims = C.dims;
-  out.dims[axis] = S;
   out.node = C.node;
-  out.own = DBuf(sizeof(double) * (size_t)std::max<int64_t>(out.numel(), 1), s);
+  out.dims[axis] = S;
+  if (rotate) {  // new axis in front: [N][S][other axes in order]
+    std::rotate(out.dims.begin(), out.dims.begin() + axis, out.dims.begin() + axis + 1);
+    std::rotate(out.node.begin(), out.node.begin() + axis, out.node.begin() + axis + 1);
+  }
+  const int64_t R2 = rotate ? A / C.N : 1;  // rows per item behind the new axis
+  if (used_norm) *used_norm = false;
+  if (!ar.mixed) {
+    if (rotate) fail(BHT_EINVAL, "internal: rotation in the FP64 form");
+    out.dtype = BHT_F64;
+    out.own = DBuf(sizeof(double) * (size_t)std::max<int64_t>(out.numel(), 1), s);
+    out.ptr = out.own.p;
+    if (C.dtype == BHT_F32)
+      ck(launch_ttm_f64<float, double>(static_cast<const float*>(C.ptr), out.own.as<double>(), U, ms, mt, A, T, B,
+                                       S, s),
+         "ttm");
+    else
+      ck(launch_ttm_f64<double, double>(static_cast<const double*>(C.ptr), out.own.as<double>(), U, ms, mt, A, T, B,
+                                        S, s),
+         "ttm");
+    return out;
+  }
+  out.dtype = BHT_F32;
+  out.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(out.numel(), 1), s);
   out.ptr = out.own.p;
+  const int nb = 2;  // the basis enters as TF32 plus its TF32 remainder: no rounding bias in any norm
+  const bool aligned = (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0;
+  if (B == 1 && C.dtype == BHT_F32 && aligned && ttm_tc_supported(T, S, nb)) {
+    DBuf W(ttm_tc_weights_bytes(T, S), s);
+    // W[s][t] = M(s, t): projection reads U transposed (ldu = S), expansion reads U as is (ldu = T)
+    const bool transpose = (ms == 1);
+    ck(launch_prep_tc_weights(U, T, S, transpose ? S : T, transpose, W.as<float>(), nb, s), "tc weights");
+    ck(launch_ttm_tc(static_cast<const float*>(C.ptr), A, T, W.as<float>(), S, nb, out.own.as<float>(), R2, norm_in,
+                     nullptr, ar.d_status, s),
+       "tensor-core mode product");
+    if (used_norm) *used_norm = norm_in != nullptr;
+    return out;
+  }
   if (C.dtype == BHT_F32)
-    ck(launch_ttm_f64<float, double>(static_cast<const float*>(C.ptr), out.own.as<double>(), M, ms, mt, A, T, B, S, s),
+    ck(launch_ttm_f32<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), U, ms, mt, A, T, B, S, R2, s),
        "ttm");
   else
-    ck(launch_ttm_f64<double, double>(static_cast<const double*>(C.ptr), out.own.as<double>(), M, ms, mt, A, T, B,
-                                      S, s),
+    ck(launch_ttm_f32<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), U, ms, mt, A, T, B, S, R2, s),
        "ttm");
   return out;
 }
 
-// Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j].
+// Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j], cheapest order first.
 LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
-                      const std::vector<int64_t>& rs, cudaStream_t s) {
+                      const std::vector<int64_t>& rs, const Arith& ar, cudaStream_t s) {
   std::vector<std::pair<int, int64_t>> ops;
   for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
   for (int k : best_order(C.dims, ops)) {
-    const int ax = ops[k].first;
-    LTensor nxt = ttm64(C, ax, Us[k], 1, rs[k], rs[k], s);
+    LTensor nxt = ttm_any(C, C.axis_of(ids[k]), Us[k], 1, rs[k], rs[k], false, ar, s);
     C = std::move(nxt);
   }
   return C;
 }
 
 struct EigOut {
-  DBuf V, lam;
+  DBuf work, lam;
   int64_t n = 0;
   std::vector<double> h_lam;
 };
 
-// Eigendecomposition of the symmetric FP64 matrix G (destroyed).
-void eig64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
+// Stage 1 of the eigensolver: every eigenvalue of the symmetric FP64 matrix G (destroyed).
+void eig_values64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
   out.n = n;
-  out.V = DBuf(sizeof(double) * n * n, s);
   out.lam = DBuf(sizeof(double) * n, s);
-  DBuf work(eig_workspace_bytes(n), s);
-  ck(launch_eig_sym(G, n, out.lam.as<double>(), out.V.as<double>(), work.p, d_status, s), "eigensolver");
+  out.work = DBuf(eig_workspace_bytes(n), s);
+  ck(launch_eig_values(G, n, out.lam.as<double>(), out.work.p, d_status, s), "eigenvalues");
+}
+
+// X (rows x r) <- X (3I - X^T X) / 2, twice: Newton-Schulz orthonormalisation of nearly orthonormal columns.
+void newton_schulz(double* X, int64_t rows, int64_t r, cudaStream_t s) {
+  if (r <= 0) return;
+  DBuf S(sizeof(double) * r * r, s), T(sizeof(double) * rows * r, s);
+  for (int it = 0; it < 2; ++it) {
+    ck(launch_gemm_f64(r, r, rows, -0.5, X, 1, r, X, r, 1, 0.0, S.as<double>(), r, 1, s), "X^T X");
+    ck(launch_add_diag(S.as<double>(), r, 1.5, s), "1.5 I");
+    ck(launch_gemm_f64(rows, r, r, 1.0, X, r, 1, S.as<double>(), r, 1, 0.0, T.as<double>(), r, 1, s), "X S");
+    ck(cudaMemcpyAsync(X, T.p, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s), "copy");
+  }
+}
+
+// Stage 2: orthonormal eigenvectors of the r largest eigenvalues, [n][r] row-major, owned by the caller.
+double* eig_vectors64(EigOut& eo, int64_t r, cudaStream_t s) {
+  const int64_t n = eo.n;
+  double* U = static_cast<double*>(dalloc(sizeof(double) * n * std::max<int64_t>(r, 1), s));
+  if (r == 0) return U;
+  DBuf scratch(eig_vectors_scratch_bytes(n, r), s);
+  ck(launch_eig_vectors(n, r, eo.lam.as<double>(), U, eo.work.p, scratch.p, s), "eigenvectors");
+  newton_schulz(U, n, r, s);
+  return U;
 }
 
 // smallest r >= rmin with sum_{i>=r} max(lam_i, 0) <= eps_nw2 (lam descending); capped at rmax
@@ -459,28 +535,76 @@ double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_
 }
 
 // Step 1 of Algorithm 2: project a batch through every layer with the current cores.
-LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, cudaStream_t s) {
+// Mode products on distinct axes commute, so every leaf is contracted first
+// (the mixed form always takes the innermost axis and rotates the result to
+// the front, which after d steps restores the mode order), then the transfer
+// nodes layer by layer. norm_y (nullable): ||Y||^2 when a kernel folded it.
+LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, const Arith& ar, cudaStream_t s,
+                    double* norm_acc = nullptr, bool* norm_done = nullptr) {
   const bht_tree& t = st->tree;
   LTensor C = input_tensor(t, Y, dtype, N);
-  for (int layer = t.p; layer >= 1; --layer) {
-    if (layer < t.p) reshape_to_layer(t, C, layer);
+  if (norm_done) *norm_done = false;
+  if (ar.mixed) {
+    for (int step = 0; step < t.d; ++step) {
+      const int ax = (int)C.dims.size() - 1;
+      const int id = C.node[ax];
+      bool used = false;
+      LTensor nxt = ttm_any(C, ax, st->U[id], 1, st->rank[id], st->rank[id], true, ar, s,
+                            step == 0 ? norm_acc : nullptr, &used);
+      if (step == 0 && norm_done) *norm_done = used;
+      C = std::move(nxt);
+    }
+  } else {
     std::vector<int> ids;
     std::vector<const double*> Us;
     std::vector<int64_t> rs;
-    for (int id : t.layers[layer]) {
+    for (int m = 0; m < t.d; ++m) {
+      const int id = t.leaf_of_mode[m];
       ids.push_back(id);
       Us.push_back(st->U[id]);
       rs.push_back(st->rank[id]);
     }
-    C = project_layer(std::move(C), ids, Us, rs, s);
+    C = project_layer(std::move(C), ids, Us, rs, ar, s);
+  }
+  for (int layer = t.p - 1; layer >= 1; --layer) {
+    reshape_to_layer(t, C, layer);
+    std::vector<int> ids;
+    std::vector<const double*> Us;
+    std::vector<int64_t> rs;
+    for (int id : t.layers[layer]) {
+      if (t.nodes[id].leaf()) continue;  // already contracted
+      ids.push_back(id);
+      Us.push_back(st->U[id]);
+      rs.push_back(st->rank[id]);
+    }
+    C = project_layer(std::move(C), ids, Us, rs, ar, s);
   }
   return C;  // [N][r11][r12]
+}
+
+Arith make_arith(int precision, double eps_rel, int* d_status) {
+  Arith ar;
+  ar.mixed = precision == BHT_PREC_MIXED;
+  ar.tight = eps_rel < 1e-3;
+  ar.d_status = d_status;
+  return ar;
+}
+
+// out (device, n elements of `out_dtype`) <- C (device, C.dtype)
+void copy_convert(const LTensor& C, void* out, int out_dtype, cudaStream_t s) {
+  const int64_t n = C.numel();
+  if (C.dtype == out_dtype) {
+    ck(cudaMemcpyAsync(out, C.ptr, dtype_size(out_dtype) * n, cudaMemcpyDeviceToDevice, s), "copy");
+  } else if (C.dtype == BHT_F32) {
+    ck(launch_cast<float, double>(static_cast<const float*>(C.ptr), static_cast<double*>(out), n, s), "cast");
+  } else {
+    ck(launch_cast<double, float>(static_cast<const double*>(C.ptr), static_cast<float*>(out), n, s), "cast");
+  }
 }
 
 void validate_opts(const bht_opts* o) {
   if (o && o->precision != BHT_PREC_FP64 && o->precision != BHT_PREC_MIXED)
     fail(BHT_EINVAL, "opts.precision must be BHT_PREC_FP64 or BHT_PREC_MIXED");
-  if (o && o->precision == BHT_PREC_MIXED) fail(BHT_EUNSUPPORTED, "mixed precision path not built yet");
 }
 
 // Root buffer with room for `cap` items of r11 x r12, old items zero-padded (eq. incremental_zero_padding1).
@@ -535,7 +659,14 @@ bht_status bht_profile_read(double* ms, int64_t* launches, double* flops, double
                             int32_t reset) {
   if (n < K_NUM_CLASSES) return BHT_ECAPACITY;
   prof_resolve();
-  for (int i = 0; i < K_NUM_CLASSES; ++i) {
+  for (int i = 0; i < n; ++i) {
+    if (i >= K_NUM_CLASSES) {
+      if (ms) ms[i] = 0.0;
+      if (launches) launches[i] = 0;
+      if (flops) flops[i] = 0.0;
+      if (bytes) bytes[i] = 0.0;
+      continue;
+    }
     if (ms) ms[i] = g_prof_ms[i];
     if (launches) launches[i] = g_prof_n[i];
     if (flops) flops[i] = g_prof_flops[i];
@@ -614,6 +745,7 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
     if (!std::isfinite(normY2)) fail(BHT_ENUMERIC, "the batch holds non-finite values");
     // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1)
     const double eps_nw2 = eps_rel * eps_rel * normY2 / (2.0 * t.d - 2.0);
+    const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
 
     LTensor C = input_tensor(t, dY, dtype, N);
     for (int layer = t.p; layer >= 1; --layer) {
@@ -625,8 +757,8 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
         const int ax = C.axis_of(ids[k]);
         const int64_t I = C.dims[ax];
         DBuf G(sizeof(double) * I * I, s);
-        gram64(C, ax, G.as<double>(), s);
-        eig64(G.as<double>(), I, eo[k], st->d_status, s);
+        gram_any(C, ax, G.as<double>(), ar, s);
+        eig_values64(G.as<double>(), I, eo[k], st->d_status, s);
       }
       for (auto& e : eo) {
         e.h_lam.resize(e.n);
@@ -638,18 +770,17 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
       for (size_t k = 0; k < ids.size(); ++k) {
         const int64_t n = eo[k].n;
         const int64_t r = tail_rank(eo[k].h_lam, eps_nw2, 1, n);  // eq. ht_leaf_svd, r >= 1
-        double* U = static_cast<double*>(dalloc(sizeof(double) * n * r, s));
-        ck(launch_copy_cols(eo[k].V.as<double>(), n, n, r, U, r, s), "extract basis");
+        double* U = eig_vectors64(eo[k], r, s);
         st->U[ids[k]] = U;
         st->rank[ids[k]] = r;
         Us.push_back(U);
         rs.push_back(r);
       }
-      C = project_layer(std::move(C), ids, Us, rs, s);
+      C = project_layer(std::move(C), ids, Us, rs, ar, s);
     }
     // G_0 = reshape(C, [r11, r12, N]) stored item-major
     grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), N, s);
-    ck(cudaMemcpyAsync(st->root, C.ptr, sizeof(double) * C.numel(), cudaMemcpyDeviceToDevice, s), "root");
+    copy_convert(C, st->root, BHT_F64, s);
     st->n_items = N;
     ck(cudaStreamSynchronize(s), "sync");
     *out = st;
@@ -676,22 +807,24 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   const void* dY = stage_input(Y, dtype, N * item, staging, s);
 
   // Step 1: project onto the existing cores; ||Y||^2 and ||C||^2 in FP64
+  const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
   DBuf acc(sizeof(double) * 2, s);
-  sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
-  LTensor Cbar = project_all(st, dY, dtype, N, s);
-  sqnorm_of(Cbar.ptr, BHT_F64, Cbar.numel(), acc.as<double>() + 1, s);
+  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 2, s), "memset");
+  bool norm_done = false;
+  LTensor Cbar = project_all(st, dY, dtype, N, ar, s, acc.as<double>(), &norm_done);
+  if (!norm_done) sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
+  sqnorm_of(Cbar.ptr, Cbar.dtype, Cbar.numel(), acc.as<double>() + 1, s);
   double h[2];
   ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H norms");
   ck(cudaStreamSynchronize(s), "sync");
   if (!std::isfinite(h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
+  check_status(st, s);
   const double eps_des = eps_rel * std::sqrt(h[0]);
   const double eps_proj = std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold
   const int64_t r11_old = st->r11(), r12_old = st->r12();
   if (eps_proj <= eps_des) {
     grow_root(st, r11_old, r12_old, r11_old, r12_old, st->n_items + N, s);
-    ck(cudaMemcpyAsync(st->root + st->n_items * r11_old * r12_old, Cbar.ptr, sizeof(double) * Cbar.numel(),
-                       cudaMemcpyDeviceToDevice, s),
-       "root append");
+    copy_convert(Cbar, st->root + st->n_items * r11_old * r12_old, BHT_F64, s);
     st->n_items += N;
     ck(cudaStreamSynchronize(s), "sync");
     if (info) *info = bht_update_info{1, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items};
@@ -719,7 +852,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         rold[k] = rank[ids[k]];
         // residual Gram R R^T = Pi G Pi with Pi = I - U U^T (eq. compute_residual)
         DBuf G(sizeof(double) * a * a, s), Pi(sizeof(double) * a * a, s), H(sizeof(double) * a * a, s);
-        gram64(C, ax, G.as<double>(), s);
+        gram_any(C, ax, G.as<double>(), ar, s);
         ck(launch_fill_identity(Pi.as<double>(), a, s), "identity");
         ck(launch_gemm_f64(a, a, rold[k], -1.0, U[ids[k]], rold[k], 1, U[ids[k]], 1, rold[k], 1.0, Pi.as<double>(),
                            a, 1, s),
@@ -728,7 +861,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
            "Pi G");
         ck(launch_gemm_f64(a, a, a, 1.0, H.as<double>(), a, 1, Pi.as<double>(), a, 1, 0.0, G.as<double>(), a, 1, s),
            "Pi G Pi");
-        eig64(G.as<double>(), a, eo[k], st->d_status, s);
+        eig_values64(G.as<double>(), a, eo[k], st->d_status, s);
       }
       for (auto& e : eo) {
         e.h_lam.resize(e.n);
@@ -742,8 +875,10 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
         const int64_t rR = tail_rank(eo[k].h_lam, eps_nw2, 0, std::max<int64_t>(a - r0, 0));
         if (rR == 0) continue;
-        DBuf UR(sizeof(double) * a * rR, s), W(sizeof(double) * r0 * rR + 8, s);
-        ck(launch_copy_cols(eo[k].V.as<double>(), a, a, rR, UR.as<double>(), rR, s), "U_R");
+        DBuf UR;
+        UR.p = eig_vectors64(eo[k], rR, s);
+        UR.s = s;
+        DBuf W(sizeof(double) * r0 * rR + 8, s);
         // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)
         for (int pass = 0; pass < 2 && r0 > 0; ++pass) {
           ck(launch_gemm_f64(r0, rR, a, 1.0, U[id], 1, r0, UR.as<double>(), rR, 1, 0.0, W.as<double>(), rR, 1, s),
@@ -751,27 +886,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
           ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, s),
              "U_R -= U W");
         }
-        // symmetric orthonormalisation U_R <- U_R S^{-1/2}, S = U_R^T U_R
-        {
-          DBuf S(sizeof(double) * rR * rR, s), Wm(sizeof(double) * rR * rR, s), T(sizeof(double) * a * rR, s);
-          ck(launch_gemm_f64(rR, rR, a, 1.0, UR.as<double>(), 1, rR, UR.as<double>(), rR, 1, 0.0, S.as<double>(), rR,
-                             1, s),
-             "S");
-          EigOut se;
-          eig64(S.as<double>(), rR, se, st->d_status, s);
-          // Wm = V diag(mu^-1/2) V^T
-          DBuf Vs(sizeof(double) * rR * rR, s);
-          ck(cudaMemcpyAsync(Vs.p, se.V.p, sizeof(double) * rR * rR, cudaMemcpyDeviceToDevice, s), "copy");
-          ck(launch_scale_cols_invsqrt(Vs.as<double>(), rR, se.lam.as<double>(), s), "scale");
-          ck(launch_gemm_f64(rR, rR, rR, 1.0, Vs.as<double>(), rR, 1, se.V.as<double>(), 1, rR, 0.0, Wm.as<double>(),
-                             rR, 1, s),
-             "S^-1/2");
-          ck(launch_gemm_f64(a, rR, rR, 1.0, UR.as<double>(), rR, 1, Wm.as<double>(), rR, 1, 0.0, T.as<double>(), rR,
-                             1, s),
-             "U_R S^-1/2");
-          ck(cudaMemcpyAsync(UR.p, T.p, sizeof(double) * a * rR, cudaMemcpyDeviceToDevice, s), "copy");
-          check_status(st, s);
-        }
+        newton_schulz(UR.as<double>(), a, rR, s);
         // expandCore: U^k = [U^{k-1}, U_R] (eq. concatenating_orthonormal_vectors)
         const int64_t rn = r0 + rR;
         double* Un = own(static_cast<double*>(dalloc(sizeof(double) * a * rn, s)));
@@ -805,14 +920,12 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         Us.push_back(U[id]);
         rs.push_back(rank[id]);
       }
-      C = project_layer(std::move(C), ids, Us, rs, s);
+      C = project_layer(std::move(C), ids, Us, rs, ar, s);
     }
     // eq. incremental_root_concatenate with the root zero-padded in modes 1, 2
     const int64_t r11 = rank[t.nodes[0].child[0]], r12 = rank[t.nodes[0].child[1]];
     grow_root(st, r11_old, r12_old, r11, r12, st->n_items + N, s);
-    ck(cudaMemcpyAsync(st->root + st->n_items * r11 * r12, C.ptr, sizeof(double) * C.numel(),
-                       cudaMemcpyDeviceToDevice, s),
-       "root append");
+    copy_convert(C, st->root + st->n_items * r11 * r12, BHT_F64, s);
     ck(cudaStreamSynchronize(s), "sync");
   } catch (...) {
     for (double* p : fresh) dfree(p, s);
@@ -841,6 +954,7 @@ bht_status ht_reconstruct(const bht_state* st, int64_t first, int64_t count, voi
   if (count == 0) return BHT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bht_tree& t = st->tree;
+  const Arith ar = make_arith(st->precision, 1.0, st->d_status);
   LTensor C;
   C.dtype = BHT_F64;
   C.N = count;
@@ -859,7 +973,7 @@ bht_status ht_reconstruct(const bht_state* st, int64_t first, int64_t count, voi
       const int id = ids[k];
       const int ax = C.axis_of(id);
       const int64_t r = st->rank[id], a = st->rows(id);
-      LTensor nxt = ttm64(C, ax, st->U[id], r, 1, a, s);
+      LTensor nxt = ttm_any(C, ax, st->U[id], r, 1, a, false, ar, s);
       C = std::move(nxt);
     }
     // split transfer axes into their successors' axes (C-order)
@@ -881,19 +995,12 @@ bht_status ht_reconstruct(const bht_state* st, int64_t first, int64_t count, voi
     C.node = node;
   }
   const int64_t n = C.numel();
-  const bool dev = is_device_ptr(out);
-  if (dtype == BHT_F64) {
-    ck(cudaMemcpyAsync(out, C.ptr, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
-       "copy out");
+  if (is_device_ptr(out)) {
+    copy_convert(C, out, dtype, s);
   } else {
-    DBuf tmp;
-    float* dst = static_cast<float*>(out);
-    if (!dev) {
-      tmp = DBuf(sizeof(float) * n, s);
-      dst = tmp.as<float>();
-    }
-    ck(launch_cast<double, float>(static_cast<const double*>(C.ptr), dst, n, s), "cast");
-    if (!dev) ck(cudaMemcpyAsync(out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "D2H");
+    DBuf tmp(dtype_size(dtype) * n, s);
+    copy_convert(C, tmp.p, dtype, s);
+    ck(cudaMemcpyAsync(out, tmp.p, dtype_size(dtype) * n, cudaMemcpyDeviceToHost, s), "D2H");
     ck(cudaStreamSynchronize(s), "sync");
   }
   ck(cudaStreamSynchronize(s), "sync");
@@ -910,12 +1017,73 @@ bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t 
   for (auto v : st->tree.dims) item *= v;
   DBuf staging;
   const void* dY = stage_input(Y, dtype, N * item, staging, s);
-  LTensor C = project_all(st, dY, dtype, N, s);
-  const bool dev = is_device_ptr(out);
-  ck(cudaMemcpyAsync(out, C.ptr, sizeof(double) * C.numel(), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                     s),
-     "copy out");
+  const Arith ar = make_arith(st->precision, st->precision == BHT_PREC_MIXED ? 1.0 : 1.0, st->d_status);
+  LTensor C = project_all(st, dY, dtype, N, ar, s);
+  if (is_device_ptr(out)) {
+    copy_convert(C, out, BHT_F64, s);
+  } else {
+    DBuf tmp(sizeof(double) * C.numel(), s);
+    copy_convert(C, tmp.p, BHT_F64, s);
+    ck(cudaMemcpyAsync(out, tmp.p, sizeof(double) * C.numel(), cudaMemcpyDeviceToHost, s), "copy out");
+  }
   ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S, int32_t precision,
+                            float* out, int64_t R2, double* norms, void* stream) {
+  BHT_API_BEGIN
+  if (!X || !U || !out) fail(BHT_EINVAL, "null argument");
+  if (rows < 1 || K < 1 || S < 1 || R2 < 1 || rows % R2 != 0) fail(BHT_EINVAL, "bad sizes (rows must be a multiple of R2)");
+  if (!is_device_ptr(X) || !is_device_ptr(U) || !is_device_ptr(out) || (norms && !is_device_ptr(norms)))
+    fail(BHT_EINVAL, "bht_mode_product takes device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  if (precision == BHT_PREC_MIXED) {
+    if (!ttm_tc_supported(K, S, 2)) fail(BHT_EUNSUPPORTED, "shape outside the tensor-core kernel (K % 4 == 0)");
+    DBuf W(ttm_tc_weights_bytes(K, S), s);
+    ck(launch_prep_tc_weights(U, K, S, S, true, W.as<float>(), 2, s), "weights");
+    ck(launch_ttm_tc(X, rows, K, W.as<float>(), S, 2, out, R2, norms, norms ? norms + 1 : nullptr,
+                     status.as<int>(), s),
+       "tensor-core mode product");
+  } else if (precision == BHT_PREC_FP64) {
+    // out[(o S + s) R2 + i]: as a TTM over the view [rows / R2][R2][K] it is a transpose; do it per layout
+    if (R2 != 1) fail(BHT_EUNSUPPORTED, "the FP64 form writes the new axis innermost (R2 = 1)");
+    ck(launch_ttm_f64<float, float>(X, out, U, 1, S, rows, K, 1, S, s), "mode product");
+  } else {
+    fail(BHT_EINVAL, "precision must be BHT_PREC_FP64 or BHT_PREC_MIXED");
+  }
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (h) fail((bht_status)h, "a bounded device-side wait gave up (tensor-core pipeline)");
+  BHT_API_END
+}
+
+bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, void* stream) {
+  BHT_API_BEGIN
+  if (!G || !lam || (r > 0 && !U)) fail(BHT_EINVAL, "null argument");
+  if (n < 1 || r < 0 || r > n) fail(BHT_EINVAL, "need 1 <= n and 0 <= r <= n");
+  if (n > 4096) fail(BHT_ECAPACITY, "n > 4096");
+  if (!is_device_ptr(G) || !is_device_ptr(lam) || (r > 0 && !is_device_ptr(U)))
+    fail(BHT_EINVAL, "bht_sym_eig takes device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  EigOut eo;
+  eig_values64(G, n, eo, status.as<int>(), s);
+  ck(cudaMemcpyAsync(lam, eo.lam.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s), "copy");
+  if (r > 0) {
+    DBuf Ur;
+    Ur.p = eig_vectors64(eo, r, s);
+    Ur.s = s;
+    ck(cudaMemcpyAsync(U, Ur.p, sizeof(double) * n * r, cudaMemcpyDeviceToDevice, s), "copy");
+  }
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (h) fail((bht_status)h, "a bounded device-side wait gave up (eigensolver)");
   BHT_API_END
 }
 

@@ -21,20 +21,18 @@ constexpr int TILE = 64;   // output tile edge
 constexpr int BK = 16;     // depth of one shared-memory stage
 constexpr int NT = 256;    // threads per CTA (16 x 16, each 4 x 4 outputs)
 
-template <typename T>
-__device__ __forceinline__ double ld_as_double(const T* p) { return static_cast<double>(*p); }
 
 // ---------------------------------------------------------------------------
 // Gram of the middle index of X[A][I][B]
 // grid.x: upper-triangular tile pairs (ti <= tj), grid.y: chunks of the
 // flattened column index k = a * B + b.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, double* __restrict__ G,
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(NT) gram_simt_kernel(const T* __restrict__ X, double* __restrict__ G,
                                                       int64_t A, int64_t I, int64_t B,
                                                       int64_t kchunk, int ntiles) {
-  __shared__ double Xi[BK][TILE + 1];
-  __shared__ double Xj[BK][TILE + 1];
+  __shared__ Acc Xi[BK][TILE + 1];
+  __shared__ Acc Xj[BK][TILE + 1];
   // decode the tile pair (ti, tj), ti <= tj, from blockIdx.x
   int pid = blockIdx.x, ti = 0;
   while (pid >= ntiles - ti) { pid -= ntiles - ti; ++ti; }
@@ -45,6 +43,7 @@ __global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, d
   const int64_t kend = min(K, kbeg + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool along_k = B >= 8;
+  // per-stage partial sums in Acc, folded into FP64 after every stage of BK columns
   double acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -57,21 +56,26 @@ __global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, d
       int kk, ii;
       if (along_k) { kk = e % BK; ii = e / BK; } else { ii = e % TILE; kk = e / TILE; }
       const int64_t k = k0 + kk;
-      double vi = 0.0, vj = 0.0;
+      Acc vi = Acc(0), vj = Acc(0);
       if (k < kend) {
         const int64_t a = k / B, b = k - a * B;
         const int64_t base = a * I * B + b;
-        if (i0 + ii < I) vi = ld_as_double(X + base + (i0 + ii) * B);
-        if (ti != tj && j0 + ii < I) vj = ld_as_double(X + base + (j0 + ii) * B);
+        if (i0 + ii < I) vi = static_cast<Acc>(X[base + (i0 + ii) * B]);
+        if (ti != tj && j0 + ii < I) vj = static_cast<Acc>(X[base + (j0 + ii) * B]);
       }
       Xi[kk][ii] = vi;
       if (ti != tj) Xj[kk][ii] = vj;
     }
     __syncthreads();
-    const double (*Bj)[TILE + 1] = (ti == tj) ? Xi : Xj;
+    const Acc (*Bj)[TILE + 1] = (ti == tj) ? Xi : Xj;
+    Acc part[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) part[u][v] = Acc(0);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      Acc a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = Xi[kk][ty + 16 * u];
 #pragma unroll
@@ -79,8 +83,12 @@ __global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, d
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) part[u][v] = fma(a[u], b[v], part[u][v]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += static_cast<double>(part[u][v]);
     __syncthreads();
   }
 #pragma unroll
@@ -105,46 +113,46 @@ __global__ void __launch_bounds__(NT) gram_f64_kernel(const T* __restrict__ X, d
 // TTM: out[a][s][b] = sum_t M(s,t) X[a][t][b]
 // grid.x: tiles of the flattened column c = a * B + b, grid.y: tiles of s.
 // ---------------------------------------------------------------------------
-template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(NT) ttm_f64_kernel(const Tin* __restrict__ X, Tout* __restrict__ out,
-                                                     const double* __restrict__ M, int64_t ms, int64_t mt,
-                                                     int64_t A, int64_t T, int64_t B, int64_t S) {
-  __shared__ double Ms[BK][TILE + 1];
-  __shared__ double Xs[BK][TILE + 1];
+template <typename Tin, typename Tout, typename Acc>
+__global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X, Tout* __restrict__ out,
+                                                      const double* __restrict__ M, int64_t ms, int64_t mt,
+                                                      int64_t A, int64_t T, int64_t B, int64_t S, int64_t R2) {
+  __shared__ Acc Ms[BK][TILE + 1];
+  __shared__ Acc Xs[BK][TILE + 1];
   const int64_t c0 = (int64_t)blockIdx.x * TILE;
   const int64_t s0 = (int64_t)blockIdx.y * TILE;
   const int64_t AB = A * B;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool m_along_s = (ms == 1);
   const bool x_along_c = B >= 8;
-  double acc[4][4];
+  Acc acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < 4; ++v) acc[u][v] = Acc(0);
 
   for (int64_t t0 = 0; t0 < T; t0 += BK) {
     for (int e = threadIdx.x; e < BK * TILE; e += NT) {
       int kk, ss;
       if (m_along_s) { ss = e % TILE; kk = e / TILE; } else { kk = e % BK; ss = e / BK; }
       const int64_t t = t0 + kk, sidx = s0 + ss;
-      Ms[kk][ss] = (t < T && sidx < S) ? M[sidx * ms + t * mt] : 0.0;
+      Ms[kk][ss] = (t < T && sidx < S) ? static_cast<Acc>(M[sidx * ms + t * mt]) : Acc(0);
     }
     for (int e = threadIdx.x; e < BK * TILE; e += NT) {
       int kk, cc;
       if (x_along_c) { cc = e % TILE; kk = e / TILE; } else { kk = e % BK; cc = e / BK; }
       const int64_t t = t0 + kk, c = c0 + cc;
-      double v = 0.0;
+      Acc v = Acc(0);
       if (t < T && c < AB) {
         const int64_t a = c / B, b = c - a * B;
-        v = ld_as_double(X + (a * T + t) * B + b);
+        v = static_cast<Acc>(X[(a * T + t) * B + b]);
       }
       Xs[kk][cc] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      Acc a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = Ms[kk][ty + 16 * u];
 #pragma unroll
@@ -161,10 +169,15 @@ __global__ void __launch_bounds__(NT) ttm_f64_kernel(const Tin* __restrict__ X, 
     const int64_t c = c0 + tx + 16 * v;
     if (c >= AB) continue;
     const int64_t a = c / B, b = c - a * B;
+    // B > 1: out[a][s][b]; B == 1: the new axis goes in front of the last R2 rows
+    const int64_t o = a / R2, i = a - o * R2;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t sidx = s0 + ty + 16 * u;
-      if (sidx < S) out[(a * S + sidx) * B + b] = static_cast<Tout>(acc[u][v]);
+      if (sidx < S) {
+        const int64_t off = (B > 1) ? (a * S + sidx) * B + b : (o * S + sidx) * R2 + i;
+        out[off] = static_cast<Tout>(acc[u][v]);
+      }
     }
   }
 }
@@ -314,6 +327,11 @@ __global__ void fill_identity_kernel(double* __restrict__ A, int64_t n) {
     A[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
+__global__ void add_diag_kernel(double* __restrict__ A, int64_t n, double alpha) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    A[i * n + i] += alpha;
+}
+
 template <typename T>
 __global__ void check_finite_kernel(const T* __restrict__ x, int64_t n, int* __restrict__ flag) {
   bool bad = false;
@@ -334,24 +352,55 @@ int grid_for(int64_t n, int threads = 256, int cap = 152 * 16) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
-  if (A <= 0 || I <= 0 || B <= 0) return cudaSuccess;
-  const int ntiles = (int)((I + TILE - 1) / TILE);
-  const int pairs = ntiles * (ntiles + 1) / 2;
-  const int64_t K = A * B;
-  // enough CTAs to fill the GPU several times, each with at least 256 columns
+namespace {
+int64_t gram_kchunk(int64_t K, int pairs, int64_t& chunks) {
   int64_t want = (4 * 152 + pairs - 1) / pairs;
-  int64_t chunks = (K + 255) / 256;
+  chunks = (K + 255) / 256;
   if (chunks > want) chunks = want;
   if (chunks < 1) chunks = 1;
   int64_t kchunk = (K + chunks - 1) / chunks;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   chunks = (K + kchunk - 1) / kchunk;
+  return kchunk;
+}
+}  // namespace
+
+template <typename T, typename Acc>
+cudaError_t launch_gram(const T* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
+  if (A <= 0 || I <= 0 || B <= 0) return cudaSuccess;
+  const int ntiles = (int)((I + TILE - 1) / TILE);
+  const int pairs = ntiles * (ntiles + 1) / 2;
+  const int64_t K = A * B;
+  int64_t chunks = 1;
+  const int64_t kchunk = gram_kchunk(K, pairs, chunks);
   dim3 grid(pairs, (unsigned)chunks);
-  ProfScope prof(K_GRAM_F64, s, (double)I * (double)(I + 1) * (double)K,
+  ProfScope prof(sizeof(Acc) == 8 ? K_GRAM_F64 : K_GRAM_F32, s, (double)I * (double)(I + 1) * (double)K,
                  (double)sizeof(T) * (double)K * (double)I + 8.0 * (double)I * (double)I);
-  gram_f64_kernel<T><<<grid, NT, 0, s>>>(X, G, A, I, B, kchunk, ntiles);
+  gram_simt_kernel<T, Acc><<<grid, NT, 0, s>>>(X, G, A, I, B, kchunk, ntiles);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
+  return launch_gram<T, double>(X, G, A, I, B, s);
+}
+
+cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
+  return launch_gram<float, float>(X, G, A, I, B, s);
+}
+
+template <typename Tin, typename Tout, typename Acc>
+cudaError_t launch_ttm(const Tin* X, Tout* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+                       int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
+  if (A <= 0 || B <= 0 || S <= 0) return cudaSuccess;
+  if (R2 < 1 || (B == 1 && A % R2 != 0) || (B > 1 && R2 != 1)) return cudaErrorInvalidValue;
+  const int64_t AB = A * B;
+  dim3 grid((unsigned)((AB + TILE - 1) / TILE), (unsigned)((S + TILE - 1) / TILE));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  ProfScope prof(sizeof(Acc) == 8 ? K_TTM_F64 : K_TTM_F32, s, 2.0 * (double)S * (double)T * (double)AB,
+                 (double)sizeof(Tin) * (double)AB * (double)T + (double)sizeof(Tout) * (double)AB * (double)S);
+  ttm_simt_kernel<Tin, Tout, Acc><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S, R2);
   note_launch();
   return cudaGetLastError();
 }
@@ -359,15 +408,13 @@ cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t
 template <typename Tin, typename Tout>
 cudaError_t launch_ttm_f64(const Tin* X, Tout* out, const double* M, int64_t ms, int64_t mt, int64_t A,
                            int64_t T, int64_t B, int64_t S, cudaStream_t s) {
-  if (A <= 0 || B <= 0 || S <= 0) return cudaSuccess;
-  const int64_t AB = A * B;
-  dim3 grid((unsigned)((AB + TILE - 1) / TILE), (unsigned)((S + TILE - 1) / TILE));
-  if (grid.y > 65535) return cudaErrorInvalidValue;
-  ProfScope prof(K_TTM_F64, s, 2.0 * (double)S * (double)T * (double)AB,
-                 (double)sizeof(Tin) * (double)AB * (double)T + (double)sizeof(Tout) * (double)AB * (double)S);
-  ttm_f64_kernel<Tin, Tout><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S);
-  note_launch();
-  return cudaGetLastError();
+  return launch_ttm<Tin, Tout, double>(X, out, M, ms, mt, A, T, B, S, 1, s);
+}
+
+template <typename Tin>
+cudaError_t launch_ttm_f32(const Tin* X, float* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+                           int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
+  return launch_ttm<Tin, float, float>(X, out, M, ms, mt, A, T, B, S, R2, s);
 }
 
 template <typename T>
@@ -443,6 +490,14 @@ cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
+  add_diag_kernel<<<grid_for(n), 256, 0, s>>>(A, n, alpha);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -459,6 +514,8 @@ template cudaError_t launch_ttm_f64<float, double>(const float*, double*, const 
                                                    int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_ttm_f64<double, double>(const double*, double*, const double*, int64_t, int64_t,
                                                     int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f64<float, float>(const float*, float*, const double*, int64_t, int64_t, int64_t,
+                                                  int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_ttm_f64<double, float>(const double*, float*, const double*, int64_t, int64_t,
                                                    int64_t, int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_sqnorm<float>(const float*, int64_t, double*, cudaStream_t);
@@ -471,6 +528,10 @@ template cudaError_t launch_copy_pad3<double, float>(const double*, int64_t, int
                                                      int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_cast<float, double>(const float*, double*, int64_t, cudaStream_t);
 template cudaError_t launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f32<float>(const float*, float*, const double*, int64_t, int64_t, int64_t, int64_t,
+                                           int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f32<double>(const double*, float*, const double*, int64_t, int64_t, int64_t, int64_t,
+                                            int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_check_finite<double>(const double*, int64_t, int*, cudaStream_t);
 

@@ -1,18 +1,23 @@
-// eig.cu — FP64 symmetric eigensolvers for the node truncations.
+// eig.cu — FP64 symmetric eigensolver for the node truncations.
 //
 // The error-truncated SVD of a node unfolding (eq. ht_leaf_svd, eq.
-// svd_on_residual) keeps the left singular vectors; they are the
-// eigenvectors of the unfolding's Gram matrix, with eigenvalues sigma_i^2.
-// Both solvers below run the cyclic Jacobi method with the round-robin
-// (circle) ordering: every round rotates n/2 disjoint index pairs at once, and
-// one round is written as independent 2 x 2 block updates
-//     A[P_i, P_j] <- J_i^T A[P_i, P_j] J_j ,   P_i = {p_i, q_i},
-// so a round needs one barrier, not two.
-//   * eig_small: one CTA per matrix, A in shared memory (n <= 128).
-//   * eig_coop : one cooperative grid, A in global memory (L2-resident), a
-//                bounded grid barrier per round; every CTA recomputes the
-//                round's rotations itself, so no rotation data is exchanged.
-#include <cooperative_groups.h>
+// svd_on_residual) keeps the left singular vectors: they are the eigenvectors
+// of the unfolding's Gram matrix, with eigenvalues sigma_i^2. The truncation
+// rank only needs all eigenvalues, and the node only needs the eigenvectors it
+// keeps, so the solver runs in two stages:
+//   stage 1  Householder tridiagonalisation Q^T G Q = T, then every eigenvalue
+//            of T by Sturm-sequence bisection (one thread per eigenvalue);
+//   stage 2  (after the caller picked r) the eigenvectors of T for the r
+//            largest eigenvalues by twisted factorisation (one thread per
+//            cluster of nearly equal eigenvalues, modified Gram-Schmidt
+//            inside a cluster), then the back-transformation U = Q Z.
+// GB300 has few FP64 units (about 2 FMA per clock per SM), so every stage is
+// spread over the whole GPU: the tridiagonalisation of a large matrix is one
+// cooperative grid with a bounded grid barrier between its phases; small
+// matrices (n <= 96) use one CTA each.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
 
 #include "internal.cuh"
 
@@ -20,167 +25,9 @@ namespace bht {
 
 namespace {
 
-constexpr int SMALL_MAX = 128;
 constexpr int EIG_THREADS = 256;
-constexpr int MAX_SWEEPS = 40;
-constexpr double EPS_REL = 2.220446049250313e-16;
+constexpr int SMALL_N = 96;
 
-struct Rot {
-  double c, s;
-};
-
-// Pair k of round r among m = n2 - 1 rotating players (n2 even).
-__device__ __forceinline__ void round_pair(int r, int k, int m, int& p, int& q) {
-  if (k == 0) {
-    p = r;
-    q = m;
-  } else {
-    p = (r + k) % m;
-    q = (r - k + m) % m;
-  }
-}
-
-// Symmetric Schur 2x2: (c, s) zeroing a_pq of [[a_pp, a_pq], [a_pq, a_qq]].
-__device__ __forceinline__ Rot schur2(double app, double aqq, double apq, double abs_tol, bool& rotated) {
-  Rot r{1.0, 0.0};
-  rotated = false;
-  const double aa = fabs(apq);
-  if (aa <= abs_tol || aa <= EPS_REL * sqrt(fabs(app) * fabs(aqq))) return r;
-  const double tau = (aqq - app) / (2.0 * apq);
-  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  r.c = 1.0 / sqrt(1.0 + t * t);
-  r.s = t * r.c;
-  rotated = true;
-  return r;
-}
-
-// 2x2 block update of A at rows (pi, qi), cols (pj, qj); `n` real size, indices
-// >= n are the dummy player (zero row / column).
-template <bool Symmetric>
-__device__ __forceinline__ void block_update(double* A, int64_t lda, int n, int pi, int qi, Rot ri, int pj, int qj,
-                                             Rot rj, bool diag) {
-  const bool vi = qi < n, vj = qj < n;
-  double m00 = A[(int64_t)pi * lda + pj];
-  double m01 = vj ? A[(int64_t)pi * lda + qj] : 0.0;
-  double m10 = vi ? A[(int64_t)qi * lda + pj] : 0.0;
-  double m11 = (vi && vj) ? A[(int64_t)qi * lda + qj] : 0.0;
-  // rows: J_i^T M
-  const double r00 = ri.c * m00 - ri.s * m10, r01 = ri.c * m01 - ri.s * m11;
-  const double r10 = ri.s * m00 + ri.c * m10, r11 = ri.s * m01 + ri.c * m11;
-  // cols: (.) J_j
-  double n00 = rj.c * r00 - rj.s * r01, n01 = rj.s * r00 + rj.c * r01;
-  double n10 = rj.c * r10 - rj.s * r11, n11 = rj.s * r10 + rj.c * r11;
-  if (diag) {  // the rotated pair itself: off-diagonal is zero by construction
-    n01 = 0.0;
-    n10 = 0.0;
-  }
-  A[(int64_t)pi * lda + pj] = n00;
-  if (vj) A[(int64_t)pi * lda + qj] = n01;
-  if (vi) A[(int64_t)qi * lda + pj] = n10;
-  if (vi && vj) A[(int64_t)qi * lda + qj] = n11;
-  if (Symmetric && !diag) {  // mirror into the lower half
-    A[(int64_t)pj * lda + pi] = n00;
-    if (vj) A[(int64_t)qj * lda + pi] = n01;
-    if (vi) A[(int64_t)pj * lda + qi] = n10;
-    if (vi && vj) A[(int64_t)qj * lda + qi] = n11;
-  }
-}
-
-__device__ __forceinline__ void vt_update(double* VT, int n, int p, int q, Rot r, int k) {
-  if (q >= n) return;
-  const double a = VT[(int64_t)p * n + k], b = VT[(int64_t)q * n + k];
-  VT[(int64_t)p * n + k] = r.c * a - r.s * b;
-  VT[(int64_t)q * n + k] = r.s * a + r.c * b;
-}
-
-// ---------------------------------------------------------------------------
-// small: one CTA per matrix, A in shared memory
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(EIG_THREADS) eig_small_kernel(const double* __restrict__ G, int n,
-                                                                double* __restrict__ lam, double* __restrict__ V,
-                                                                double* __restrict__ VT) {
-  extern __shared__ double smem[];
-  const int n2 = n + (n & 1);
-  const int m = n2 - 1;
-  const int np = n2 / 2;
-  double* A = smem;                          // n x n, lda = n
-  Rot* rot = reinterpret_cast<Rot*>(A + (int64_t)n * n);  // np
-  int* rank = reinterpret_cast<int*>(rot + np);           // n
-  __shared__ int any_rot;
-  __shared__ double normA;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    A[e] = G[e];
-    const int i = e / n, k = e - i * n;
-    VT[e] = (i == k) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int e = 0; e < n * n; ++e) s += A[e] * A[e];
-    normA = sqrt(s);
-  }
-  __syncthreads();
-  const double abs_tol = 1e-17 * normA;
-  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-    if (threadIdx.x == 0) any_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < m; ++r) {
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int p, q;
-        round_pair(r, k, m, p, q);
-        bool did = false;
-        Rot rr{1.0, 0.0};
-        if (q < n) rr = schur2(A[p * n + p], A[q * n + q], A[p * n + q], abs_tol, did);
-        rot[k] = rr;
-        if (did) any_rot = 1;
-      }
-      __syncthreads();
-      const int nblk = np * (np + 1) / 2;
-      for (int w = threadIdx.x; w < nblk; w += blockDim.x) {
-        int i = 0, rem = w;
-        while (rem >= np - i) { rem -= np - i; ++i; }
-        const int j = i + rem;
-        int pi, qi, pj, qj;
-        round_pair(r, i, m, pi, qi);
-        round_pair(r, j, m, pj, qj);
-        if (pi >= n) { int t = pi; pi = qi; qi = t; }
-        if (pj >= n) { int t = pj; pj = qj; qj = t; }
-        Rot ri = rot[i], rj = rot[j];
-        block_update<true>(A, n, n, pi, qi, ri, pj, qj, rj, i == j);
-      }
-      for (int w = threadIdx.x; w < np * n; w += blockDim.x) {
-        const int k = w / n, col = w - k * n;
-        int p, q;
-        round_pair(r, k, m, p, q);
-        if (p >= n) continue;
-        vt_update(VT, n, p, q, rot[k], col);
-      }
-      __syncthreads();
-    }
-    if (!any_rot) break;
-    __syncthreads();
-  }
-  // sort eigenvalues descending (ties by index) and scatter eigenvectors
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double li = A[i * n + i];
-    int rk = 0;
-    for (int j = 0; j < n; ++j) {
-      const double lj = A[j * n + j];
-      rk += (lj > li) || (lj == li && j < i);
-    }
-    rank[i] = rk;
-    lam[rk] = li;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, k = e - i * n;  // eigenvector i, component k
-    V[(int64_t)k * n + rank[i]] = VT[e];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// cooperative: A in global memory, bounded grid barrier
-// ---------------------------------------------------------------------------
 struct Barrier {
   unsigned int count;
   unsigned int gen;
@@ -192,10 +39,12 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Returns false when the wait gave up (status set to BHT_ETIMEOUT = 6).
+// Grid-wide barrier with a 1 s limit; returns false when the wait gave up
+// (the status word is then BHT_ETIMEOUT = 6). With one CTA it is __syncthreads.
 __device__ bool grid_barrier(Barrier* bar, int* status) {
   __shared__ int ok;
   __syncthreads();
+  if (gridDim.x == 1) return true;
   if (threadIdx.x == 0) {
     ok = 1;
     volatile unsigned int* vgen = &bar->gen;
@@ -209,13 +58,16 @@ __device__ bool grid_barrier(Barrier* bar, int* status) {
     } else {
       const uint64_t t0 = global_ns();
       while (*vgen == g) {
-        if (*(volatile int*)status != 0) { ok = 0; break; }
-        if (global_ns() - t0 > 1000000000ull) {  // 1 s
+        if (*(volatile int*)status != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > 1000000000ull) {
           atomicExch(status, 6);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -224,218 +76,368 @@ __device__ bool grid_barrier(Barrier* bar, int* status) {
   return ok != 0;
 }
 
-// Partner of index x in round r (m rotating players, dummy/fixed player m).
-__device__ __forceinline__ int round_partner(int x, int r, int m) {
-  if (x == m) return r;
-  if (x == r) return m;
-  int y = (2 * r - x) % m;
-  return y < 0 ? y + m : y;
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// Slot (0 .. np-1) of the pair containing index x in round r.
-__device__ __forceinline__ int round_slot(int x, int r, int m) {
-  if (x == m || x == r) return 0;
-  int k = (x - r) % m;
-  if (k < 0) k += m;
-  return k < m - k ? k : m - k;
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    t = warp_sum(t);
+    if (l == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) eig_coop_kernel(double* __restrict__ A, int n,
-                                                               double* __restrict__ lam, double* __restrict__ V,
-                                                               double* __restrict__ VT, Barrier* bar,
-                                                               int* status, double normA,
-                                                               double* __restrict__ diagv,   // [2][n2]
-                                                               double* __restrict__ offv) {  // [2][np]
-  extern __shared__ double smem[];
-  const int n2 = n + (n & 1);
-  const int m = n2 - 1;
-  const int np = n2 / 2;
-  Rot* rot = reinterpret_cast<Rot*>(smem);        // np
-  __shared__ int any_rot;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = gtid; e < (int64_t)n * n; e += gsz) {
-    const int64_t i = e / n, k = e - i * n;
-    VT[e] = (i == k) ? 1.0 : 0.0;
-  }
-  // snapshots read by the rotation computation of the first round
-  for (int64_t x = gtid; x < n2; x += gsz) diagv[x] = (x < n) ? A[x * n + x] : 0.0;
-  for (int64_t k = gtid; k < np; k += gsz) {
-    int p, q;
-    round_pair(0, (int)k, m, p, q);
-    offv[k] = (p < n && q < n) ? A[(int64_t)p * n + q] : 0.0;
-  }
-  if (!grid_barrier(bar, status)) return;
-  const double abs_tol = 1e-17 * normA;
-  const int64_t nblk = (int64_t)np * (np + 1) / 2;
-  int64_t gr = 0;  // rounds executed so far: selects the snapshot buffer
-  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-    if (threadIdx.x == 0) any_rot = 0;
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation of the symmetric matrix A (n x n, both
+// triangles kept up to date). Step k maps column k below the diagonal onto
+// beta e_1 with H_k = I - tau_k v_k v_k^T, v_k[0] = 1 (stored in Vh row k):
+//   p = tau A22 v,  w = p - (tau/2)(p.v) v,  A22 -= v w^T + w v^T.
+// Every CTA recomputes v (and w) from the same data, so only p is exchanged.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict__ A, int n,
+                                                              double* __restrict__ Vh, double* __restrict__ d,
+                                                              double* __restrict__ e, double* __restrict__ tau,
+                                                              double* __restrict__ pbuf, Barrier* bar,
+                                                              int* status) {
+  extern __shared__ double sm[];
+  double* v = sm;       // n
+  double* w = sm + n;   // n
+  __shared__ double red[33];
+  __shared__ double sc[3];
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const double* rowk = A + (int64_t)k * n + k + 1;  // = column k below the diagonal
+    double s = 0.0;
+    for (int j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(rowk[j], rowk[j], s);
+    const double xn2 = block_sum(s, red);
+    if (threadIdx.x == 0) {
+      const double alpha = rowk[0];
+      double t = 0.0, beta = alpha, scale = 0.0;
+      if (xn2 > 0.0) {
+        beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      sc[0] = t;
+      sc[1] = beta;
+      sc[2] = scale;
+    }
     __syncthreads();
-    for (int r = 0; r < m; ++r, ++gr) {
-      const double* dcur = diagv + (gr & 1) * n2;
-      const double* ocur = offv + (gr & 1) * np;
-      double* dnext = diagv + ((gr + 1) & 1) * n2;
-      double* onext = offv + ((gr + 1) & 1) * np;
-      const int rn = (r + 1 == m) ? 0 : r + 1;  // next round (wraps into the next sweep)
-      // every CTA derives the same rotations from the same snapshot values
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int p, q;
-        round_pair(r, k, m, p, q);
-        bool did = false;
-        Rot rr{1.0, 0.0};
-        if (q < n && p < n) rr = schur2(dcur[p], dcur[q], ocur[k], abs_tol, did);
-        rot[k] = rr;
-        if (did) any_rot = 1;
+    const double tk = sc[0], scale = sc[2];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) v[j] = (j == 0) ? 1.0 : (tk != 0.0 ? rowk[j] * scale : 0.0);
+    if (blockIdx.x == 0) {
+      for (int j = threadIdx.x; j < m; j += blockDim.x) Vh[(int64_t)k * n + j] = v[j];
+      if (threadIdx.x == 0) {
+        d[k] = A[(int64_t)k * n + k];
+        e[k] = sc[1];
+        tau[k] = tk;
       }
-      __syncthreads();
-      // upper-triangular block pairs (i <= j); consecutive threads take consecutive j
-      for (int64_t w = gtid; w < nblk; w += gsz) {
-        const double b2 = 2.0 * np + 1.0;
-        int i = (int)((b2 - sqrt(b2 * b2 - 8.0 * (double)w)) * 0.5);
-        if (i < 0) i = 0;
-        if (i > np - 1) i = np - 1;
-        int64_t start = (int64_t)i * np - (int64_t)i * (i - 1) / 2;
-        while (start > w) { --i; start = (int64_t)i * np - (int64_t)i * (i - 1) / 2; }
-        while (start + (np - i) <= w) { start += np - i; ++i; }
-        const int j = i + (int)(w - start);
-        int pi, qi, pj, qj;
-        round_pair(r, i, m, pi, qi);
-        round_pair(r, j, m, pj, qj);
-        block_update<true>(A, n, n, pi, qi, rot[i], pj, qj, rot[j], i == j);
-        // publish what the next round's rotations read
-        const int xs[2] = {pi, qi}, ys[2] = {pj, qj};
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const int x = xs[u], y = ys[v];
-            if (x >= n || y >= n) continue;
-            const double val = A[(int64_t)x * n + y];
-            if (x == y) {
-              dnext[x] = val;
-            } else if (round_partner(x, rn, m) == y && (i != j || x < y)) {
-              onext[round_slot(x, rn, m)] = val;
-            }
-          }
-      }
-      for (int64_t w = gtid; w < (int64_t)np * n; w += gsz) {
-        const int k = (int)(w / n), col = (int)(w - (int64_t)k * n);
-        int p, q;
-        round_pair(r, k, m, p, q);
-        if (p >= n) continue;
-        vt_update(VT, n, p, q, rot[k], col);
-      }
+    }
+    __syncthreads();
+    if (tk == 0.0) {  // column already reduced: no reflection, nothing to update
       if (!grid_barrier(bar, status)) return;
+      continue;
     }
+    // p = tau A22 v, one warp per row
+    const int64_t base = (int64_t)(k + 1) * n + (k + 1);
+    for (int i = gwarp; i < m; i += nwarps) {
+      const double* row = A + base + (int64_t)i * n;
+      double dot = 0.0;
+      for (int j = lane; j < m; j += 32) dot = fma(row[j], v[j], dot);
+      dot = warp_sum(dot);
+      if (lane == 0) pbuf[i] = tk * dot;
+    }
+    if (!grid_barrier(bar, status)) return;
+    // w = p - (tau/2)(p.v) v
+    double pv = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double pj = pbuf[j];
+      w[j] = pj;
+      pv = fma(pj, v[j], pv);
+    }
+    const double K = 0.5 * tk * block_sum(pv, red);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] -= K * v[j];
     __syncthreads();
-    if (!any_rot) break;
-  }
-  // every CTA ranks the eigenvalues itself and writes its share of V
-  int* rank = reinterpret_cast<int*>(smem);
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double li = A[(int64_t)i * n + i];
-    int rk = 0;
-    for (int j = 0; j < n; ++j) {
-      const double lj = A[(int64_t)j * n + j];
-      rk += (lj > li) || (lj == li && j < i);
+    // A22 -= v w^T + w v^T, one warp per row
+    for (int i = gwarp; i < m; i += nwarps) {
+      double* row = A + base + (int64_t)i * n;
+      const double vi = v[i], wi = w[i];
+      for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
     }
-    rank[i] = rk;
-    if (blockIdx.x == 0) lam[rk] = li;
+    if (!grid_barrier(bar, status)) return;
   }
-  __syncthreads();
-  for (int64_t e = gtid; e < (int64_t)n * n; e += gsz) {
-    const int64_t i = e / n, k = e - i * n;
-    V[k * n + rank[i]] = VT[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(int64_t)(n - 2) * n + (n - 2)];
+      e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+      tau[n - 2] = 0.0;
+    }
+    d[n - 1] = A[(int64_t)(n - 1) * n + (n - 1)];
+    e[n - 1] = 0.0;
+    tau[n - 1] = 0.0;
   }
 }
 
-__global__ void fro_norm_kernel(const double* __restrict__ A, int64_t nn, double* __restrict__ out) {
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma(A[i], A[i], s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+// ---------------------------------------------------------------------------
+// Sturm-sequence bisection: every eigenvalue of the tridiagonal (d, e); one
+// thread per eigenvalue. lam is written in descending order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) <= pivmin) q = -pivmin;
+  int cnt = q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - (e[i - 1] * e[i - 1]) / q;
+    if (fabs(q) <= pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
 }
 
-size_t small_smem_bytes(int64_t n) {
-  const int64_t n2 = n + (n & 1);
-  return (size_t)(n * n) * sizeof(double) + (size_t)(n2 / 2) * sizeof(Rot) + (size_t)n * sizeof(int) + 16;
+__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                              double* __restrict__ lam) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // ascending index
+  if (k >= n) return;
+  double gl = d[0], gu = d[0], emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    gl = fmin(gl, d[i] - r);
+    gu = fmax(gu, d[i] + r);
+    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  const double tnorm = fmax(fabs(gl), fabs(gu));
+  gl -= 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
+  gu += 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
+  double lo = gl, hi = gu;
+  for (int it = 0; it < 128; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin || mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, n, mid, pivmin) > k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  lam[n - 1 - k] = 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------
+// Eigenvectors of T for the r largest eigenvalues by twisted factorisation:
+// with the stationary (top-down) and progressive (bottom-up) LDL^T
+// factorisations of T - lambda I, the twist index k minimising
+// |gamma_k| = |D+_k + D-_k - (d_k - lambda)| gives the eigenvector from
+// z_k = 1 and two one-sided recurrences. One thread leads each cluster of
+// eigenvalues closer than ctol and orthogonalises the members it computes
+// against the earlier ones (modified Gram-Schmidt, twice).
+// Z[i * r + j] receives component i of eigenvector j of T.
+// Scratch per eigenvalue index: 5 n doubles.
+// ---------------------------------------------------------------------------
+__global__ void invit_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                             const double* __restrict__ lam, int r, double* __restrict__ Z,
+                             double* __restrict__ scratch) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= r) return;
+  const double tnorm = fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN;
+  const double ctol = 1e-9 * tnorm;
+  const double tiny = 1e-3 * DBL_EPSILON * tnorm + DBL_MIN;
+  if (j > 0 && fabs(lam[j - 1] - lam[j]) <= ctol) return;  // not a cluster leader
+  int c = 1;
+  while (j + c < r && fabs(lam[j + c - 1] - lam[j + c]) <= ctol) ++c;
+  double* Dp = scratch + (int64_t)j * 5 * n;
+  double* Lp = Dp + n;
+  double* Dm = Lp + n;
+  double* Um = Dm + n;
+  double* z = Um + n;
+  for (int m = j; m < j + c; ++m) {
+    // perturb repeated shifts slightly so the members differ
+    const double s = lam[m] + (double)(m - j) * 10.0 * DBL_EPSILON * tnorm;
+    Dp[0] = d[0] - s;
+    for (int i = 0; i + 1 < n; ++i) {
+      if (fabs(Dp[i]) < tiny) Dp[i] = tiny;
+      Lp[i] = e[i] / Dp[i];
+      Dp[i + 1] = (d[i + 1] - s) - Lp[i] * e[i];
+    }
+    Dm[n - 1] = d[n - 1] - s;
+    for (int i = n - 1; i >= 1; --i) {
+      if (fabs(Dm[i]) < tiny) Dm[i] = tiny;
+      Um[i] = e[i - 1] / Dm[i];
+      Dm[i - 1] = (d[i - 1] - s) - Um[i] * e[i - 1];
+    }
+    int k = 0;
+    double best = INFINITY;
+    for (int i = 0; i < n; ++i) {
+      const double g = fabs(Dp[i] + Dm[i] - (d[i] - s));
+      if (g < best) {
+        best = g;
+        k = i;
+      }
+    }
+    z[k] = 1.0;
+    for (int i = k - 1; i >= 0; --i) z[i] = -Lp[i] * z[i + 1];
+    for (int i = k + 1; i < n; ++i) z[i] = -Um[i] * z[i - 1];
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = j; q < m; ++q) {
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot = fma(Z[(int64_t)i * r + q], z[i], dot);
+        for (int i = 0; i < n; ++i) z[i] -= dot * Z[(int64_t)i * r + q];
+      }
+    }
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(z[i]));
+    if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) {
+      z[i] /= mx;
+      nrm = fma(z[i], z[i], nrm);
+    }
+    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+    for (int i = 0; i < n; ++i) Z[(int64_t)i * r + m] = z[i] * inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Back-transformation U = Q Z = H_0 H_1 ... H_{n-3} Z, one warp per column,
+// reflectors applied last-first; the column lives in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EIG_THREADS) backtransform_kernel(const double* __restrict__ Vh,
+                                                                    const double* __restrict__ tau, int n, int r,
+                                                                    double* __restrict__ Z) {
+  extern __shared__ double col[];  // (blockDim / 32) columns of n
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (c >= r) return;
+  double* z = col + (int64_t)wid * n;
+  for (int i = lane; i < n; i += 32) z[i] = Z[(int64_t)i * r + c];
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    const int m = n - k - 1;
+    const double* v = Vh + (int64_t)k * n;
+    double dot = 0.0;
+    for (int i = lane; i < m; i += 32) dot = fma(v[i], z[k + 1 + i], dot);
+    dot = warp_sum(dot) * t;
+    for (int i = lane; i < m; i += 32) z[k + 1 + i] -= dot * v[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) Z[(int64_t)i * r + c] = z[i];
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct WorkLayout {
+  double *Vh, *d, *e, *tau, *pbuf;
+  Barrier* bar;
+};
+
+WorkLayout layout(void* work, int64_t n) {
+  char* p = static_cast<char*>(work);
+  WorkLayout L;
+  L.Vh = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * n * n);
+  L.d = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * n);
+  L.e = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * n);
+  L.tau = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * n);
+  L.pbuf = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * n);
+  L.bar = reinterpret_cast<Barrier*>(p);
+  return L;
 }
 
 }  // namespace
 
 size_t eig_workspace_bytes(int64_t n) {
-  // VT (n x n) + barrier + norm scalar + two rounds of rotation snapshots
-  size_t vt = ((size_t)(n * n) * sizeof(double) + 255) & ~(size_t)255;
-  size_t snap = ((size_t)(2 * (n + 1) + 2 * (n / 2 + 1)) * sizeof(double) + 255) & ~(size_t)255;
-  return vt + 256 + 256 + snap;
+  return align256(sizeof(double) * n * n) + 4 * align256(sizeof(double) * n) + 256;
 }
 
-cudaError_t launch_eig_sym(double* G, int64_t n, double* lam, double* V, void* work, int* status,
-                           cudaStream_t s) {
+size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 5 * (size_t)n * (size_t)r + 256; }
+
+cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int* status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (n > 8192) return cudaErrorInvalidValue;
-  char* w = static_cast<char*>(work);
-  double* VT = reinterpret_cast<double*>(w);
-  size_t vt = ((size_t)(n * n) * sizeof(double) + 255) & ~(size_t)255;
-  Barrier* bar = reinterpret_cast<Barrier*>(w + vt);
-  double* nrm = reinterpret_cast<double*>(w + vt + 256);
-  const int64_t n2e = n + (n & 1);
-  double* diagv = reinterpret_cast<double*>(w + vt + 512);
-  double* offv = diagv + 2 * n2e;
-  if (n <= SMALL_MAX) {
-    const size_t sm = small_smem_bytes(n);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(eig_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
-    ProfScope prof(K_EIG_SMALL, s, 9.0 * (double)n * (double)n * (double)n, 24.0 * (double)n * (double)n);
-    eig_small_kernel<<<1, EIG_THREADS, sm, s>>>(G, (int)n, lam, V, VT);
-    note_launch();
-    return cudaGetLastError();
-  }
-  // Frobenius norm for the absolute rotation threshold, read back to the host
-  cudaError_t e = cudaMemsetAsync(nrm, 0, sizeof(double), s);
+  if (n > 4096) return cudaErrorInvalidValue;
+  WorkLayout L = layout(work, n);
+  cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
-  {
-    ProfScope prof(K_NORM, s);
-    fro_norm_kernel<<<152, 256, 0, s>>>(G, n * n, nrm);
-  }
-  note_launch();
-  double h_nrm = 0.0;
-  e = cudaMemcpyAsync(&h_nrm, nrm, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  h_nrm = sqrt(h_nrm);
-  e = cudaMemsetAsync(bar, 0, sizeof(Barrier), s);
-  if (e != cudaSuccess) return e;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t n2 = n + (n & 1);
-  const size_t sm = (size_t)(n2 / 2) * sizeof(Rot) + 64;
+  const size_t sm = 2 * sizeof(double) * (size_t)n;
   if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(eig_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_coop_kernel, EIG_THREADS, sm);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int blocks = nsm * (per_sm > 2 ? 2 : per_sm);
-  int nn = (int)n;
-  void* args[] = {&G, &nn, &lam, &V, &VT, &bar, &status, &h_nrm, &diagv, &offv};
-  {
-    ProfScope prof(K_EIG_COOP, s, 9.0 * (double)n * (double)n * (double)n, 24.0 * (double)n * (double)n);
-    e = cudaLaunchCooperativeKernel((void*)eig_coop_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
+  const double flops = 4.0 / 3.0 * (double)n * (double)n * (double)n;
+  if (n <= SMALL_N) {
+    ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+    tridiag_kernel<<<1, EIG_THREADS, sm, s>>>(G, (int)n, L.Vh, L.d, L.e, L.tau, L.pbuf, L.bar, status);
+    note_launch();
+    e = cudaGetLastError();
+  } else {
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, EIG_THREADS, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // about one warp per row, never more CTAs than can be co-resident
+    const int64_t want = (n + (EIG_THREADS / 32) - 1) / (EIG_THREADS / 32);
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
+    int nn = (int)n;
+    void* args[] = {&G, &nn, &L.Vh, &L.d, &L.e, &L.tau, &L.pbuf, &L.bar, &status};
+    ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+    e = cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
+    note_launch();
   }
-  note_launch();
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope prof(K_EIG_BISECT, s);
+    bisect_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(L.d, L.e, (int)n, lam);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* U, void* work, void* scratch,
+                               cudaStream_t s) {
+  if (n <= 0 || r <= 0) return cudaSuccess;
+  WorkLayout L = layout(work, n);
+  {
+    ProfScope prof(K_EIG_INVIT, s);
+    invit_kernel<<<(unsigned)((r + 63) / 64), 64, 0, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
+                                                          static_cast<double*>(scratch));
+    note_launch();
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (n >= 3) {
+    // one warp per column, each column held in shared memory (at most ~200 KB per CTA)
+    const int cols_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(8, (200 * 1024) / (8 * n)));
+    const size_t sm = sizeof(double) * (size_t)n * cols_per_cta;
+    if (sm > 48 * 1024) {
+      e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    ProfScope prof(K_EIG_BACK, s, 2.0 * (double)n * (double)n * (double)r,
+                   8.0 * (double)n * (0.5 * (double)n + 2.0 * (double)r));
+    backtransform_kernel<<<(unsigned)((r + cols_per_cta - 1) / cols_per_cta), cols_per_cta * 32, sm, s>>>(
+        L.Vh, L.tau, (int)n, (int)r, U);
+    note_launch();
+    e = cudaGetLastError();
+  }
   return e;
 }
 

@@ -14,15 +14,18 @@ void note_launch(int n = 1);
 enum KernelClass {
   K_GRAM_F64 = 0,
   K_TTM_F64 = 1,
-  K_EIG_SMALL = 2,
-  K_EIG_COOP = 3,
+  K_EIG_TRIDIAG = 2,
+  K_EIG_BISECT = 3,
   K_GEMM_F64 = 4,
   K_NORM = 5,
   K_COPY = 6,
   K_TTM_TC = 7,
   K_GRAM_F32 = 8,
-  K_OTHER = 9,
-  K_NUM_CLASSES = 10
+  K_EIG_INVIT = 9,
+  K_EIG_BACK = 10,
+  K_TTM_F32 = 11,
+  K_OTHER = 12,
+  K_NUM_CLASSES = 13
 };
 const char* kernel_class_name(int cls);
 
@@ -56,6 +59,15 @@ struct DevStatus {
 template <typename T>
 cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t B,
                             cudaStream_t s);
+
+// Same Gram with FP32 products, partial sums promoted to FP64 every 16 columns.
+cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s);
+
+// FP32 SIMT mode product; with B == 1 the new axis is written in front of the
+// last R2 rows: out[(o * S + s) * R2 + i] for a = o * R2 + i (R2 = 1: in place).
+template <typename Tin>
+cudaError_t launch_ttm_f32(const Tin* X, float* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+                           int64_t B, int64_t S, int64_t R2, cudaStream_t s);
 
 // out[a][s][b] = sum_t M(s, t) X[a][t][b], M(s, t) = M[s * ms + t * mt], s < S, t < T.
 template <typename Tin, typename Tout>
@@ -103,13 +115,35 @@ cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t s
 // FP64 symmetric eigensolvers (eig.cu)
 // ---------------------------------------------------------------------------
 
-// Full eigendecomposition of a symmetric n x n FP64 matrix G (overwritten).
-// lam[0..n-1] receive the eigenvalues in descending order; V ([n][n] row-major)
-// receives the matching eigenvectors as columns. work must hold
-// eig_workspace_bytes(n) bytes. status: device int, set to a bht_status code
-// on a failed bounded wait.
+// Two-stage eigensolver of a symmetric n x n FP64 matrix G (n <= 4096).
+// Stage 1 overwrites G, keeps the tridiagonal form and its reflectors in
+// `work` (eig_workspace_bytes(n)) and writes every eigenvalue, descending,
+// to lam. Stage 2 (same `work`, after stage 1) writes the eigenvectors of the
+// r largest eigenvalues as the columns of U ([n][r] row-major), using
+// `scratch` (eig_vectors_scratch_bytes(n, r)). status: device int, set to a
+// bht_status code when a bounded wait gives up.
 size_t eig_workspace_bytes(int64_t n);
-cudaError_t launch_eig_sym(double* G, int64_t n, double* lam, double* V, void* work,
-                           int* status, cudaStream_t s);
+size_t eig_vectors_scratch_bytes(int64_t n, int64_t r);
+cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int* status, cudaStream_t s);
+cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* U, void* work, void* scratch,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// tcgen05 tensor-core mode product over the innermost axis (tc.cu)
+//   out[(o * S + s) * R2 + i] = sum_k X[o * R2 + i][k] U[k][s]
+// X fp32 [rows][K] (K % 4 == 0, 16-byte aligned); W prepared by
+// launch_prep_tc_weights from the FP64 basis (nb = 1: TF32 of U^T;
+// nb = 2: TF32 of U^T plus its TF32 remainder). norm_in / norm_out (nullable,
+// device doubles) accumulate ||X||^2 and ||out||^2 in FP64.
+// ---------------------------------------------------------------------------
+bool ttm_tc_supported(int64_t K, int64_t S, int nb);
+size_t ttm_tc_weights_bytes(int64_t K, int64_t S);
+cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_t ldu, bool transpose, float* W,
+                                   int nb, cudaStream_t s);
+cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
+                          int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s);
+
+// A (n x n) += alpha I
+cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s);
 
 }  // namespace bht

@@ -1,0 +1,451 @@
+// tc.cu — tcgen05 tensor-core mode product over the innermost axis.
+//
+//   out[(o * S + s) * R2 + i] = sum_k X[o * R2 + i][k] * U[k][s]
+//
+// X is an item-major layer intermediate viewed as rows of its innermost axis
+// (K contiguous); U is a node basis, so this is the leaf contraction
+// C x_j U_j^T of eq. ht_leaf_contraction (and of Step 1 of Algorithm 2) for
+// the innermost axis j. The new axis of size S is written in front of the
+// last R2-sized group of axes: R2 = 1 keeps it innermost, R2 = (product of
+// all other axes) rotates it to the front, which makes the next axis the
+// innermost one.
+//
+// Arithmetic: X is split into x_hi + x_lo with x_hi = x with its 13 low
+// mantissa bits cleared (what the TF32 datapath reads) and x_lo = x - x_hi;
+// U^T is rounded to TF32 (round-to-nearest), optionally with its own low part.
+// Two (or three) TF32 MMAs per K step, FP32 accumulation in TMEM: the result
+// carries no truncation bias and a relative error of about 2^-12 (2^-20 with
+// the low part of U), which keeps the norm difference of the skip test of
+// Algorithm 2 (eq. relative_error_threshold) unbiased.
+//
+// Structure: persistent CTAs (one per SM), 128-row tiles, 8 warps:
+//   warp 0      TMA producer (cp.async.bulk.tensor, 128B swizzle)
+//   warp 1      TMEM allocator and single-thread MMA issuer
+//   warps 2-3   split x into hi / lo in shared memory, fold ||X||^2 (FP64)
+//   warps 4-7   epilogue: tcgen05.ld, scattered store, fold ||out||^2 (FP64)
+// Every mbarrier wait is bounded (1 s); a wait that gives up sets the status
+// word to BHT_ETIMEOUT and the CTA winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace bht {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int BM = 128;           // rows per tile (MMA M)
+constexpr int KC = 32;            // fp32 per 128-byte swizzle row (one K chunk)
+constexpr int NSLOT = 4;          // K-chunk ring depth
+constexpr int CHUNK_BYTES = BM * KC * 4;  // 16 KB
+constexpr uint64_t WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Bounded wait for the completion of phase `parity`; false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status) {
+  uint32_t ok = 0;
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255) {
+      const uint64_t t = gtimer();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > WAIT_NS) {
+        atomicExch(status, 6);
+        return false;
+      }
+      if (*(volatile int*)status != 0) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart (tcgen05 shared-memory descriptor).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)2 << 61;                         // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct TcParams {
+  int64_t rows;    // rows of X
+  int nkc;         // K chunks of 32
+  int S;           // output extent
+  int S_pad;       // rows of one weight plane (multiple of 16)
+  int S_tile;      // MMA N per work unit (multiple of 16, <= 256)
+  int n_ntiles;    // ceil(S_pad / S_tile)
+  int nb;          // 1: B rounded to TF32; 2: B = hi + lo
+  int nslot;       // K-chunk ring depth
+  int64_t R2;      // placement of the new axis
+  float* out;
+  double* norm_in;
+  double* norm_out;
+  int* status;
+};
+
+// Work unit u = (m tile, n tile): m = u / n_ntiles, n = u % n_ntiles. Every
+// K chunk of a unit fills one ring slot: the X chunk (16 KB), its low part
+// (16 KB) and the matching chunk of every weight plane (S_tile x 128 B each).
+__global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_constant__ CUtensorMap mapX,
+                                                                const __grid_constant__ CUtensorMap mapW,
+                                                                const TcParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int w_bytes = P.S_tile * 128;
+  const int slot_bytes = 2 * CHUNK_BYTES + P.nb * w_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)P.nslot * slot_bytes);
+  uint64_t* full = bars;                  // nslot
+  uint64_t* ready = bars + P.nslot;       // nslot
+  uint64_t* empty = bars + 2 * P.nslot;   // nslot
+  uint64_t* tfull = bars + 3 * P.nslot;   // 2
+  uint64_t* tempty = tfull + 2;           // 2
+  __shared__ uint32_t tmem_base;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nunits = ((P.rows + BM - 1) / BM) * P.n_ntiles;
+  const uint32_t ncols = (2 * P.S_tile <= 32) ? 32u
+                         : (2 * P.S_tile <= 64) ? 64u
+                         : (2 * P.S_tile <= 128) ? 128u
+                         : (2 * P.S_tile <= 256) ? 256u : 512u;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < P.nslot; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&ready[i], 2);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int64_t mt = u / P.n_ntiles;
+        const int nt = (int)(u - mt * P.n_ntiles);
+        for (int kc = 0; kc < P.nkc; ++kc, ++g) {
+          const uint32_t slot = g % P.nslot, ph = (g / P.nslot) & 1;
+          if (!mbar_wait(&empty[slot], ph ^ 1, P.status)) goto producer_done;
+          uint8_t* sb = base + (size_t)slot * slot_bytes;
+          mbar_expect_tx(&full[slot], (uint32_t)(CHUNK_BYTES + P.nb * w_bytes));
+          tma_load_2d(&mapX, &full[slot], sb, kc * KC, (int)(mt * BM));
+          for (int b = 0; b < P.nb; ++b)
+            tma_load_2d(&mapW, &full[slot], sb + 2 * CHUNK_BYTES + b * w_bytes, kc * KC, b * P.S_pad + nt * P.S_tile);
+        }
+      }
+    producer_done:;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(P.S_tile >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+      bool ok = true;
+      uint32_t g = 0, it = 0;
+      for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x, ++it) {
+        const uint32_t acc = it & 1, aph = (it >> 1) & 1;
+        if (!mbar_wait(&tempty[acc], aph ^ 1, P.status)) break;
+        fence_after();
+        const uint32_t dt = tmem + acc * P.S_tile;
+        for (int kc = 0; kc < P.nkc; ++kc, ++g) {
+          const uint32_t slot = g % P.nslot, ph = (g / P.nslot) & 1;
+          if (!mbar_wait(&full[slot], ph, P.status) || !mbar_wait(&ready[slot], ph, P.status)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sb = smem_u32(base + (size_t)slot * slot_bytes);
+          const uint32_t ahi = sb, alo = sb + CHUNK_BYTES, bhi = sb + 2 * CHUNK_BYTES, blo = bhi + w_bytes;
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const uint64_t bd = sw128_desc(bhi + 32 * k4);
+            mma_tf32(dt, sw128_desc(ahi + 32 * k4), bd, idesc, (kc | k4) != 0);
+            mma_tf32(dt, sw128_desc(alo + 32 * k4), bd, idesc, 1);
+            if (P.nb == 2) mma_tf32(dt, sw128_desc(ahi + 32 * k4), sw128_desc(blo + 32 * k4), idesc, 1);
+          }
+          mma_commit(&empty[slot]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+      }
+    }
+  } else if (warp < 4) {
+    // ---------------- hi / lo split of X, ||X||^2 ----------------
+    const int tid = threadIdx.x - 64;  // 0..63
+    double sq = 0.0;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      const int64_t mt = u / P.n_ntiles;
+      const bool count = P.norm_in && (u - mt * P.n_ntiles) == 0;  // each X tile once
+      for (int kc = 0; kc < P.nkc; ++kc, ++g) {
+        const uint32_t slot = g % P.nslot, ph = (g / P.nslot) & 1;
+        if (!mbar_wait(&full[slot], ph, P.status)) {
+          ok = false;
+          break;
+        }
+        const float4* src = reinterpret_cast<const float4*>(base + (size_t)slot * slot_bytes);
+        float4* dst = reinterpret_cast<float4*>(base + (size_t)slot * slot_bytes + CHUNK_BYTES);
+        for (int q = tid; q < CHUNK_BYTES / 16; q += 64) {
+          const float4 x = src[q];
+          float4 l;
+          l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+          l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+          l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+          l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+          dst[q] = l;
+          if (count) sq += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[slot]);
+      }
+    }
+    if (P.norm_in) {
+      sq = warp_sum_d(sq);
+      if (lane == 0) atomicAdd(P.norm_in, sq);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp - 4;  // TMEM lane quarter
+    double sq = 0.0;
+    uint32_t it = 0;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++it) {
+      const int64_t mt = u / P.n_ntiles;
+      const int nt = (int)(u - mt * P.n_ntiles);
+      const uint32_t acc = it & 1, aph = (it >> 1) & 1;
+      if (!mbar_wait(&tfull[acc], aph, P.status)) break;
+      fence_after();
+      const int64_t row = mt * BM + q * 32 + lane;
+      const bool valid = row < P.rows;
+      int64_t o = 0, i = 0;
+      if (valid) {
+        o = row / P.R2;
+        i = row - o * P.R2;
+      }
+      const int s0 = nt * P.S_tile;
+      float* dst = P.out + (o * P.S) * P.R2 + i;
+      for (int c0 = 0; c0 < P.S_tile && s0 + c0 < P.S; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * P.S_tile + c0, v);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int s = s0 + c0 + j;
+            if (s < P.S) {
+              dst[(int64_t)s * P.R2] = v[j];
+              sq += (double)v[j] * v[j];
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+    if (P.norm_out) {
+      sq = warp_sum_d(sq);
+      if (lane == 0) atomicAdd(P.norm_out, sq);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// W[b][s][k] (b = 0: RN-rounded TF32 of U^T; b = 1: RN-rounded TF32 of the remainder), zero padded.
+__global__ void prep_weights_kernel(const double* __restrict__ U, int64_t K, int64_t S, int64_t ldu, int transpose,
+                                    float* __restrict__ W, int S_pad, int K_pad, int nb) {
+  const int64_t total = (int64_t)S_pad * K_pad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / K_pad, k = e - s * K_pad;
+    float x = 0.f;
+    if (s < S && k < K) x = (float)(transpose ? U[k * ldu + s] : U[s * ldu + k]);
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float xh = __uint_as_float(h);
+    W[e] = xh;
+    if (nb == 2) {
+      uint32_t l;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - xh));
+      W[total + e] = __uint_as_float(l);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                 uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool ttm_tc_supported(int64_t K, int64_t S, int nb) {
+  return K >= 4 && K % 4 == 0 && S >= 1 && S <= 4096 && nb >= 1 && nb <= 2;
+}
+
+size_t ttm_tc_weights_bytes(int64_t K, int64_t S) {
+  const int64_t S_pad = (S + 15) / 16 * 16, K_pad = (K + 31) / 32 * 32;
+  return (size_t)2 * S_pad * K_pad * sizeof(float);
+}
+
+cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_t ldu, bool transpose, float* W,
+                                   int nb, cudaStream_t s) {
+  const int S_pad = (int)((S + 15) / 16 * 16), K_pad = (int)((K + 31) / 32 * 32);
+  ProfScope prof(K_COPY, s);
+  prep_weights_kernel<<<64, 256, 0, s>>>(U, K, S, ldu, transpose ? 1 : 0, W, S_pad, K_pad, nb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
+                          int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s) {
+  if (!ttm_tc_supported(K, S, nb) || rows <= 0 || R2 <= 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || (reinterpret_cast<uintptr_t>(W) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const int S_pad = (int)((S + 15) / 16 * 16), K_pad = (int)((K + 31) / 32 * 32);
+  // MMA N per unit: the whole padded output when it fits (<= 256), else balanced tiles of <= 256
+  const int n_ntiles = (S_pad + 255) / 256;
+  const int S_tile = ((S_pad + n_ntiles - 1) / n_ntiles + 15) / 16 * 16;
+  const int nkc = K_pad / KC;
+  const int w_bytes = S_tile * 128;
+  const int slot_bytes = 2 * CHUNK_BYTES + nb * w_bytes;
+  const int nslot = std::max(2, std::min(6, (200 * 1024) / slot_bytes));
+  CUtensorMap mx, mw;
+  if (!make_map_2d(&mx, X, (uint64_t)K, (uint64_t)rows, KC, BM)) return cudaErrorInvalidValue;
+  if (!make_map_2d(&mw, W, (uint64_t)K_pad, (uint64_t)S_pad * nb, KC, (uint32_t)S_tile)) return cudaErrorInvalidValue;
+  const size_t smem = 1024 + (size_t)nslot * slot_bytes + (size_t)(3 * nslot + 4) * 8;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nunits = ((rows + BM - 1) / BM) * n_ntiles;
+  const int grid = (int)std::min<int64_t>(nunits, nsm);
+  TcParams P{rows, nkc, (int)S, S_pad, S_tile, n_ntiles, nb, nslot, R2, out, norm_in, norm_out, status};
+  ProfScope prof(K_TTM_TC, s, 2.0 * (double)rows * (double)K * (double)S,
+                 4.0 * (double)rows * ((double)K + (double)S));
+  ttm_tc_kernel<<<grid, TC_THREADS, smem, s>>>(mx, mw, P);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace bht
