@@ -149,6 +149,22 @@ bht_status ht_encode(const bht_state* state, const void* Y, int32_t dtype, int64
 bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S,
                             int32_t precision, float* out, int64_t R2, double* norms, void* stream);
 
+/* bht_mode_product without any device allocation (the paper has no
+ * counterpart: this is an interface for callers that may not allocate device
+ * memory during the call, e.g. when another allocator owns the GPU's memory or
+ * in a latency-critical loop where cudaMalloc / cudaFree could synchronise).
+ * Same operation and arguments as bht_mode_product with precision
+ * BHT_PREC_MIXED; X, U, out and norms are the caller's device buffers. The
+ * scratch (split TF32 weight planes and a status word, 1 MiB + 256 B) is a
+ * file-scope device array that every GPU loading the library holds until the
+ * process exits; it limits K <= 512 and S <= 256 (BHT_ECAPACITY beyond) and
+ * needs K % 4 == 0. The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make it before any stream capture. All calls share
+ * the array and it keeps the last call's contents: calls that overlap on the
+ * GPU race on it and must be serialised by the caller. Synchronises `stream`. */
+bht_status bht_mode_product_noalloc(const float* X, int64_t rows, int64_t K, const double* U, int64_t S,
+                                    float* out, int64_t R2, double* norms, void* stream);
+
 /* Node eigensolver (the error-truncated SVD of eq. ht_leaf_svd taken through
  * the Gram matrix of the unfolding): G is a symmetric FP64 device matrix
  * [n][n] (overwritten); lam receives all n eigenvalues in descending order;

@@ -67,6 +67,7 @@ def _load():
         "bht_profile_enable": [ctypes.c_uint32],
         "bht_mode_product": [vp, i64, i64, vp, i64, i32, vp, i64, vp, vp],
         "bht_sym_eig": [vp, i64, vp, vp, i64, vp],
+        "bht_mode_product_noalloc": [vp, i64, i64, vp, i64, vp, i64, vp, vp],
         "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
     }
     for name, args in sig.items():
@@ -86,7 +87,7 @@ _lib = _load()
 EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
-            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig"]
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc"]
 KERNEL_CLASSES = 16
 
 
@@ -285,6 +286,18 @@ def bht_mode_product(X, U, S: int, precision="mixed", R2: int = 1, out=None, nor
     _check(_lib.bht_mode_product(ctypes.c_void_p(X.data_ptr()), rows, K, ctypes.c_void_p(U.data_ptr()), int(S),
                                  int(code), ctypes.c_void_p(out.data_ptr()), int(R2), nptr, _stream(stream)),
            "bht_mode_product")
+    return out
+
+
+def bht_mode_product_noalloc(X, U, S: int, R2: int = 1, out=None, norms=None, stream=None):
+    """bht_mode_product (tensor cores) with the library allocating nothing: out must be given by the caller."""
+    rows, K = X.shape
+    if out is None:
+        raise ValueError("bht_mode_product_noalloc writes into a caller-owned output")
+    nptr = ctypes.c_void_p(norms.data_ptr()) if norms is not None else None
+    _check(_lib.bht_mode_product_noalloc(ctypes.c_void_p(X.data_ptr()), rows, K, ctypes.c_void_p(U.data_ptr()),
+                                         int(S), ctypes.c_void_p(out.data_ptr()), int(R2), nptr, _stream(stream)),
+           "bht_mode_product_noalloc")
     return out
 
 

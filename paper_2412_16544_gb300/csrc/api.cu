@@ -88,6 +88,7 @@ void prof_resolve() {
 
 namespace bht {
 void note_launch(int n) { g_launches += n; }
+void set_last_error(const char* msg) { g_err = msg; }
 
 const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",

@@ -10,6 +10,9 @@ namespace bht {
 // Launch counter (kernels launched by the library on the calling thread).
 void note_launch(int n = 1);
 
+// Message returned by bht_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Kernel classes timed by the optional per-launch CUDA-event profiler.
 enum KernelClass {
   K_GRAM_F64 = 0,
