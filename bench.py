@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default=os.environ.get("BHT_BENCH_PRECISION", "fp64"))
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=os.environ.get("BHT_BENCH_PRECISION", "mixed"))
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--increments", type=int, default=20)
     ap.add_argument("--items", type=int, default=32)
@@ -226,8 +226,17 @@ def run_ours(a, rank, world, local_rank):
     B.bht_state_destroy(st)
     dom_name = max(breakdown, key=lambda k: breakdown[k][0])
     dom_cls = [B.bht_kernel_class_name(i) for i in range(B.KERNEL_CLASSES)].index(dom_name)
+    hbm_peak = 6800.0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak_src = "fallback 6.8 TB/s (profiling recipe)"
+    if os.path.exists(peaks_path):
+        hbm_peak = float(json.load(open(peaks_path)).get("hbm_gbs", hbm_peak))
+        peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
 
-    ms, launches, prof, clocks, states = timed(a.precision, a.steps, a.warmup, profile_mask=1 << dom_cls)
+    names = [B.bht_kernel_class_name(i) for i in range(B.KERNEL_CLASSES)]
+    tc_cls = names.index("ttm_tc")
+    ms, launches, prof, clocks, states = timed(a.precision, a.steps, a.warmup,
+                                               profile_mask=(1 << dom_cls) | (1 << tc_cls))
     value = bytes_per_step * world / (ms / 1000.0) / 1e9
 
     # accuracy of the last timed pass: per-increment relative error of the reconstruction
@@ -279,22 +288,31 @@ def run_ours(a, rank, world, local_rank):
         oracle_diff = float(np.linalg.norm(r_gpu - r_or) / np.linalg.norm(Yh[0]))
         B.bht_state_destroy(st1)
 
-    # roofline of the dominant kernel class (algorithmic work accumulated by the library)
-    dom_ms, dom_n, flops, nbytes = prof.get(dom_name, (0.0, 0, 0.0, 0.0))
-    roof = None
-    if dom_n:
-        if dom_name in ("ttm_tc", "gram_f32", "copy", "norm"):
-            ach = nbytes / dom_n / (dom_ms / dom_n / 1000.0) / 1e9
-            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-                if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": None, "kernel": dom_name, "launches_per_step": dom_n / a.steps}
+    # roofline of the dominant kernel class and of the tensor-core mode product (algorithmic work per launch
+    # accumulated by the library, CUDA-event durations on the launch stream over the timed region)
+    def roof(name):
+        t_ms, n_l, flops, nbytes = prof.get(name, (0.0, 0, 0.0, 0.0))
+        if not n_l or t_ms <= 0:
+            return None
+        per_launch_s = t_ms / n_l / 1000.0
+        if name in ("ttm_tc", "copy", "norm"):
+            ach = nbytes / n_l / per_launch_s / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None, "kernel": name, "launches_per_step": n_l / a.steps,
+                    "ms_per_launch": per_launch_s * 1e3, "peak_source": peak_src}
+        if name.endswith("f32"):
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+            src = "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz"
         else:
-            ach = flops / dom_n / (dom_ms / dom_n / 1000.0) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / PEAK_FP64_TFLOPS, "traffic": None, "kernel": dom_name,
-                    "launches_per_step": dom_n / a.steps,
-                    "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)"}
+            peak = PEAK_FP64_TFLOPS
+            src = "FP64 nominal of the profiling recipe (1.25 TFLOP/s)"
+        ach = flops / n_l / per_launch_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": name, "launches_per_step": n_l / a.steps,
+                "ms_per_launch": per_launch_s * 1e3, "peak_source": src}
+
+    roofline = roof(dom_name)
+    roofline_tc = roof("ttm_tc")
 
     if dist is not None:
         dist.barrier()
@@ -307,7 +325,7 @@ def run_ours(a, rank, world, local_rank):
         "config": {"workload": workload_name(a), "precision": a.precision, "items_per_step": a.increments * a.items,
                    "bytes_per_step": bytes_per_step, "parallelism": f"{world} independent streams",
                    "l2": "inputs (671 MB per stream) larger than L2 (129 MB); no flush"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roofline, "roofline_ttm_tc": roofline_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "plain_fp64": plain,
         "accuracy": {"max_rel_err_per_increment": max(errs), "eps_rel": a.eps,

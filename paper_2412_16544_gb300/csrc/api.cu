@@ -458,22 +458,75 @@ LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<
 struct EigOut {
   DBuf work, lam;
   int64_t n = 0;
-  std::vector<double> h_lam;
+  int64_t computed = 0;          // eigenvalues known: descending indices [0, computed)
+  double trace = 0.0;            // trace of the matrix (= sum of the tridiagonal's diagonal)
+  std::vector<double> h_lam;     // host copy of lam[0, computed)
+  std::vector<double> h_diag;
 };
 
-// Stage 1 of the eigensolver: every eigenvalue of the symmetric FP64 matrix G (destroyed).
-void eig_values64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
+// Stage 1a of the eigensolver: tridiagonalise the symmetric FP64 matrix G (destroyed) and start the
+// copy of the tridiagonal's diagonal (its sum is the trace) to the host.
+void eig_tridiag64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
   out.n = n;
+  out.computed = 0;
   out.lam = DBuf(sizeof(double) * n, s);
   out.work = DBuf(eig_workspace_bytes(n), s);
-  ck(launch_eig_values(G, n, out.lam.as<double>(), out.work.p, d_status, s), "eigenvalues");
+  ck(launch_eig_tridiag(G, n, out.work.p, d_status, s), "tridiagonalisation");
+  out.h_diag.resize(n);
+  ck(cudaMemcpyAsync(out.h_diag.data(), eig_tridiag_diagonal(out.work.p, n), sizeof(double) * n,
+                     cudaMemcpyDeviceToHost, s),
+     "D2H diagonal");
 }
 
-// X (rows x r) <- X (3I - X^T X) / 2, twice: Newton-Schulz orthonormalisation of nearly orthonormal columns.
-void newton_schulz(double* X, int64_t rows, int64_t r, cudaStream_t s) {
+// Stage 1 complete: every eigenvalue (for the small nodes and the explicit entry point).
+void eig_values64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t s) {
+  eig_tridiag64(G, n, out, d_status, s);
+  ck(launch_eig_bisect(n, out.work.p, out.lam.as<double>(), 0, n, s), "eigenvalues");
+  out.computed = n;
+}
+
+// Truncation rank of eq. ht_leaf_svd / eq. svd_on_residual from the largest eigenvalues only: the
+// discarded energy after r kept values is trace - sum_{i<r} lam_i, so eigenvalues are bisected from the
+// top, in chunks that double, until some r >= rmin meets tail <= eps_nw2 (or all are known).
+// Called after the tridiagonalisation has finished (the stream was synchronised).
+int64_t eig_rank64(EigOut& eo, double eps_nw2, int64_t rmin, int64_t rmax, cudaStream_t s) {
+  const int64_t n = eo.n;
+  double tr = 0.0;
+  for (double v : eo.h_diag) tr += v;
+  eo.trace = tr;
+  rmax = std::min(rmax, n);
+  // every eigenvalue in one launch: a Sturm sweep is latency-bound, so fewer eigenvalues do not cost less
+  int64_t want = n;
+  while (true) {
+    if (want > eo.computed) {
+      ck(launch_eig_bisect(n, eo.work.p, eo.lam.as<double>(), eo.computed, want, s), "eigenvalues");
+      eo.h_lam.resize(want);
+      ck(cudaMemcpyAsync(eo.h_lam.data() + eo.computed, eo.lam.as<double>() + eo.computed,
+                         sizeof(double) * (want - eo.computed), cudaMemcpyDeviceToHost, s),
+         "D2H eigenvalues");
+      ck(cudaStreamSynchronize(s), "sync");
+      eo.computed = want;
+    }
+    // smallest r >= rmin with tail(r) <= eps_nw2 among r <= computed; tail(n) = 0 when all are known
+    double kept = 0.0;
+    for (int64_t r = 0; r <= eo.computed; ++r) {
+      if (r >= rmin) {
+        const double tail = (r == n) ? 0.0 : std::max(tr - kept, 0.0);
+        if (tail <= eps_nw2 || r >= rmax) return std::min(r, rmax);
+      }
+      if (r < eo.computed) kept += std::max(eo.h_lam[r], 0.0);
+    }
+    if (eo.computed >= n) return std::min(n, rmax);
+    want = std::min<int64_t>(n, 2 * eo.computed);
+  }
+}
+
+// X (rows x r) <- X (3I - X^T X) / 2: Newton-Schulz orthonormalisation of nearly orthonormal
+// columns (an orthonormality error e becomes about 3e^2/4 per step).
+void newton_schulz(double* X, int64_t rows, int64_t r, cudaStream_t s, int iters = 1) {
   if (r <= 0) return;
   DBuf S(sizeof(double) * r * r, s), T(sizeof(double) * rows * r, s);
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < iters; ++it) {
     ck(launch_gemm_f64(r, r, rows, -0.5, X, 1, r, X, r, 1, 0.0, S.as<double>(), r, 1, s), "X^T X");
     ck(launch_add_diag(S.as<double>(), r, 1.5, s), "1.5 I");
     ck(launch_gemm_f64(rows, r, r, 1.0, X, r, 1, S.as<double>(), r, 1, 0.0, T.as<double>(), r, 1, s), "X S");
@@ -490,22 +543,6 @@ double* eig_vectors64(EigOut& eo, int64_t r, cudaStream_t s) {
   ck(launch_eig_vectors(n, r, eo.lam.as<double>(), U, eo.work.p, scratch.p, s), "eigenvectors");
   newton_schulz(U, n, r, s);
   return U;
-}
-
-// smallest r >= rmin with sum_{i>=r} max(lam_i, 0) <= eps_nw2 (lam descending); capped at rmax
-int64_t tail_rank(const std::vector<double>& lam, double eps_nw2, int64_t rmin, int64_t rmax) {
-  const int64_t n = (int64_t)lam.size();
-  std::vector<double> tail(n + 1, 0.0);
-  for (int64_t i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + std::max(lam[i], 0.0);
-  int64_t r = n;
-  for (int64_t i = 0; i <= n; ++i)
-    if (tail[i] <= eps_nw2) {
-      r = i;
-      break;
-    }
-  r = std::max(r, rmin);
-  r = std::min(r, std::min(rmax, n));
-  return r;
 }
 
 void check_status(bht_state* st, cudaStream_t s) {
@@ -759,18 +796,14 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
         const int64_t I = C.dims[ax];
         DBuf G(sizeof(double) * I * I, s);
         gram_any(C, ax, G.as<double>(), ar, s);
-        eig_values64(G.as<double>(), I, eo[k], st->d_status, s);
-      }
-      for (auto& e : eo) {
-        e.h_lam.resize(e.n);
-        ck(cudaMemcpyAsync(e.h_lam.data(), e.lam.p, sizeof(double) * e.n, cudaMemcpyDeviceToHost, s), "D2H lam");
+        eig_tridiag64(G.as<double>(), I, eo[k], st->d_status, s);
       }
       check_status(st, s);
       std::vector<const double*> Us;
       std::vector<int64_t> rs;
       for (size_t k = 0; k < ids.size(); ++k) {
         const int64_t n = eo[k].n;
-        const int64_t r = tail_rank(eo[k].h_lam, eps_nw2, 1, n);  // eq. ht_leaf_svd, r >= 1
+        const int64_t r = eig_rank64(eo[k], eps_nw2, 1, n, s);  // eq. ht_leaf_svd, r >= 1
         double* U = eig_vectors64(eo[k], r, s);
         st->U[ids[k]] = U;
         st->rank[ids[k]] = r;
@@ -851,8 +884,23 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         const int64_t a = C.dims[ax];
         alpha[k] = a;
         rold[k] = rank[ids[k]];
-        // residual Gram R R^T = Pi G Pi with Pi = I - U U^T (eq. compute_residual)
-        DBuf G(sizeof(double) * a * a, s), Pi(sizeof(double) * a * a, s), H(sizeof(double) * a * a, s);
+        // residual Gram R R^T with R = (I - U U^T) C_(j) (eq. compute_residual). A large node forms R from the
+        // data (two mode products and a difference); a small one forms Pi G Pi from its Gram matrix.
+        DBuf G(sizeof(double) * a * a, s);
+        if (a >= 256 && rold[k] > 0) {
+          const double* Uo = U[ids[k]];
+          LTensor W = ttm_any(C, ax, Uo, 1, rold[k], rold[k], false, ar, s);
+          LTensor P = ttm_any(W, ax, Uo, rold[k], 1, a, false, ar, s);
+          W = LTensor();
+          if (C.dtype == BHT_F32)
+            ck(launch_diff_inplace<float>(static_cast<const float*>(C.ptr), P.own.p, P.dtype, P.numel(), s), "R");
+          else
+            ck(launch_diff_inplace<double>(static_cast<const double*>(C.ptr), P.own.p, P.dtype, P.numel(), s), "R");
+          gram_any(P, ax, G.as<double>(), ar, s);
+          eig_tridiag64(G.as<double>(), a, eo[k], st->d_status, s);
+          continue;
+        }
+        DBuf Pi(sizeof(double) * a * a, s), H(sizeof(double) * a * a, s);
         gram_any(C, ax, G.as<double>(), ar, s);
         ck(launch_fill_identity(Pi.as<double>(), a, s), "identity");
         ck(launch_gemm_f64(a, a, rold[k], -1.0, U[ids[k]], rold[k], 1, U[ids[k]], 1, rold[k], 1.0, Pi.as<double>(),
@@ -862,11 +910,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
            "Pi G");
         ck(launch_gemm_f64(a, a, a, 1.0, H.as<double>(), a, 1, Pi.as<double>(), a, 1, 0.0, G.as<double>(), a, 1, s),
            "Pi G Pi");
-        eig_values64(G.as<double>(), a, eo[k], st->d_status, s);
-      }
-      for (auto& e : eo) {
-        e.h_lam.resize(e.n);
-        ck(cudaMemcpyAsync(e.h_lam.data(), e.lam.p, sizeof(double) * e.n, cudaMemcpyDeviceToHost, s), "D2H lam");
+        eig_tridiag64(G.as<double>(), a, eo[k], st->d_status, s);
       }
       check_status(st, s);
       std::vector<int> grown_parents;
@@ -874,7 +918,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         const int id = ids[k];
         const int64_t a = alpha[k], r0 = rold[k];
         // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
-        const int64_t rR = tail_rank(eo[k].h_lam, eps_nw2, 0, std::max<int64_t>(a - r0, 0));
+        const int64_t rR = eig_rank64(eo[k], eps_nw2, 0, std::max<int64_t>(a - r0, 0), s);
         if (rR == 0) continue;
         DBuf UR;
         UR.p = eig_vectors64(eo[k], rR, s);
@@ -887,7 +931,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
           ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, s),
              "U_R -= U W");
         }
-        newton_schulz(UR.as<double>(), a, rR, s);
+        newton_schulz(UR.as<double>(), a, rR, s, 2);
         // expandCore: U^k = [U^{k-1}, U_R] (eq. concatenating_orthonormal_vectors)
         const int64_t rn = r0 + rR;
         double* Un = own(static_cast<double*>(dalloc(sizeof(double) * a * rn, s)));

@@ -327,6 +327,13 @@ __global__ void fill_identity_kernel(double* __restrict__ A, int64_t n) {
     A[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
+// y <- x - y, y of type Ty
+template <typename Tx, typename Ty>
+__global__ void diff_kernel(const Tx* __restrict__ x, Ty* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = static_cast<Ty>(static_cast<Ty>(x[i]) - y[i]);
+}
+
 __global__ void add_diag_kernel(double* __restrict__ A, int64_t n, double alpha) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     A[i * n + i] += alpha;
@@ -489,6 +496,20 @@ cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
   note_launch();
   return cudaGetLastError();
 }
+
+template <typename Tx>
+cudaError_t launch_diff_inplace(const Tx* x, void* y, int y_is_f64, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s, (double)n, (double)n * (sizeof(Tx) + 2 * (y_is_f64 ? 8 : 4)));
+  if (y_is_f64)
+    diff_kernel<Tx, double><<<grid_for(n), 256, 0, s>>>(x, static_cast<double*>(y), n);
+  else
+    diff_kernel<Tx, float><<<grid_for(n), 256, 0, s>>>(x, static_cast<float*>(y), n);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_diff_inplace<float>(const float*, void*, int, int64_t, cudaStream_t);
+template cudaError_t launch_diff_inplace<double>(const double*, void*, int, int64_t, cudaStream_t);
 
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

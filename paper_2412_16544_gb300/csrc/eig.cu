@@ -6,7 +6,7 @@
 // rank only needs all eigenvalues, and the node only needs the eigenvectors it
 // keeps, so the solver runs in two stages:
 //   stage 1  Householder tridiagonalisation Q^T G Q = T, then every eigenvalue
-//            of T by Sturm-sequence bisection (one thread per eigenvalue);
+//            of T by Sturm-sequence multisection (8 lanes, 16 points per round);
 //   stage 2  (after the caller picked r) the eigenvectors of T for the r
 //            largest eigenvalues by twisted factorisation (one thread per
 //            cluster of nearly equal eigenvalues, modified Gram-Schmidt
@@ -196,22 +196,68 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
 // Sturm-sequence bisection: every eigenvalue of the tridiagonal (d, e); one
 // thread per eigenvalue. lam is written in descending order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
-  double q = d[0] - x;
-  if (fabs(q) <= pivmin) q = -pivmin;
-  int cnt = q < 0.0;
+// Numbers of eigenvalues of T below xa and below xb: negative ratios q_i of
+// the LDL^T factorisations of T - x I. The ratios are carried as
+// p_i = q_i p_{i-1} (p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}), so a step
+// costs one multiply and one FMA instead of a division; p is rescaled by exact
+// powers of two to stay in range, and a ratio no larger than pivmin counts as
+// -pivmin. Two independent recurrences give the FP64 pipeline two chains.
+__device__ __forceinline__ void sturm_count2(const double* d, const double* e, int n, double xa, double xb,
+                                             double pivmin, int& ca, int& cb) {
+  constexpr double BIG = 0x1p+800, SMALL = 0x1p-800;
+  double a0 = 1.0, a1 = d[0] - xa, b0 = 1.0, b1 = d[0] - xb;
+  if (fabs(a1) <= pivmin) a1 = -pivmin;
+  if (fabs(b1) <= pivmin) b1 = -pivmin;
+  int na = a1 < 0.0, nb = b1 < 0.0;
+#pragma unroll 2
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - (e[i - 1] * e[i - 1]) / q;
-    if (fabs(q) <= pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    const double e2 = e[i - 1] * e[i - 1], di = d[i];
+    double ta = fma(-e2, a0, (di - xa) * a1);
+    double tb = fma(-e2, b0, (di - xb) * b1);
+    if (fabs(ta) <= pivmin * fabs(a1)) ta = -pivmin * a1;
+    if (fabs(tb) <= pivmin * fabs(b1)) tb = -pivmin * b1;
+    na += (ta < 0.0) != (a1 < 0.0);
+    nb += (tb < 0.0) != (b1 < 0.0);
+    a0 = a1;
+    a1 = ta;
+    b0 = b1;
+    b1 = tb;
+    const double fa = fabs(a1), fb = fabs(b1);
+    if (fa > BIG) { a0 *= SMALL; a1 *= SMALL; } else if (fa < SMALL) { a0 *= BIG; a1 *= BIG; }
+    if (fb > BIG) { b0 *= SMALL; b1 *= SMALL; } else if (fb < SMALL) { b0 *= BIG; b1 *= BIG; }
   }
-  return cnt;
+  ca = na;
+  cb = nb;
 }
 
-__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
-                              double* __restrict__ lam) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // ascending index
-  if (k >= n) return;
+// MS_LANES lanes of one warp share an eigenvalue and evaluate 2 * MS_LANES
+// interior points of its interval per round (multisection): the interval
+// shrinks 17-fold per round and MS_LANES times more warps take part than with
+// plain bisection. Intervals stop at a relative width of 2 eps or an absolute
+// width of 1e-19 ||T||: eigenvalues below that only enter tail sums.
+constexpr int MS_LANES = 8;
+constexpr int MS_PTS = 2 * MS_LANES;
+
+// Eigenvalues with descending indices [j0, j1) (lam[j] = j-th largest).
+__global__ void bisect_kernel(const double* d, const double* e, int n, double* __restrict__ lam, int j0, int j1) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = j0 + gtid / MS_LANES;  // descending index
+  const int k = n - 1 - j;             // ascending index
+  const int g = gtid % MS_LANES;
+  const bool active = j < j1;
+  const int lane = threadIdx.x & 31;
+  const int base = (lane / MS_LANES) * MS_LANES;
+  // the Sturm sweeps are latency-bound: keep the tridiagonal in shared memory
+  extern __shared__ double tsm[];
+  double* sd = tsm;
+  double* se = tsm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = d[i];
+    se[i] = e[i];
+  }
+  __syncthreads();
+  d = sd;
+  e = se;
   double gl = d[0], gu = d[0], emax2 = 0.0;
   for (int i = 0; i < n; ++i) {
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
@@ -221,18 +267,32 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
   }
   const double pivmin = DBL_MIN * fmax(1.0, emax2);
   const double tnorm = fmax(fabs(gl), fabs(gu));
+  const double abs_floor = 1e-19 * tnorm + 4.0 * pivmin;
   gl -= 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
   gu += 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
   double lo = gl, hi = gu;
-  for (int it = 0; it < 128; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin || mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, n, mid, pivmin) > k)
-      hi = mid;
-    else
-      lo = mid;
+  for (int it = 0; it < 40; ++it) {
+    const bool done = !active || hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + abs_floor;
+    if (__all_sync(0xffffffffu, done)) break;
+    const double step = (hi - lo) / (double)(MS_PTS + 1);
+    int ca = 0, cb = 0;
+    if (!done) sturm_count2(d, e, n, lo + step * (double)(2 * g + 1), lo + step * (double)(2 * g + 2), pivmin, ca, cb);
+    const unsigned balA = __ballot_sync(0xffffffffu, !done && ca > k);
+    const unsigned balB = __ballot_sync(0xffffffffu, !done && cb > k);
+    if (!done) {
+      const unsigned ga = (balA >> base) & ((1u << MS_LANES) - 1u);
+      const unsigned gb = (balB >> base) & ((1u << MS_LANES) - 1u);
+      // point p = 2 g + 1 + (0: A, 1: B); counts grow with x, so the points above form a suffix
+      int first = MS_PTS;
+      if (ga) first = 2 * (__ffs(ga) - 1);
+      if (gb) first = min(first, 2 * (__ffs(gb) - 1) + 1);
+      const double nlo = (first == 0) ? lo : lo + step * (double)first;
+      const double nhi = (first == MS_PTS) ? hi : lo + step * (double)(first + 1);
+      lo = nlo;
+      hi = nhi;
+    }
   }
-  lam[n - 1 - k] = 0.5 * (lo + hi);
+  if (active && g == 0) lam[j] = 0.5 * (lo + hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,9 +306,16 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
 // Z[i * r + j] receives component i of eigenvector j of T.
 // Scratch per eigenvalue index: 5 n doubles.
 // ---------------------------------------------------------------------------
-__global__ void invit_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
-                             const double* __restrict__ lam, int r, double* __restrict__ Z,
-                             double* __restrict__ scratch) {
+__global__ void invit_kernel(const double* dg, const double* eg, int n, const double* __restrict__ lam, int r,
+                             double* __restrict__ Z, double* __restrict__ scratch) {
+  extern __shared__ double tsm[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    tsm[i] = dg[i];
+    tsm[n + i] = eg[i];
+  }
+  __syncthreads();
+  const double* d = tsm;
+  const double* e = tsm + n;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= r) return;
   const double tnorm = fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN;
@@ -369,7 +436,7 @@ size_t eig_workspace_bytes(int64_t n) {
 
 size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 5 * (size_t)n * (size_t)r + 256; }
 
-cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int* status, cudaStream_t s) {
+cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 4096) return cudaErrorInvalidValue;
   WorkLayout L = layout(work, n);
@@ -385,30 +452,48 @@ cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int
     ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
     tridiag_kernel<<<1, EIG_THREADS, sm, s>>>(G, (int)n, L.Vh, L.d, L.e, L.tau, L.pbuf, L.bar, status);
     note_launch();
-    e = cudaGetLastError();
-  } else {
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, EIG_THREADS, sm);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // about one warp per row, never more CTAs than can be co-resident
-    const int64_t want = (n + (EIG_THREADS / 32) - 1) / (EIG_THREADS / 32);
-    const int blocks = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
-    int nn = (int)n;
-    void* args[] = {&G, &nn, &L.Vh, &L.d, &L.e, &L.tau, &L.pbuf, &L.bar, &status};
-    ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
-    e = cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
-    note_launch();
+    return cudaGetLastError();
   }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, EIG_THREADS, sm);
   if (e != cudaSuccess) return e;
-  {
-    ProfScope prof(K_EIG_BISECT, s);
-    bisect_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(L.d, L.e, (int)n, lam);
-    note_launch();
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // about one warp per row, never more CTAs than can be co-resident
+  const int64_t want = (n + (EIG_THREADS / 32) - 1) / (EIG_THREADS / 32);
+  const int blocks = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
+  int nn = (int)n;
+  void* args[] = {&G, &nn, &L.Vh, &L.d, &L.e, &L.tau, &L.pbuf, &L.bar, &status};
+  ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+  e = cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(EIG_THREADS), args, sm, s);
+  note_launch();
+  return e;
+}
+
+cudaError_t launch_eig_bisect(int64_t n, void* work, double* lam, int64_t j0, int64_t j1, cudaStream_t s) {
+  if (n <= 0 || j1 <= j0) return cudaSuccess;
+  WorkLayout L = layout(work, n);
+  const int64_t threads = (j1 - j0) * MS_LANES;  // small blocks spread the warps over every SM
+  // algorithmic work: about 3 FP64 operations per Sturm step, 53 / log2(G + 1) rounds of G counts
+  ProfScope prof(K_EIG_BISECT, s, 4.0 * (double)n * (double)MS_PTS * 14.0 * (double)(j1 - j0), 16.0 * (double)n);
+  const int bt = 64;
+  const size_t sm = 2 * sizeof(double) * (size_t)n;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
   }
+  bisect_kernel<<<(unsigned)((threads + bt - 1) / bt), bt, sm, s>>>(L.d, L.e, (int)n, lam, (int)j0, (int)j1);
+  note_launch();
   return cudaGetLastError();
+}
+
+const double* eig_tridiag_diagonal(void* work, int64_t n) { return layout(work, n).d; }
+
+cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int* status, cudaStream_t s) {
+  cudaError_t e = launch_eig_tridiag(G, n, work, status, s);
+  if (e != cudaSuccess) return e;
+  return launch_eig_bisect(n, work, lam, 0, n, s);
 }
 
 cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* U, void* work, void* scratch,
@@ -417,8 +502,13 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
   WorkLayout L = layout(work, n);
   {
     ProfScope prof(K_EIG_INVIT, s);
-    invit_kernel<<<(unsigned)((r + 63) / 64), 64, 0, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
-                                                          static_cast<double*>(scratch));
+    const size_t sm = 2 * sizeof(double) * (size_t)n;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    invit_kernel<<<(unsigned)((r + 31) / 32), 32, sm, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
+                                                           static_cast<double*>(scratch));
     note_launch();
   }
   cudaError_t e = cudaGetLastError();

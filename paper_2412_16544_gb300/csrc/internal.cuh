@@ -128,6 +128,12 @@ cudaError_t launch_check_finite(const T* x, int64_t n, int* flag, cudaStream_t s
 size_t eig_workspace_bytes(int64_t n);
 size_t eig_vectors_scratch_bytes(int64_t n, int64_t r);
 cudaError_t launch_eig_values(double* G, int64_t n, double* lam, void* work, int* status, cudaStream_t s);
+// Stage 1 split in two: the tridiagonalisation (G overwritten), then the eigenvalues with
+// descending indices [j0, j1) only (lam[j] = j-th largest). The diagonal of T (device, n doubles)
+// gives trace(G) for tail sums without the small eigenvalues.
+cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cudaStream_t s);
+cudaError_t launch_eig_bisect(int64_t n, void* work, double* lam, int64_t j0, int64_t j1, cudaStream_t s);
+const double* eig_tridiag_diagonal(void* work, int64_t n);
 cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* U, void* work, void* scratch,
                                cudaStream_t s);
 
@@ -145,6 +151,10 @@ cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_
                                    int nb, cudaStream_t s);
 cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
                           int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s);
+
+// y <- x - y elementwise; y is FP64 when y_is_f64 (the dtype code BHT_F64 = 1), else fp32
+template <typename Tx>
+cudaError_t launch_diff_inplace(const Tx* x, void* y, int y_is_f64, int64_t n, cudaStream_t s);
 
 // A (n x n) += alpha I
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s);
