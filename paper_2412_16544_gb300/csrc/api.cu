@@ -244,6 +244,7 @@ struct bht_state {
   int precision = BHT_PREC_FP64;
   std::vector<int64_t> rank;    // per node id; rank[0] unused
   std::vector<double*> U;       // per node id: orthonormal matrix form [rows][rank], FP64, device
+  std::vector<double*> Q;       // per node id: orthonormal complement of U in R^rows, [rows][rows - rank]
   double* root = nullptr;       // [root_cap][r11][r12], FP64, device
   int64_t root_cap = 0;
   int64_t n_items = 0;
@@ -361,9 +362,10 @@ std::vector<int> best_order(const std::vector<int64_t>& dims, const std::vector<
 //   mixed: full-data contractions of an innermost axis on tcgen05 tensor cores
 //          (split TF32, FP32 accumulation), other contractions in FP32 SIMT,
 //          Grams with FP32 products promoted to FP64 every 16 columns; node
-//          eigensolves, orthogonalisation and norms in FP64. At tight
-//          tolerances (eps_rel < 1e-3) the Grams stay FP64 and the basis
-//          enters the tensor cores with its TF32 remainder (three products).
+//          eigensolves, orthogonalisation and norms in FP64 (the tensor-core
+//          kernel folds ||Y||^2 from FP32 partial sums of 16 squares). At tight
+//          tolerances (eps_rel < 1e-3) the Grams stay FP64 and ||Y||^2 is
+//          summed in FP64 from the data.
 // ---------------------------------------------------------------------------
 struct Arith {
   bool mixed = false;
@@ -545,14 +547,63 @@ double* eig_vectors64(EigOut& eo, int64_t r, cudaStream_t s) {
   return U;
 }
 
-void check_status(bht_state* st, cudaStream_t s) {
+void check_status_word(int* d_status, cudaStream_t s) {
   int h = 0;
-  ck(cudaMemcpyAsync(&h, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
+  ck(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
   ck(cudaStreamSynchronize(s), "sync");
   if (h != 0) {
-    cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
+    cudaMemsetAsync(d_status, 0, sizeof(int), s);
     fail((bht_status)h, "a bounded device-side wait gave up (eigensolver barrier)");
   }
+}
+
+void check_status(bht_state* st, cudaStream_t s) { check_status_word(st->d_status, s); }
+
+// Orthonormal basis [n][n - r] of the orthogonal complement of the orthonormal columns V [n][r]
+// (caller owns it). X = (I - V V^T) Omega for a deterministic pseudo-random Omega with c + 8 columns
+// spans the complement (c = n - r); its orthonormal basis is X Z Lambda^{-1/2} from the c leading
+// eigenpairs of X^T X, after which one more pass against V and Newton-Schulz steps restore FP64
+// orthogonality. A random start avoids the clusters of tiny eigenvalues that an eigenvector
+// route through the discarded part of a Gram spectrum would meet.
+double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int* d_status, cudaStream_t s) {
+  const int64_t c = n - r;
+  double* Q = static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(n * c, 1), s));
+  if (c <= 0) return Q;
+  if (r == 0) {
+    ck(launch_fill_identity(Q, n, s), "identity");
+    return Q;
+  }
+  try {
+    const int64_t k = std::min<int64_t>(n, c + 8);
+    DBuf X(sizeof(double) * n * k, s), W(sizeof(double) * r * std::max(k, c), s);
+    ck(launch_fill_uniform(X.as<double>(), n * k, seed, s), "random start");
+    ck(launch_gemm_f64(r, k, n, 1.0, V, 1, r, X.as<double>(), k, 1, 0.0, W.as<double>(), k, 1, s), "V^T X");
+    ck(launch_gemm_f64(n, k, r, -1.0, V, r, 1, W.as<double>(), k, 1, 1.0, X.as<double>(), k, 1, s), "X -= V W");
+    DBuf M(sizeof(double) * k * k, s);
+    ck(launch_gemm_f64(k, k, n, 1.0, X.as<double>(), 1, k, X.as<double>(), k, 1, 0.0, M.as<double>(), k, 1, s),
+       "X^T X");
+    EigOut eo;
+    eig_tridiag64(M.as<double>(), k, eo, d_status, s);
+    ck(launch_eig_bisect(k, eo.work.p, eo.lam.as<double>(), 0, k, s), "eigenvalues");
+    eo.computed = k;
+    DBuf Z;
+    Z.p = eig_vectors64(eo, c, s);
+    Z.s = s;
+    ck(launch_scale_cols_invsqrt(Z.as<double>(), k, c, eo.lam.as<double>(), s), "Z Lambda^-1/2");
+    ck(launch_gemm_f64(n, c, k, 1.0, X.as<double>(), k, 1, Z.as<double>(), c, 1, 0.0, Q, c, 1, s), "X Z");
+    ck(launch_gemm_f64(r, c, n, 1.0, V, 1, r, Q, c, 1, 0.0, W.as<double>(), c, 1, s), "V^T Q");
+    ck(launch_gemm_f64(n, c, r, -1.0, V, r, 1, W.as<double>(), c, 1, 1.0, Q, c, 1, s), "Q -= V W");
+    newton_schulz(Q, n, c, s, 2);
+    check_status_word(d_status, s);
+  } catch (...) {
+    dfree(Q, s);
+    throw;
+  }
+  return Q;
+}
+
+uint64_t complement_seed(int id, int64_t n_items) {
+  return 0x42485452495345ull ^ ((uint64_t)id << 40) ^ (uint64_t)n_items;
 }
 
 // Stage host data to the device when needed.
@@ -588,7 +639,7 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       const int id = C.node[ax];
       bool used = false;
       LTensor nxt = ttm_any(C, ax, st->U[id], 1, st->rank[id], st->rank[id], true, ar, s,
-                            step == 0 ? norm_acc : nullptr, &used);
+                            step == 0 && !ar.tight ? norm_acc : nullptr, &used);
       if (step == 0 && norm_done) *norm_done = used;
       C = std::move(nxt);
     }
@@ -772,6 +823,7 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
   st->precision = opts ? opts->precision : BHT_PREC_FP64;
   st->rank.assign(t.nodes.size(), 0);
   st->U.assign(t.nodes.size(), nullptr);
+  st->Q.assign(t.nodes.size(), nullptr);
   try {
     ck(cudaMalloc(&st->d_status, sizeof(int)), "cudaMalloc status");
     ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
@@ -807,6 +859,8 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
         double* U = eig_vectors64(eo[k], r, s);
         st->U[ids[k]] = U;
         st->rank[ids[k]] = r;
+        // kept for HT-RISE: the residual of a later batch lives in span(Q) (eq. compute_residual)
+        st->Q[ids[k]] = complement_of(U, n, r, complement_seed(ids[k], 0), st->d_status, s);
         Us.push_back(U);
         rs.push_back(r);
       }
@@ -869,7 +923,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   // Steps 2-3 layer by layer; the new cores live in a shadow copy until commit
   const double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
   std::vector<int64_t> rank = st->rank;
-  std::vector<double*> U = st->U;
+  std::vector<double*> U = st->U, Q = st->Q;
   std::vector<double*> fresh;  // buffers created by this call
   auto own = [&](double* p) { fresh.push_back(p); return p; };
   try {
@@ -878,51 +932,46 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
       std::vector<EigOut> eo(ids.size());
-      std::vector<int64_t> alpha(ids.size()), rold(ids.size());
+      std::vector<int64_t> alpha(ids.size()), rold(ids.size()), qc(ids.size());
       for (size_t k = 0; k < ids.size(); ++k) {
         const int ax = C.axis_of(ids[k]);
         const int64_t a = C.dims[ax];
         alpha[k] = a;
         rold[k] = rank[ids[k]];
-        // residual Gram R R^T with R = (I - U U^T) C_(j) (eq. compute_residual). A large node forms R from the
-        // data (two mode products and a difference); a small one forms Pi G Pi from its Gram matrix.
-        DBuf G(sizeof(double) * a * a, s);
-        if (a >= 256 && rold[k] > 0) {
-          const double* Uo = U[ids[k]];
-          LTensor W = ttm_any(C, ax, Uo, 1, rold[k], rold[k], false, ar, s);
-          LTensor P = ttm_any(W, ax, Uo, rold[k], 1, a, false, ar, s);
-          W = LTensor();
-          if (C.dtype == BHT_F32)
-            ck(launch_diff_inplace<float>(static_cast<const float*>(C.ptr), P.own.p, P.dtype, P.numel(), s), "R");
-          else
-            ck(launch_diff_inplace<double>(static_cast<const double*>(C.ptr), P.own.p, P.dtype, P.numel(), s), "R");
-          gram_any(P, ax, G.as<double>(), ar, s);
-          eig_tridiag64(G.as<double>(), a, eo[k], st->d_status, s);
-          continue;
-        }
-        DBuf Pi(sizeof(double) * a * a, s), H(sizeof(double) * a * a, s);
-        gram_any(C, ax, G.as<double>(), ar, s);
-        ck(launch_fill_identity(Pi.as<double>(), a, s), "identity");
-        ck(launch_gemm_f64(a, a, rold[k], -1.0, U[ids[k]], rold[k], 1, U[ids[k]], 1, rold[k], 1.0, Pi.as<double>(),
-                           a, 1, s),
-           "Pi = I - U U^T");
-        ck(launch_gemm_f64(a, a, a, 1.0, Pi.as<double>(), a, 1, G.as<double>(), a, 1, 0.0, H.as<double>(), a, 1, s),
-           "Pi G");
-        ck(launch_gemm_f64(a, a, a, 1.0, H.as<double>(), a, 1, Pi.as<double>(), a, 1, 0.0, G.as<double>(), a, 1, s),
-           "Pi G Pi");
-        eig_tridiag64(G.as<double>(), a, eo[k], st->d_status, s);
+        qc[k] = a - rold[k];
+        if (qc[k] <= 0) continue;  // U spans R^alpha: the residual vanishes
+        // residual R = (I - U U^T) C_(j) (eq. compute_residual). With Q the orthonormal complement of U,
+        // I - U U^T = Q Q^T, so R R^T = Q (W W^T) Q^T for W = Q^T C_(j): the nonzero eigenpairs of the
+        // residual Gram are those of the qc x qc Gram W W^T, mapped through Q.
+        LTensor W = ttm_any(C, ax, Q[ids[k]], 1, qc[k], qc[k], false, ar, s);
+        DBuf G(sizeof(double) * qc[k] * qc[k], s);
+        gram_any(W, ax, G.as<double>(), ar, s);
+        eig_tridiag64(G.as<double>(), qc[k], eo[k], st->d_status, s);
       }
       check_status(st, s);
       std::vector<int> grown_parents;
       for (size_t k = 0; k < ids.size(); ++k) {
         const int id = ids[k];
-        const int64_t a = alpha[k], r0 = rold[k];
+        const int64_t a = alpha[k], r0 = rold[k], c = qc[k];
+        if (c <= 0) continue;
         // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
-        const int64_t rR = eig_rank64(eo[k], eps_nw2, 0, std::max<int64_t>(a - r0, 0), s);
+        const int64_t rR = eig_rank64(eo[k], eps_nw2, 0, c, s);
         if (rR == 0) continue;
-        DBuf UR;
-        UR.p = eig_vectors64(eo[k], rR, s);
-        UR.s = s;
+        DBuf Zk;
+        Zk.p = eig_vectors64(eo[k], rR, s);  // [c][rR]
+        Zk.s = s;
+        DBuf UR(sizeof(double) * a * rR, s);
+        ck(launch_gemm_f64(a, rR, c, 1.0, Q[id], c, 1, Zk.as<double>(), rR, 1, 0.0, UR.as<double>(), rR, 1, s),
+           "U_R = Q Z");
+        // the complement shrinks to Q times the complement of Z inside R^c
+        double* Qn = own(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(a * (c - rR), 1), s)));
+        if (c > rR) {
+          DBuf Yc;
+          Yc.p = complement_of(Zk.as<double>(), c, rR, complement_seed(id, st->n_items), st->d_status, s);
+          Yc.s = s;
+          ck(launch_gemm_f64(a, c - rR, c, 1.0, Q[id], c, 1, Yc.as<double>(), c - rR, 1, 0.0, Qn, c - rR, 1, s),
+             "Q Y");
+        }
         DBuf W(sizeof(double) * r0 * rR + 8, s);
         // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)
         for (int pass = 0; pass < 2 && r0 > 0; ++pass) {
@@ -938,6 +987,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         if (r0 > 0) ck(launch_copy_cols(U[id], r0, a, r0, Un, rn, s), "expand old");
         ck(launch_copy_cols(UR.as<double>(), rR, a, rR, Un + r0, rn, s), "expand new");
         U[id] = Un;
+        Q[id] = Qn;
         rank[id] = rn;
         const int par = t.nodes[id].parent;
         if (par > 0 && std::find(grown_parents.begin(), grown_parents.end(), par) == grown_parents.end())
@@ -953,10 +1003,16 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
           if (ids[k] == c0) ra0 = rold[k];
           if (ids[k] == c1) rb0 = rold[k];
         }
-        const int64_t rp = rank[par];
-        double* Pn = own(static_cast<double*>(dalloc(sizeof(double) * rank[c0] * rank[c1] * rp, s)));
-        ck(launch_copy_pad3<double, double>(U[par], ra0, rb0, rp, Pn, rank[c0], rank[c1], rp, s), "pad parent");
+        const int64_t rp = rank[par], ra = rank[c0], rb = rank[c1];
+        double* Pn = own(static_cast<double*>(dalloc(sizeof(double) * ra * rb * rp, s)));
+        ck(launch_copy_pad3<double, double>(U[par], ra0, rb0, rp, Pn, ra, rb, rp, s), "pad parent");
         U[par] = Pn;
+        // the complement gains a unit vector for each new merged coordinate
+        const int64_t q0 = ra0 * rb0 - rp, q1 = ra * rb - rp;
+        double* Pq = own(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(ra * rb * q1, 1), s)));
+        ck(launch_copy_pad3<double, double>(Q[par], ra0, rb0, q0, Pq, ra, rb, q1, s), "pad complement");
+        ck(launch_unit_cols(Pq, q1, q0, ra0, rb0, ra, rb, s), "complement of new coordinates");
+        Q[par] = Pq;
       }
       // Step 1 revisited: project onto the updated cores of the layer
       std::vector<const double*> Us;
@@ -978,11 +1034,14 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
     throw;
   }
   // commit: release the replaced cores and any intermediate core superseded within this call
-  for (size_t id = 1; id < U.size(); ++id)
+  for (size_t id = 1; id < U.size(); ++id) {
     if (U[id] != st->U[id]) dfree(st->U[id], s);
+    if (Q[id] != st->Q[id]) dfree(st->Q[id], s);
+  }
   for (double* p : fresh)
-    if (std::find(U.begin(), U.end(), p) == U.end()) dfree(p, s);
+    if (std::find(U.begin(), U.end(), p) == U.end() && std::find(Q.begin(), Q.end(), p) == Q.end()) dfree(p, s);
   st->U = U;
+  st->Q = Q;
   st->rank = rank;
   st->n_items += N;
   ck(cudaStreamSynchronize(s), "sync");
@@ -1189,6 +1248,8 @@ bht_status bht_state_destroy(bht_state* st) {
   if (!st) return BHT_OK;
   cudaDeviceSynchronize();
   for (double* p : st->U)
+    if (p) cudaFreeAsync(p, nullptr);
+  for (double* p : st->Q)
     if (p) cudaFreeAsync(p, nullptr);
   if (st->root) cudaFreeAsync(st->root, nullptr);
   cudaDeviceSynchronize();

@@ -313,11 +313,41 @@ __global__ void cast_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, 
     out[i] = static_cast<Tout>(in[i]);
 }
 
-__global__ void scale_cols_invsqrt_kernel(double* __restrict__ W, int64_t k, const double* __restrict__ lam) {
-  const int64_t total = k * k;
+__global__ void scale_cols_invsqrt_kernel(double* __restrict__ W, int64_t rows, int64_t cols,
+                                          const double* __restrict__ lam) {
+  const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e % k;
-    W[e] *= rsqrt(fmax(lam[j], 1e-300));
+    const int64_t j = e % cols;
+    W[e] /= sqrt(fmax(lam[j], 1e-300));
+  }
+}
+
+// splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014) of seed + index, mapped to [-1, 1)
+__global__ void fill_uniform_kernel(double* __restrict__ X, int64_t n, uint64_t seed) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    X[e] = (double)(int64_t)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
+// Unit column for every coordinate j = i * rb + k of a grown merged index with i >= ra0 or k >= rb0,
+// numbered in C order from column col0: Q[j * ldq + col0 + idx(j)] = 1.
+__global__ void unit_cols_kernel(double* __restrict__ Q, int64_t ldq, int64_t col0, int64_t ra0, int64_t rb0,
+                                 int64_t ra, int64_t rb) {
+  const int64_t total = ra * rb;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = j / rb, k = j - i * rb;
+    int64_t idx;
+    if (i < ra0) {
+      if (k < rb0) continue;
+      idx = i * (rb - rb0) + (k - rb0);
+    } else {
+      idx = ra0 * (rb - rb0) + (i - ra0) * rb + k;
+    }
+    Q[j * ldq + col0 + idx] = 1.0;
   }
 }
 
@@ -325,13 +355,6 @@ __global__ void fill_identity_kernel(double* __restrict__ A, int64_t n) {
   const int64_t total = n * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     A[e] = (e / n == e % n) ? 1.0 : 0.0;
-}
-
-// y <- x - y, y of type Ty
-template <typename Tx, typename Ty>
-__global__ void diff_kernel(const Tx* __restrict__ x, Ty* __restrict__ y, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = static_cast<Ty>(static_cast<Ty>(x[i]) - y[i]);
 }
 
 __global__ void add_diag_kernel(double* __restrict__ A, int64_t n, double alpha) {
@@ -481,10 +504,27 @@ cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_cols_invsqrt(double* W, int64_t k, const double* lam, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
+cudaError_t launch_scale_cols_invsqrt(double* W, int64_t rows, int64_t cols, const double* lam, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
   ProfScope prof(K_COPY, s);
-  scale_cols_invsqrt_kernel<<<grid_for(k * k), 256, 0, s>>>(W, k, lam);
+  scale_cols_invsqrt_kernel<<<grid_for(rows * cols), 256, 0, s>>>(W, rows, cols, lam);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_uniform(double* X, int64_t n, uint64_t seed, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
+  fill_uniform_kernel<<<grid_for(n), 256, 0, s>>>(X, n, seed);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_cols(double* Q, int64_t ldq, int64_t col0, int64_t ra0, int64_t rb0, int64_t ra, int64_t rb,
+                             cudaStream_t s) {
+  if (ra * rb <= ra0 * rb0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
+  unit_cols_kernel<<<grid_for(ra * rb), 256, 0, s>>>(Q, ldq, col0, ra0, rb0, ra, rb);
   note_launch();
   return cudaGetLastError();
 }
@@ -497,19 +537,6 @@ cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename Tx>
-cudaError_t launch_diff_inplace(const Tx* x, void* y, int y_is_f64, int64_t n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  ProfScope prof(K_COPY, s, (double)n, (double)n * (sizeof(Tx) + 2 * (y_is_f64 ? 8 : 4)));
-  if (y_is_f64)
-    diff_kernel<Tx, double><<<grid_for(n), 256, 0, s>>>(x, static_cast<double*>(y), n);
-  else
-    diff_kernel<Tx, float><<<grid_for(n), 256, 0, s>>>(x, static_cast<float*>(y), n);
-  note_launch();
-  return cudaGetLastError();
-}
-template cudaError_t launch_diff_inplace<float>(const float*, void*, int, int64_t, cudaStream_t);
-template cudaError_t launch_diff_inplace<double>(const double*, void*, int, int64_t, cudaStream_t);
 
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -6,7 +6,7 @@
 // rank only needs all eigenvalues, and the node only needs the eigenvectors it
 // keeps, so the solver runs in two stages:
 //   stage 1  Householder tridiagonalisation Q^T G Q = T, then every eigenvalue
-//            of T by Sturm-sequence multisection (8 lanes, 16 points per round);
+//            of T by Sturm-sequence multisection (16 or 32 points per round);
 //   stage 2  (after the caller picked r) the eigenvectors of T for the r
 //            largest eigenvalues by twisted factorisation (one thread per
 //            cluster of nearly equal eigenvalues, modified Gram-Schmidt
@@ -193,106 +193,111 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Sturm-sequence bisection: every eigenvalue of the tridiagonal (d, e); one
-// thread per eigenvalue. lam is written in descending order.
+// Sturm-sequence multisection: every eigenvalue of the tridiagonal (d, e).
 // ---------------------------------------------------------------------------
-// Numbers of eigenvalues of T below xa and below xb: negative ratios q_i of
-// the LDL^T factorisations of T - x I. The ratios are carried as
-// p_i = q_i p_{i-1} (p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}), so a step
-// costs one multiply and one FMA instead of a division; p is rescaled by exact
-// powers of two to stay in range, and a ratio no larger than pivmin counts as
-// -pivmin. Two independent recurrences give the FP64 pipeline two chains.
-__device__ __forceinline__ void sturm_count2(const double* d, const double* e, int n, double xa, double xb,
-                                             double pivmin, int& ca, int& cb) {
-  constexpr double BIG = 0x1p+800, SMALL = 0x1p-800;
-  double a0 = 1.0, a1 = d[0] - xa, b0 = 1.0, b1 = d[0] - xb;
-  if (fabs(a1) <= pivmin) a1 = -pivmin;
-  if (fabs(b1) <= pivmin) b1 = -pivmin;
-  int na = a1 < 0.0, nb = b1 < 0.0;
-#pragma unroll 2
+// The number of eigenvalues of T below x is the number of negative ratios
+// q_i = p_i / p_{i-1} of the leading principal minors p_i of T - x I,
+// p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}. The minors are carried instead
+// of the ratios, so a step costs three FP64 operations (no division): FP64
+// issues at 1/64 of the FP32 rate on this part and dominates the sweep. The
+// sign test and the range test read the high word of p as an integer (sign
+// bit and exponent field), off the FP64 pipe. T arrives scaled by a power of
+// two so that |d_i|, |x| <= 2 and e_i^2 <= 4: one step grows |p| at most
+// 8-fold, and whenever |p_i| leaves [2^-500, 2^500] both carried minors are
+// rescaled by 2^-+500 (exact). An exactly zero minor becomes -2^-200 p_{i-1}:
+// a zero pivot counts as negative.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                           double x) {
+  double a0 = 1.0, a1 = d[0] - x;
+  if (a1 == 0.0) a1 = -0x1p-200;
+  int cnt = a1 < 0.0;
+#pragma unroll 4
   for (int i = 1; i < n; ++i) {
-    const double e2 = e[i - 1] * e[i - 1], di = d[i];
-    double ta = fma(-e2, a0, (di - xa) * a1);
-    double tb = fma(-e2, b0, (di - xb) * b1);
-    if (fabs(ta) <= pivmin * fabs(a1)) ta = -pivmin * a1;
-    if (fabs(tb) <= pivmin * fabs(b1)) tb = -pivmin * b1;
-    na += (ta < 0.0) != (a1 < 0.0);
-    nb += (tb < 0.0) != (b1 < 0.0);
+    double t = fma(d[i] - x, a1, -e2[i - 1] * a0);
+    const unsigned ex = ((unsigned)__double2hiint(t) >> 20) & 0x7FFu;
+    if (ex - (1023u - 500u) > 1000u) {  // exponent outside [-500, 500], zero or subnormal
+      if (t == 0.0) t = -0x1p-200 * a1;
+      const double f = fabs(t) > 1.0 ? 0x1p-500 : 0x1p+500;
+      if (fabs(t) > 0x1p+500 || fabs(t) < 0x1p-500) {
+        t *= f;
+        a1 *= f;
+      }
+    }
+    cnt += (__double2hiint(t) ^ __double2hiint(a1)) < 0;
     a0 = a1;
-    a1 = ta;
-    b0 = b1;
-    b1 = tb;
-    const double fa = fabs(a1), fb = fabs(b1);
-    if (fa > BIG) { a0 *= SMALL; a1 *= SMALL; } else if (fa < SMALL) { a0 *= BIG; a1 *= BIG; }
-    if (fb > BIG) { b0 *= SMALL; b1 *= SMALL; } else if (fb < SMALL) { b0 *= BIG; b1 *= BIG; }
+    a1 = t;
   }
-  ca = na;
-  cb = nb;
+  return cnt;
 }
 
-// MS_LANES lanes of one warp share an eigenvalue and evaluate 2 * MS_LANES
-// interior points of its interval per round (multisection): the interval
-// shrinks 17-fold per round and MS_LANES times more warps take part than with
-// plain bisection. Intervals stop at a relative width of 2 eps or an absolute
-// width of 1e-19 ||T||: eigenvalues below that only enter tail sums.
-constexpr int MS_LANES = 8;
-constexpr int MS_PTS = 2 * MS_LANES;
-
-// Eigenvalues with descending indices [j0, j1) (lam[j] = j-th largest).
-__global__ void bisect_kernel(const double* d, const double* e, int n, double* __restrict__ lam, int j0, int j1) {
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = j0 + gtid / MS_LANES;  // descending index
-  const int k = n - 1 - j;             // ascending index
-  const int g = gtid % MS_LANES;
-  const bool active = j < j1;
-  const int lane = threadIdx.x & 31;
-  const int base = (lane / MS_LANES) * MS_LANES;
-  // the Sturm sweeps are latency-bound: keep the tridiagonal in shared memory
+// L lanes share an eigenvalue and evaluate L interior points of its interval
+// per round (multisection): the interval shrinks (L + 1)-fold per round. An
+// interval stops at a width of 2 eps |lambda| or 4 eps ||T||: the
+// tridiagonalisation already perturbs every eigenvalue by about eps ||T||.
+template <int L>
+__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ dg, const double* __restrict__ eg,
+                                                     int n, double* __restrict__ lam, int j0, int j1) {
   extern __shared__ double tsm[];
-  double* sd = tsm;
-  double* se = tsm + n;
+  double* d = tsm;       // scaled diagonal
+  double* e2 = tsm + n;  // scaled squared off-diagonal
+  __shared__ double red_lo[4], red_hi[4];
+  // Gershgorin interval of T, block-wide
+  double gl = INFINITY, gu = -INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sd[i] = d[i];
-    se[i] = e[i];
+    const double r = (i > 0 ? fabs(eg[i - 1]) : 0.0) + (i + 1 < n ? fabs(eg[i]) : 0.0);
+    gl = fmin(gl, dg[i] - r);
+    gu = fmax(gu, dg[i] + r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+    gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_lo[threadIdx.x >> 5] = gl;
+    red_hi[threadIdx.x >> 5] = gu;
   }
   __syncthreads();
-  d = sd;
-  e = se;
-  double gl = d[0], gu = d[0], emax2 = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
-    gl = fmin(gl, d[i] - r);
-    gu = fmax(gu, d[i] + r);
-    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  gl = fmin(fmin(red_lo[0], red_lo[1]), fmin(red_lo[2], red_lo[3]));
+  gu = fmax(fmax(red_hi[0], red_hi[1]), fmax(red_hi[2], red_hi[3]));
+  const double tnorm = fmax(fmax(fabs(gl), fabs(gu)), DBL_MIN);
+  int ex = 0;
+  frexp(tnorm, &ex);
+  const double sc = ldexp(1.0, -ex);  // tnorm * sc in [0.5, 1)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = dg[i] * sc;
+    const double ei = (i + 1 < n) ? eg[i] * sc : 0.0;
+    e2[i] = ei * ei;
   }
-  const double pivmin = DBL_MIN * fmax(1.0, emax2);
-  const double tnorm = fmax(fabs(gl), fabs(gu));
-  const double abs_floor = 1e-19 * tnorm + 4.0 * pivmin;
-  gl -= 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
-  gu += 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
-  double lo = gl, hi = gu;
-  for (int it = 0; it < 40; ++it) {
+  __syncthreads();
+  const int sub = (threadIdx.x & 31) / L;                   // eigenvalue slot in the warp
+  const int g = threadIdx.x & (L - 1);                      // point of the multisection
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int j = j0 + warp_global * (32 / L) + sub;          // descending index
+  const int k = n - 1 - j;                                  // ascending index
+  const bool active = j < j1;
+  const double tn = tnorm * sc;
+  const double abs_floor = 4.0 * DBL_EPSILON * tn;
+  double lo = gl * sc - 2.0 * DBL_EPSILON * tn * n, hi = gu * sc + 2.0 * DBL_EPSILON * tn * n;
+  const unsigned gmask = (0xffffffffu >> (32 - L)) << (sub * L);
+  for (int it = 0; it < 64; ++it) {
     const bool done = !active || hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + abs_floor;
     if (__all_sync(0xffffffffu, done)) break;
-    const double step = (hi - lo) / (double)(MS_PTS + 1);
-    int ca = 0, cb = 0;
-    if (!done) sturm_count2(d, e, n, lo + step * (double)(2 * g + 1), lo + step * (double)(2 * g + 2), pivmin, ca, cb);
-    const unsigned balA = __ballot_sync(0xffffffffu, !done && ca > k);
-    const unsigned balB = __ballot_sync(0xffffffffu, !done && cb > k);
+    const double step = (hi - lo) / (double)(L + 1);
+    const double x = lo + step * (double)(g + 1);
+    const bool above = !done && sturm_count(d, e2, n, x) > k;
+    const unsigned bal = __ballot_sync(0xffffffffu, above) & gmask;
     if (!done) {
-      const unsigned ga = (balA >> base) & ((1u << MS_LANES) - 1u);
-      const unsigned gb = (balB >> base) & ((1u << MS_LANES) - 1u);
-      // point p = 2 g + 1 + (0: A, 1: B); counts grow with x, so the points above form a suffix
-      int first = MS_PTS;
-      if (ga) first = 2 * (__ffs(ga) - 1);
-      if (gb) first = min(first, 2 * (__ffs(gb) - 1) + 1);
+      // counts grow with x, so the points above eigenvalue k form a suffix
+      const unsigned mine = bal >> (sub * L);
+      const int first = mine ? __ffs(mine) - 1 : L;  // first point above
       const double nlo = (first == 0) ? lo : lo + step * (double)first;
-      const double nhi = (first == MS_PTS) ? hi : lo + step * (double)(first + 1);
+      const double nhi = (first == L) ? hi : lo + step * (double)(first + 1);
       lo = nlo;
       hi = nhi;
     }
   }
-  if (active && g == 0) lam[j] = 0.5 * (lo + hi);
+  if (active && g == 0) lam[j] = 0.5 * (lo + hi) / sc;
 }
 
 // ---------------------------------------------------------------------------
@@ -471,21 +476,31 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
   return e;
 }
 
+template <int L>
+cudaError_t launch_bisect_l(int64_t n, const double* d, const double* e, double* lam, int64_t j0, int64_t j1,
+                            cudaStream_t s) {
+  const size_t sm = 2 * sizeof(double) * (size_t)n;
+  if (sm > 48 * 1024) {
+    cudaError_t e2 = cudaFuncSetAttribute(bisect_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e2 != cudaSuccess) return e2;
+  }
+  const int64_t per_block = 128 / L;  // eigenvalues per 128-thread CTA
+  const int64_t blocks = (j1 - j0 + per_block - 1) / per_block;
+  // algorithmic work: 3 FP64 operations per Sturm step, about 53 / log2(L + 1) rounds of L points
+  ProfScope prof(K_EIG_BISECT, s, 3.0 * (double)n * (double)L * (53.0 / std::log2((double)L + 1.0)) * (double)(j1 - j0),
+                 16.0 * (double)n);
+  bisect_kernel<L><<<(unsigned)blocks, 128, sm, s>>>(d, e, (int)n, lam, (int)j0, (int)j1);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eig_bisect(int64_t n, void* work, double* lam, int64_t j0, int64_t j1, cudaStream_t s) {
   if (n <= 0 || j1 <= j0) return cudaSuccess;
   WorkLayout L = layout(work, n);
-  const int64_t threads = (j1 - j0) * MS_LANES;  // small blocks spread the warps over every SM
-  // algorithmic work: about 3 FP64 operations per Sturm step, 53 / log2(G + 1) rounds of G counts
-  ProfScope prof(K_EIG_BISECT, s, 4.0 * (double)n * (double)MS_PTS * 14.0 * (double)(j1 - j0), 16.0 * (double)n);
-  const int bt = 64;
-  const size_t sm = 2 * sizeof(double) * (size_t)n;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  bisect_kernel<<<(unsigned)((threads + bt - 1) / bt), bt, sm, s>>>(L.d, L.e, (int)n, lam, (int)j0, (int)j1);
-  note_launch();
-  return cudaGetLastError();
+  // 16 points per eigenvalue once there are enough eigenvalues to give every SM sub-partition a warp,
+  // 32 below that (fewer rounds)
+  if (j1 - j0 >= 512) return launch_bisect_l<16>(n, L.d, L.e, lam, j0, j1, s);
+  return launch_bisect_l<32>(n, L.d, L.e, lam, j0, j1, s);
 }
 
 const double* eig_tridiag_diagonal(void* work, int64_t n) { return layout(work, n).d; }

@@ -104,8 +104,16 @@ cudaError_t launch_copy_cols(const double* in, int64_t ld_in, int64_t rows, int6
 template <typename Tin, typename Tout>
 cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s);
 
-// Symmetric orthonormalisation helper: W (k x k) <- W * diag(1/sqrt(max(lam, tiny)))
-cudaError_t launch_scale_cols_invsqrt(double* W, int64_t k, const double* lam, cudaStream_t s);
+// W (rows x cols, row-major) <- W * diag(1/sqrt(max(lam, tiny)))
+cudaError_t launch_scale_cols_invsqrt(double* W, int64_t rows, int64_t cols, const double* lam, cudaStream_t s);
+
+// X[e] <- uniform in [-1, 1) from a counter-based hash of (seed, e); deterministic
+cudaError_t launch_fill_uniform(double* X, int64_t n, uint64_t seed, cudaStream_t s);
+
+// Q[j * ldq + col0 + idx(j)] = 1 for the coordinates j = i * rb + k of a merged index grown from
+// ra0 x rb0 to ra x rb that are new (i >= ra0 or k >= rb0), idx numbering them in C order.
+cudaError_t launch_unit_cols(double* Q, int64_t ldq, int64_t col0, int64_t ra0, int64_t rb0, int64_t ra, int64_t rb,
+                             cudaStream_t s);
 
 // A (n x n) <- identity
 cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s);
@@ -151,10 +159,6 @@ cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_
                                    int nb, cudaStream_t s);
 cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
                           int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s);
-
-// y <- x - y elementwise; y is FP64 when y_is_f64 (the dtype code BHT_F64 = 1), else fp32
-template <typename Tx>
-cudaError_t launch_diff_inplace(const Tx* x, void* y, int y_is_f64, int64_t n, cudaStream_t s);
 
 // A (n x n) += alpha I
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s);

@@ -279,6 +279,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
         }
         const float4* src = reinterpret_cast<const float4*>(base + (size_t)slot * slot_bytes);
         float4* dst = reinterpret_cast<float4*>(base + (size_t)slot * slot_bytes + CHUNK_BYTES);
+        // ||X||^2: four FP32 partial sums of CHUNK_BYTES / 1024 squares each per chunk, folded into FP64
+        // once per chunk (FP64 issues at 1/64 of the FP32 rate on this part)
+        float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int q = tid; q < CHUNK_BYTES / 16; q += 64) {
           const float4 x = src[q];
           float4 l;
@@ -287,8 +290,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
           l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
           l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
           dst[q] = l;
-          if (count) sq += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+          part.x = fmaf(x.x, x.x, part.x);
+          part.y = fmaf(x.y, x.y, part.y);
+          part.z = fmaf(x.z, x.z, part.z);
+          part.w = fmaf(x.w, x.w, part.w);
         }
+        if (count) sq += ((double)part.x + (double)part.y) + ((double)part.z + (double)part.w);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&ready[slot]);
@@ -322,14 +329,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * P.S_tile + c0, v);
         if (valid) {
+          float part = 0.f;  // 16 squares in FP32, folded into FP64 once
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int s = s0 + c0 + j;
             if (s < P.S) {
               dst[(int64_t)s * P.R2] = v[j];
-              sq += (double)v[j] * v[j];
+              part = fmaf(v[j], v[j], part);
             }
           }
+          if (P.norm_out) sq += (double)part;
         }
       }
       fence_before();

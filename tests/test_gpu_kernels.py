@@ -63,5 +63,6 @@ def test_tensor_core_mode_product(B, rows, K, S, R2):
     bias = (np.linalg.norm(out) ** 2 - np.linalg.norm(ref) ** 2) / np.linalg.norm(ref) ** 2
     assert abs(bias) < 1e-5, bias                        # no truncation or rounding bias in the norm
     n = norms.cpu().numpy()
-    assert abs(n[0] - np.sum(X.astype(np.float64) ** 2)) <= 1e-9 * n[0]
+    # ||X||^2: FP32 partial sums of 16 squares folded into FP64, so at most 16 * 2^-24 relative
+    assert abs(n[0] - np.sum(X.astype(np.float64) ** 2)) <= 16 * 2.0 ** -24 * n[0]
     assert abs(n[1] - np.sum(out ** 2)) <= 1e-6 * n[1]

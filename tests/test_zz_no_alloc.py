@@ -37,7 +37,8 @@ def test_noalloc_matches_allocating_entry_point_twice(B):
         assert np.isfinite(a).all()
         assert np.linalg.norm(a - b) <= 2e-5 * np.linalg.norm(b)
         n = norms.cpu().numpy()
-        assert abs(n[0] - float(torch.sum(X.double() ** 2))) <= 1e-9 * n[0]
+        # ||X||^2 from FP32 partial sums of 16 squares folded into FP64: at most 16 * 2^-24 relative
+        assert abs(n[0] - float(torch.sum(X.double() ** 2))) <= 16 * 2.0 ** -24 * n[0]
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(B):
