@@ -11,6 +11,8 @@
 // GB300 has few FP64 units (≈1/64 of the FP32 rate), so these kernels are
 // FP64-ALU bound; they are the reference GPU form the mixed path is measured
 // against.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace bht {
@@ -185,11 +187,13 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
 // ---------------------------------------------------------------------------
 // Generic small FP64 GEMM with strided operands
 // ---------------------------------------------------------------------------
+// grid.z splits K into chunks of kchunk; with more than one chunk every CTA adds alpha * its partial
+// product to C atomically (C was scaled by beta beforehand).
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                       const double* __restrict__ Am, int64_t a_rs, int64_t a_cs,
                                                       const double* __restrict__ Bm, int64_t b_rs, int64_t b_cs,
                                                       double beta, double* __restrict__ C, int64_t c_rs,
-                                                      int64_t c_cs) {
+                                                      int64_t c_cs, int64_t kchunk) {
   __shared__ double As[BK][TILE + 1];
   __shared__ double Bs[BK][TILE + 1];
   const int64_t m0 = (int64_t)blockIdx.y * TILE, n0 = (int64_t)blockIdx.x * TILE;
@@ -201,7 +205,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int6
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
   const bool a_along_m = (a_rs == 1);
   const bool b_along_n = (b_cs == 1);
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  K = min(K, kbeg + kchunk);
+  for (int64_t k0 = kbeg; k0 < K; k0 += BK) {
     for (int e = threadIdx.x; e < BK * TILE; e += NT) {
       int kk, mm;
       if (a_along_m) { mm = e % TILE; kk = e / TILE; } else { kk = e % BK; mm = e / BK; }
@@ -238,7 +244,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int6
       const int64_t n = n0 + tx + 16 * v;
       if (n >= N) continue;
       double* cp = C + m * c_rs + n * c_cs;
-      *cp = (beta == 0.0) ? alpha * acc[u][v] : alpha * acc[u][v] + beta * (*cp);
+      if (gridDim.z > 1)
+        atomicAdd(cp, alpha * acc[u][v]);
+      else
+        *cp = (beta == 0.0) ? alpha * acc[u][v] : alpha * acc[u][v] + beta * (*cp);
     }
   }
 }
@@ -348,6 +357,15 @@ __global__ void unit_cols_kernel(double* __restrict__ Q, int64_t ldq, int64_t co
       idx = ra0 * (rb - rb0) + (i - ra0) * rb + k;
     }
     Q[j * ldq + col0 + idx] = 1.0;
+  }
+}
+
+__global__ void scale_strided_kernel(double* __restrict__ C, int64_t M, int64_t N, int64_t c_rs, int64_t c_cs,
+                                     double beta) {
+  const int64_t total = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    double* cp = C + (e / N) * c_rs + (e % N) * c_cs;
+    *cp = (beta == 0.0) ? 0.0 : beta * (*cp);
   }
 }
 
@@ -467,10 +485,26 @@ cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const
                             int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
                             int64_t c_rs, int64_t c_cs, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((M + TILE - 1) / TILE));
+  const int64_t gx = (N + TILE - 1) / TILE, gy = (M + TILE - 1) / TILE;
+  // FP64 issues at two FMA per clock per SM here: a grid smaller than two CTAs per SM splits K
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t splits = 1, kchunk = std::max<int64_t>(K, 1);
+  if (gx * gy < 2 * (int64_t)nsm && K > 2 * BK) {
+    splits = std::min<int64_t>((2 * nsm + gx * gy - 1) / (gx * gy), (K + 4 * BK - 1) / (4 * BK));
+    kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    splits = (K + kchunk - 1) / kchunk;
+  }
   ProfScope prof(K_GEMM_F64, s, 2.0 * (double)M * (double)N * (double)K,
                  8.0 * ((double)M * (double)K + (double)K * (double)N + (double)M * (double)N));
-  gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs);
+  if (splits > 1) {
+    scale_strided_kernel<<<grid_for(M * N), 256, 0, s>>>(C, M, N, c_rs, c_cs, beta);
+    note_launch();
+  }
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)splits);
+  gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs,
+                                      kchunk);
   note_launch();
   return cudaGetLastError();
 }

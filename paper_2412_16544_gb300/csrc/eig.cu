@@ -12,9 +12,10 @@
 //            cluster of nearly equal eigenvalues, modified Gram-Schmidt
 //            inside a cluster), then the back-transformation U = Q Z.
 // GB300 has few FP64 units (about 2 FMA per clock per SM), so every stage is
-// spread over the whole GPU: the tridiagonalisation of a large matrix is one
-// cooperative grid with a bounded grid barrier between its phases; small
-// matrices (n <= 96) use one CTA each.
+// spread over the whole GPU: the tridiagonalisation keeps the matrix rows in
+// the shared memory of one cooperative grid (one CTA for n <= 96) with one
+// bounded grid barrier per column; matrices too large for that fall back to a
+// global-memory form with two barriers per column.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -188,6 +189,152 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
     }
     d[n - 1] = A[(int64_t)(n - 1) * n + (n - 1)];
     e[n - 1] = 0.0;
+    tau[n - 1] = 0.0;
+  }
+}
+
+// Householder reflector of x[0..m) (m >= 2), computed by every thread of the
+// block: v[0] = 1, v[j] = x[j] / (x[0] - beta), tau = (beta - x[0]) / beta,
+// H x = beta e_1. Returns tau; *beta_out receives beta. x and v in shared memory.
+__device__ double householder(const double* x, int m, double* v, double* red, double* beta_out) {
+  double s = 0.0;
+  for (int j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(x[j], x[j], s);
+  const double xn2 = block_sum(s, red);
+  const double alpha = x[0];
+  double t = 0.0, beta = alpha, scale = 0.0;
+  if (xn2 > 0.0) {
+    beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) v[j] = (j == 0) ? 1.0 : (t != 0.0 ? x[j] * scale : 0.0);
+  *beta_out = beta;
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation with the matrix resident in shared memory.
+// Row gi belongs to CTA gi % gridDim.x (slot gi / gridDim.x) for the whole
+// reduction, so the rank-2 updates and matrix-vector products never leave the
+// SM. One grid barrier per column: after it every CTA holds p_t = tau A22 v_t
+// and row t+1 as it was before update t (published by its owner), and itself
+// forms w_t, the updated column t+1 and the next reflector v_{t+1}; then one
+// pass over its rows applies update t and accumulates p_{t+1} at once.
+// p and the published row alternate between two buffers by column parity.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double* __restrict__ A, int n, int rpb,
+                                                                   double* __restrict__ Vh, double* __restrict__ d,
+                                                                   double* __restrict__ e, double* __restrict__ tau,
+                                                                   double* __restrict__ pbuf, double* __restrict__ pub,
+                                                                   Barrier* bar, int* status) {
+  extern __shared__ double sm[];
+  double* rows = sm;                         // rpb x n
+  double* vb[2] = {rows + (size_t)rpb * n, rows + (size_t)(rpb + 1) * n};
+  double* w = rows + (size_t)(rpb + 2) * n;  // n
+  double* x = rows + (size_t)(rpb + 3) * n;  // n
+  __shared__ double red[33];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = 0; l < rpb; ++l) {
+    const int gi = b + l * nb;
+    if (gi >= n) break;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) rows[(size_t)l * n + j] = A[(size_t)gi * n + j];
+  }
+  // column 0: reflector from row 0, p_0 from the own rows
+  for (int j = threadIdx.x; j < n - 1; j += blockDim.x) x[j] = A[j + 1];
+  __syncthreads();
+  double beta = 0.0;
+  double tc = householder(x, n - 1, vb[0], red, &beta);
+  if (b == 0) {
+    for (int j = threadIdx.x; j < n - 1; j += blockDim.x) Vh[j] = vb[0][j];
+    if (threadIdx.x == 0) {
+      d[0] = A[0];
+      e[0] = beta;
+      tau[0] = tc;
+    }
+  }
+  for (int l = warp; l < rpb; l += nw) {
+    const int gi = b + l * nb;
+    if (gi < 1 || gi >= n) continue;
+    const double* r = rows + (size_t)l * n;
+    double dot = 0.0;
+    for (int c = 1 + lane; c < n; c += 32) dot = fma(r[c], vb[0][c - 1], dot);
+    dot = warp_sum(dot);
+    if (lane == 0) pbuf[gi - 1] = tc * dot;
+    if (gi == 1)
+      for (int c = 1 + lane; c < n; c += 32) pub[n + c] = r[c];
+  }
+  if (!grid_barrier(bar, status)) return;
+
+  for (int t = 0; t + 2 < n; ++t) {
+    const int m = n - t - 1;  // length of v_t; index q <-> column t + 1 + q
+    const double* v = vb[t & 1];
+    double* vn = vb[(t + 1) & 1];
+    const double* p = pbuf + (size_t)(t & 1) * n;
+    const double* R = pub + (size_t)((t + 1) & 1) * n;  // row t + 1 before update t
+    // w_t = p - (tau/2)(p.v) v
+    double pv = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+      const double pq = p[q];
+      w[q] = pq;
+      pv = fma(pq, v[q], pv);
+    }
+    const double Kc = 0.5 * tc * block_sum(pv, red);
+    for (int q = threadIdx.x; q < m; q += blockDim.x) w[q] -= Kc * v[q];
+    __syncthreads();
+    // column t + 1 after update t: x[c - t - 2] for columns c >= t + 2
+    const int m1 = m - 1;
+    for (int q = 1 + threadIdx.x; q < m; q += blockDim.x) x[q - 1] = R[t + 1 + q] - (w[q] + w[0] * v[q]);
+    __syncthreads();
+    const double dnext = R[t + 1] - 2.0 * w[0];
+    double tn = 0.0;
+    if (m1 >= 2) {
+      tn = householder(x, m1, vn, red, &beta);
+    } else {
+      beta = x[0];
+      if (threadIdx.x == 0) vn[0] = 1.0;
+      __syncthreads();
+    }
+    if (b == 0) {
+      if (m1 >= 2)
+        for (int j = threadIdx.x; j < m1; j += blockDim.x) Vh[(size_t)(t + 1) * n + j] = vn[j];
+      if (threadIdx.x == 0) {
+        d[t + 1] = dnext;
+        e[t + 1] = beta;
+        tau[t + 1] = tn;
+      }
+    }
+    // update t on the own rows gi >= t + 2, with p_{t+1} from the updated entries
+    double* pn = pbuf + (size_t)((t + 1) & 1) * n;
+    double* Rn = pub + (size_t)(t & 1) * n;  // row t + 2 after update t
+    for (int l = warp; l < rpb; l += nw) {
+      const int gi = b + l * nb;
+      if (gi < t + 2 || gi >= n) continue;
+      double* r = rows + (size_t)l * n;
+      const int ig = gi - t - 1;
+      const double vi = v[ig], wi = w[ig];
+      const bool publish = (gi == t + 2);
+      double dot = 0.0;
+      for (int q = 1 + lane; q < m; q += 32) {
+        const int c = t + 1 + q;
+        const double a = r[c] - (vi * w[q] + wi * v[q]);
+        r[c] = a;
+        dot = fma(a, vn[q - 1], dot);
+        if (publish) Rn[c] = a;
+      }
+      if (m1 >= 2) {
+        dot = warp_sum(dot);
+        if (lane == 0) pn[gi - t - 2] = tn * dot;
+      }
+      if (gi == n - 1 && m1 < 2 && lane == 0) d[n - 1] = r[n - 1];
+    }
+    tc = tn;
+    if (!grid_barrier(bar, status)) return;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    e[n - 1] = 0.0;
+    tau[n - 2] = 0.0;
     tau[n - 1] = 0.0;
   }
 }
@@ -412,7 +559,7 @@ __global__ void __launch_bounds__(EIG_THREADS) backtransform_kernel(const double
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct WorkLayout {
-  double *Vh, *d, *e, *tau, *pbuf;
+  double *Vh, *d, *e, *tau, *pbuf, *pub;
   Barrier* bar;
 };
 
@@ -428,7 +575,9 @@ WorkLayout layout(void* work, int64_t n) {
   L.tau = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * n);
   L.pbuf = reinterpret_cast<double*>(p);
-  p += align256(sizeof(double) * n);
+  p += align256(sizeof(double) * 2 * n);
+  L.pub = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * 2 * n);
   L.bar = reinterpret_cast<Barrier*>(p);
   return L;
 }
@@ -436,7 +585,8 @@ WorkLayout layout(void* work, int64_t n) {
 }  // namespace
 
 size_t eig_workspace_bytes(int64_t n) {
-  return align256(sizeof(double) * n * n) + 4 * align256(sizeof(double) * n) + 256;
+  return align256(sizeof(double) * n * n) + 3 * align256(sizeof(double) * n) + 2 * align256(sizeof(double) * 2 * n) +
+         256;
 }
 
 size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 5 * (size_t)n * (size_t)r + 256; }
@@ -453,15 +603,46 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
     if (e != cudaSuccess) return e;
   }
   const double flops = 4.0 / 3.0 * (double)n * (double)n * (double)n;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (n >= 3) {
+    // rows resident in shared memory: one CTA for a small matrix, else about one warp per row
+    // (at least ceil(n / #SM) rows per CTA, at most one CTA per SM)
+    const int warps = EIG_THREADS / 32;
+    const int rpb = n <= SMALL_N ? (int)n : (int)std::max<int64_t>(warps, (n + nsm - 1) / nsm);
+    const int nbk = (int)((n + rpb - 1) / rpb);
+    const size_t smr = sizeof(double) * (size_t)(rpb + 4) * (size_t)n;
+    if (smr <= 200 * 1024) {
+      if (smr > 48 * 1024) {
+        e = cudaFuncSetAttribute(tridiag_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        if (e != cudaSuccess) return e;
+      }
+      ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+      int nn = (int)n, r = rpb;
+      const double* Gc = G;
+      if (nbk == 1) {
+        tridiag_rows_kernel<<<1, EIG_THREADS, smr, s>>>(Gc, nn, r, L.Vh, L.d, L.e, L.tau, L.pbuf, L.pub, L.bar,
+                                                         status);
+        note_launch();
+        return cudaGetLastError();
+      }
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_rows_kernel, EIG_THREADS, smr);
+      if (e != cudaSuccess) return e;
+      if ((int64_t)per_sm * nsm >= nbk) {
+        void* args[] = {&Gc, &nn, &r, &L.Vh, &L.d, &L.e, &L.tau, &L.pbuf, &L.pub, &L.bar, &status};
+        e = cudaLaunchCooperativeKernel((void*)tridiag_rows_kernel, dim3(nbk), dim3(EIG_THREADS), args, smr, s);
+        note_launch();
+        return e;
+      }
+    }
+  }
   if (n <= SMALL_N) {
     ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
     tridiag_kernel<<<1, EIG_THREADS, sm, s>>>(G, (int)n, L.Vh, L.d, L.e, L.tau, L.pbuf, L.bar, status);
     note_launch();
     return cudaGetLastError();
   }
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, EIG_THREADS, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
