@@ -536,6 +536,43 @@ void newton_schulz(double* X, int64_t rows, int64_t r, cudaStream_t s, int iters
   }
 }
 
+double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_t s);
+
+// Estimate of ||X^T X - I||_2 for X (rows x r): four power steps on E = X^T X - I from a
+// pseudo-random start, each two matrix-vector products (the ratio of the last two iterates).
+double orth_error(const double* X, int64_t rows, int64_t r, cudaStream_t s) {
+  if (r <= 0) return 0.0;
+  DBuf v(sizeof(double) * 2 * r, s), y(sizeof(double) * rows, s), acc(sizeof(double) * 2, s);
+  double* x = v.as<double>();
+  double* z = x + r;
+  ck(launch_fill_uniform(x, r, 0x6f727468ull, s), "probe");
+  for (int it = 0; it < 4; ++it) {
+    if (it == 3) sqnorm_of(x, BHT_F64, r, acc.as<double>(), s);
+    ck(launch_gemm_f64(rows, 1, r, 1.0, X, r, 1, x, 1, 1, 0.0, y.as<double>(), 1, 1, s), "X x");
+    ck(cudaMemcpyAsync(z, x, sizeof(double) * r, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(launch_gemm_f64(r, 1, rows, 1.0, X, 1, r, y.as<double>(), 1, 1, -1.0, z, 1, 1, s), "X^T y - x");
+    std::swap(x, z);
+  }
+  sqnorm_of(x, BHT_F64, r, acc.as<double>() + 1, s);
+  double h[2];
+  ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H probe");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (!(h[0] > 0.0)) return h[1] > 0.0 ? 1.0 : 0.0;
+  return std::sqrt(h[1] / h[0]);
+}
+
+// Newton-Schulz steps until the estimated orthonormality error is below 1e-12 (none when the
+// columns already are orthonormal to that level; at most max_iters).
+void orthonormalise(double* X, int64_t rows, int64_t r, cudaStream_t s, int max_iters) {
+  double e = orth_error(X, rows, r, s);
+  int iters = 0;
+  while (e > 1e-12 && iters < max_iters) {
+    e = 0.75 * e * e + 1e-16;
+    ++iters;
+  }
+  newton_schulz(X, rows, r, s, iters);
+}
+
 // Stage 2: orthonormal eigenvectors of the r largest eigenvalues, [n][r] row-major, owned by the caller.
 double* eig_vectors64(EigOut& eo, int64_t r, cudaStream_t s) {
   const int64_t n = eo.n;
@@ -543,7 +580,7 @@ double* eig_vectors64(EigOut& eo, int64_t r, cudaStream_t s) {
   if (r == 0) return U;
   DBuf scratch(eig_vectors_scratch_bytes(n, r), s);
   ck(launch_eig_vectors(n, r, eo.lam.as<double>(), U, eo.work.p, scratch.p, s), "eigenvectors");
-  newton_schulz(U, n, r, s);
+  orthonormalise(U, n, r, s, 3);
   return U;
 }
 
@@ -593,7 +630,7 @@ double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int*
     ck(launch_gemm_f64(n, c, k, 1.0, X.as<double>(), k, 1, Z.as<double>(), c, 1, 0.0, Q, c, 1, s), "X Z");
     ck(launch_gemm_f64(r, c, n, 1.0, V, 1, r, Q, c, 1, 0.0, W.as<double>(), c, 1, s), "V^T Q");
     ck(launch_gemm_f64(n, c, r, -1.0, V, r, 1, W.as<double>(), c, 1, 1.0, Q, c, 1, s), "Q -= V W");
-    newton_schulz(Q, n, c, s, 2);
+    orthonormalise(Q, n, c, s, 3);
     check_status_word(d_status, s);
   } catch (...) {
     dfree(Q, s);
@@ -980,7 +1017,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
           ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, s),
              "U_R -= U W");
         }
-        newton_schulz(UR.as<double>(), a, rR, s, 2);
+        orthonormalise(UR.as<double>(), a, rR, s, 3);
         // expandCore: U^k = [U^{k-1}, U_R] (eq. concatenating_orthonormal_vectors)
         const int64_t rn = r0 + rR;
         double* Un = own(static_cast<double*>(dalloc(sizeof(double) * a * rn, s)));

@@ -185,62 +185,67 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
 }
 
 // ---------------------------------------------------------------------------
-// Generic small FP64 GEMM with strided operands
-// ---------------------------------------------------------------------------
-// grid.z splits K into chunks of kchunk; with more than one chunk every CTA adds alpha * its partial
+// Generic FP64 GEMM with strided operands. FP64 issues at about two FMA per
+// clock per SM on this part, so the tile edge follows the output size (64, 32
+// or 16, 256 threads each with (TE/16)^2 outputs) and K is split across CTAs
+// until the grid covers every SM several times; grid.z splits K into chunks of
+// kchunk and, with more than one chunk, every CTA adds alpha * its partial
 // product to C atomically (C was scaled by beta beforehand).
+// ---------------------------------------------------------------------------
+template <int TE>
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                       const double* __restrict__ Am, int64_t a_rs, int64_t a_cs,
                                                       const double* __restrict__ Bm, int64_t b_rs, int64_t b_cs,
                                                       double beta, double* __restrict__ C, int64_t c_rs,
                                                       int64_t c_cs, int64_t kchunk) {
-  __shared__ double As[BK][TILE + 1];
-  __shared__ double Bs[BK][TILE + 1];
-  const int64_t m0 = (int64_t)blockIdx.y * TILE, n0 = (int64_t)blockIdx.x * TILE;
+  constexpr int R = TE / 16;  // outputs per thread along each edge
+  __shared__ double As[BK][TE + 1];
+  __shared__ double Bs[BK][TE + 1];
+  const int64_t m0 = (int64_t)blockIdx.y * TE, n0 = (int64_t)blockIdx.x * TE;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < R; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < R; ++v) acc[u][v] = 0.0;
   const bool a_along_m = (a_rs == 1);
   const bool b_along_n = (b_cs == 1);
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   K = min(K, kbeg + kchunk);
   for (int64_t k0 = kbeg; k0 < K; k0 += BK) {
-    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+    for (int e = threadIdx.x; e < BK * TE; e += NT) {
       int kk, mm;
-      if (a_along_m) { mm = e % TILE; kk = e / TILE; } else { kk = e % BK; mm = e / BK; }
+      if (a_along_m) { mm = e % TE; kk = e / TE; } else { kk = e % BK; mm = e / BK; }
       const int64_t k = k0 + kk, m = m0 + mm;
       As[kk][mm] = (k < K && m < M) ? Am[m * a_rs + k * a_cs] : 0.0;
     }
-    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
+    for (int e = threadIdx.x; e < BK * TE; e += NT) {
       int kk, nn;
-      if (b_along_n) { nn = e % TILE; kk = e / TILE; } else { kk = e % BK; nn = e / BK; }
+      if (b_along_n) { nn = e % TE; kk = e / TE; } else { kk = e % BK; nn = e / BK; }
       const int64_t k = k0 + kk, n = n0 + nn;
       Bs[kk][nn] = (k < K && n < N) ? Bm[k * b_rs + n * b_cs] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+      for (int u = 0; u < R; ++u) a[u] = As[kk][ty + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+      for (int v = 0; v < R; ++v) b[v] = Bs[kk][tx + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < R; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < R; ++u) {
     const int64_t m = m0 + ty + 16 * u;
     if (m >= M) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < R; ++v) {
       const int64_t n = n0 + tx + 16 * v;
       if (n >= N) continue;
       double* cp = C + m * c_rs + n * c_cs;
@@ -249,6 +254,21 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(int64_t M, int64_t N, int6
       else
         *cp = (beta == 0.0) ? alpha * acc[u][v] : alpha * acc[u][v] + beta * (*cp);
     }
+  }
+}
+
+// y(m) = alpha sum_k A(m, k) x(k) + beta y(m): one warp per output row.
+__global__ void gemv_f64_kernel(int64_t M, int64_t K, double alpha, const double* __restrict__ Am, int64_t a_rs,
+                                int64_t a_cs, const double* __restrict__ x, int64_t x_s, double beta,
+                                double* __restrict__ y, int64_t y_s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += nw) {
+    double dot = 0.0;
+    for (int64_t k = lane; k < K; k += 32) dot = fma(Am[m * a_rs + k * a_cs], x[k * x_s], dot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if (lane == 0) y[m * y_s] = (beta == 0.0) ? alpha * dot : alpha * dot + beta * y[m * y_s];
   }
 }
 
@@ -481,32 +501,52 @@ cudaError_t launch_trace(const double* G, int64_t n, double* acc, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
-                            int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
-                            int64_t c_rs, int64_t c_cs, cudaStream_t s) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  const int64_t gx = (N + TILE - 1) / TILE, gy = (M + TILE - 1) / TILE;
-  // FP64 issues at two FMA per clock per SM here: a grid smaller than two CTAs per SM splits K
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+template <int TE>
+cudaError_t launch_gemm_tiles(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
+                              int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
+                              int64_t c_rs, int64_t c_cs, int nsm, cudaStream_t s) {
+  const int64_t gx = (N + TE - 1) / TE, gy = (M + TE - 1) / TE;
   int64_t splits = 1, kchunk = std::max<int64_t>(K, 1);
-  if (gx * gy < 2 * (int64_t)nsm && K > 2 * BK) {
-    splits = std::min<int64_t>((2 * nsm + gx * gy - 1) / (gx * gy), (K + 4 * BK - 1) / (4 * BK));
+  if (gx * gy < 4 * (int64_t)nsm && K > 2 * BK) {
+    splits = std::min<int64_t>((4 * nsm + gx * gy - 1) / (gx * gy), (K + 2 * BK - 1) / (2 * BK));
     kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
     splits = (K + kchunk - 1) / kchunk;
   }
-  ProfScope prof(K_GEMM_F64, s, 2.0 * (double)M * (double)N * (double)K,
-                 8.0 * ((double)M * (double)K + (double)K * (double)N + (double)M * (double)N));
   if (splits > 1) {
     scale_strided_kernel<<<grid_for(M * N), 256, 0, s>>>(C, M, N, c_rs, c_cs, beta);
     note_launch();
   }
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)splits);
-  gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs,
-                                      kchunk);
+  gemm_f64_kernel<TE><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)splits), NT, 0, s>>>(
+      M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs, kchunk);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
+                            int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
+                            int64_t c_rs, int64_t c_cs, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  ProfScope prof(K_GEMM_F64, s, 2.0 * (double)M * (double)N * (double)K,
+                 8.0 * ((double)M * (double)K + (double)K * (double)N + (double)M * (double)N));
+  if (N == 1 || M == 1) {
+    // matrix-vector product: C(m, 0) = alpha A(m, :) B(:, 0) + beta C(m, 0), or its transpose for M == 1
+    const bool col = (N == 1);
+    const int64_t rows = col ? M : N;
+    const int blocks = (int)std::min<int64_t>((rows + 7) / 8, 152 * 8);
+    if (col)
+      gemv_f64_kernel<<<blocks, 256, 0, s>>>(M, K, alpha, A, a_rs, a_cs, B, b_rs, beta, C, c_rs);
+    else
+      gemv_f64_kernel<<<blocks, 256, 0, s>>>(N, K, alpha, B, b_cs, b_rs, A, a_cs, beta, C, c_cs);
+    note_launch();
+    return cudaGetLastError();
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t mn = std::min(M, N);
+  if (mn >= 256) return launch_gemm_tiles<64>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs, nsm, s);
+  if (mn >= 48) return launch_gemm_tiles<32>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs, nsm, s);
+  return launch_gemm_tiles<16>(M, N, K, alpha, A, a_rs, a_cs, B, b_rs, b_cs, beta, C, c_rs, c_cs, nsm, s);
 }
 
 template <typename Tin, typename Tout>

@@ -9,11 +9,11 @@
 //            of T by Sturm-sequence multisection (16 or 32 points per round);
 //   stage 2  (after the caller picked r) the eigenvectors of T for the r
 //            largest eigenvalues by twisted factorisation (one thread per
-//            cluster of nearly equal eigenvalues, modified Gram-Schmidt
-//            inside a cluster), then the back-transformation U = Q Z.
+//            eigenvalue; one CTA per cluster of nearly equal eigenvalues
+//            orthogonalises its members), then the back-transformation U = Q Z.
 // GB300 has few FP64 units (about 2 FMA per clock per SM), so every stage is
 // spread over the whole GPU: the tridiagonalisation keeps the matrix rows in
-// the shared memory of one cooperative grid (one CTA for n <= 96) with one
+// the shared memory of one cooperative grid (one CTA for n <= 16) with one
 // bounded grid barrier per column; matrices too large for that fall back to a
 // global-memory form with two barriers per column.
 #include <algorithm>
@@ -27,7 +27,7 @@ namespace bht {
 namespace {
 
 constexpr int EIG_THREADS = 256;
-constexpr int SMALL_N = 96;
+constexpr int SMALL_N = 16;
 
 struct Barrier {
   unsigned int count;
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
       double dot = 0.0;
       for (int q = 1 + lane; q < m; q += 32) {
         const int c = t + 1 + q;
-        const double a = r[c] - (vi * w[q] + wi * v[q]);
+        const double a = fma(-vi, w[q], fma(-wi, v[q], r[c]));  // three FP64 operations per entry with the dot
         r[c] = a;
         dot = fma(a, vn[q - 1], dot);
         if (publish) Rn[c] = a;
@@ -452,12 +452,17 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
 // with the stationary (top-down) and progressive (bottom-up) LDL^T
 // factorisations of T - lambda I, the twist index k minimising
 // |gamma_k| = |D+_k + D-_k - (d_k - lambda)| gives the eigenvector from
-// z_k = 1 and two one-sided recurrences. One thread leads each cluster of
-// eigenvalues closer than ctol and orthogonalises the members it computes
-// against the earlier ones (modified Gram-Schmidt, twice).
+// z_k = 1 and two one-sided recurrences. One thread per eigenvalue; inside a
+// cluster (a chain of eigenvalues closer than ctol) the shifts are spread by
+// 10 eps ||T|| per member so the members differ, and cluster_orth_kernel
+// then orthogonalises each cluster.
 // Z[i * r + j] receives component i of eigenvector j of T.
-// Scratch per eigenvalue index: 5 n doubles.
+// Scratch per eigenvalue index: 4 n doubles.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double cluster_tol(const double* lam, int n) {
+  return 1e-9 * (fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN);
+}
+
 __global__ void invit_kernel(const double* dg, const double* eg, int n, const double* __restrict__ lam, int r,
                              double* __restrict__ Z, double* __restrict__ scratch) {
   extern __shared__ double tsm[];
@@ -471,60 +476,100 @@ __global__ void invit_kernel(const double* dg, const double* eg, int n, const do
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= r) return;
   const double tnorm = fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN;
-  const double ctol = 1e-9 * tnorm;
+  const double ctol = cluster_tol(lam, n);
   const double tiny = 1e-3 * DBL_EPSILON * tnorm + DBL_MIN;
-  if (j > 0 && fabs(lam[j - 1] - lam[j]) <= ctol) return;  // not a cluster leader
-  int c = 1;
-  while (j + c < r && fabs(lam[j + c - 1] - lam[j + c]) <= ctol) ++c;
-  double* Dp = scratch + (int64_t)j * 5 * n;
+  int lead = j;
+  while (lead > 0 && fabs(lam[lead - 1] - lam[lead]) <= ctol) --lead;
+  double* Dp = scratch + (int64_t)j * 4 * n;
   double* Lp = Dp + n;
   double* Dm = Lp + n;
   double* Um = Dm + n;
-  double* z = Um + n;
-  for (int m = j; m < j + c; ++m) {
-    // perturb repeated shifts slightly so the members differ
-    const double s = lam[m] + (double)(m - j) * 10.0 * DBL_EPSILON * tnorm;
-    Dp[0] = d[0] - s;
-    for (int i = 0; i + 1 < n; ++i) {
-      if (fabs(Dp[i]) < tiny) Dp[i] = tiny;
-      Lp[i] = e[i] / Dp[i];
-      Dp[i + 1] = (d[i + 1] - s) - Lp[i] * e[i];
+  const double s = lam[j] + (double)(j - lead) * 10.0 * DBL_EPSILON * tnorm;
+  Dp[0] = d[0] - s;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (fabs(Dp[i]) < tiny) Dp[i] = tiny;
+    Lp[i] = e[i] / Dp[i];
+    Dp[i + 1] = (d[i + 1] - s) - Lp[i] * e[i];
+  }
+  Dm[n - 1] = d[n - 1] - s;
+  for (int i = n - 1; i >= 1; --i) {
+    if (fabs(Dm[i]) < tiny) Dm[i] = tiny;
+    Um[i] = e[i - 1] / Dm[i];
+    Dm[i - 1] = (d[i - 1] - s) - Um[i] * e[i - 1];
+  }
+  int k = 0;
+  double best = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const double g = fabs(Dp[i] + Dm[i] - (d[i] - s));
+    if (g < best) {
+      best = g;
+      k = i;
     }
-    Dm[n - 1] = d[n - 1] - s;
-    for (int i = n - 1; i >= 1; --i) {
-      if (fabs(Dm[i]) < tiny) Dm[i] = tiny;
-      Um[i] = e[i - 1] / Dm[i];
-      Dm[i - 1] = (d[i - 1] - s) - Um[i] * e[i - 1];
-    }
-    int k = 0;
-    double best = INFINITY;
-    for (int i = 0; i < n; ++i) {
-      const double g = fabs(Dp[i] + Dm[i] - (d[i] - s));
-      if (g < best) {
-        best = g;
-        k = i;
-      }
-    }
-    z[k] = 1.0;
-    for (int i = k - 1; i >= 0; --i) z[i] = -Lp[i] * z[i + 1];
-    for (int i = k + 1; i < n; ++i) z[i] = -Um[i] * z[i - 1];
+  }
+  // z in the output column: z_k = 1, then the two one-sided recurrences
+  double* zc = Z + j;
+  zc[(int64_t)k * r] = 1.0;
+  double mx = 1.0;
+  for (int i = k - 1; i >= 0; --i) {
+    const double z = -Lp[i] * zc[(int64_t)(i + 1) * r];
+    zc[(int64_t)i * r] = z;
+    mx = fmax(mx, fabs(z));
+  }
+  for (int i = k + 1; i < n; ++i) {
+    const double z = -Um[i] * zc[(int64_t)(i - 1) * r];
+    zc[(int64_t)i * r] = z;
+    mx = fmax(mx, fabs(z));
+  }
+  if (!isfinite(mx)) mx = 1.0;
+  const double inv_mx = 1.0 / mx;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double z = zc[(int64_t)i * r] * inv_mx;
+    nrm = fma(z, z, nrm);
+  }
+  const double sc = nrm > 0.0 ? inv_mx / sqrt(nrm) : 0.0;
+  for (int i = 0; i < n; ++i) zc[(int64_t)i * r] *= sc;
+}
+
+// One CTA per potential cluster leader j < r (an index that starts a chain of
+// at least two eigenvalues closer than ctol, chains cut at r): classical
+// Gram-Schmidt of every later member against the earlier ones, twice, then
+// normalisation. Dot products one warp per earlier member; the update one
+// thread per component.
+__global__ void __launch_bounds__(EIG_THREADS) cluster_orth_kernel(const double* __restrict__ lam, int n, int r,
+                                                                   double* __restrict__ Z) {
+  const int j0 = blockIdx.x;
+  const double ctol = cluster_tol(lam, n);
+  if (j0 + 1 >= r || fabs(lam[j0] - lam[j0 + 1]) > ctol) return;
+  if (j0 > 0 && fabs(lam[j0 - 1] - lam[j0]) <= ctol) return;  // not the leader
+  int cs = 2;
+  while (j0 + cs < r && fabs(lam[j0 + cs - 1] - lam[j0 + cs]) <= ctol) ++cs;
+  extern __shared__ double dots[];  // cs
+  __shared__ double red[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = j0 + 1; m < j0 + cs; ++m) {
     for (int pass = 0; pass < 2; ++pass) {
-      for (int q = j; q < m; ++q) {
-        double dot = 0.0;
-        for (int i = 0; i < n; ++i) dot = fma(Z[(int64_t)i * r + q], z[i], dot);
-        for (int i = 0; i < n; ++i) z[i] -= dot * Z[(int64_t)i * r + q];
+      for (int q = j0 + warp; q < m; q += nw) {
+        double dt = 0.0;
+        for (int i = lane; i < n; i += 32) dt = fma(Z[(int64_t)i * r + q], Z[(int64_t)i * r + m], dt);
+        dt = warp_sum(dt);
+        if (lane == 0) dots[q - j0] = dt;
       }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double* row = Z + (int64_t)i * r;
+        double acc = row[m];
+        for (int q = j0; q < m; ++q) acc = fma(-dots[q - j0], row[q], acc);
+        Z[(int64_t)i * r + m] = acc;
+      }
+      __syncthreads();
     }
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(z[i]));
-    if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
-    double nrm = 0.0;
-    for (int i = 0; i < n; ++i) {
-      z[i] /= mx;
-      nrm = fma(z[i], z[i], nrm);
-    }
+    double s2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s2 = fma(Z[(int64_t)i * r + m], Z[(int64_t)i * r + m], s2);
+    const double nrm = block_sum(s2, red);
     const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-    for (int i = 0; i < n; ++i) Z[(int64_t)i * r + m] = z[i] * inv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Z[(int64_t)i * r + m] *= inv;
+    __syncthreads();
   }
 }
 
@@ -589,7 +634,7 @@ size_t eig_workspace_bytes(int64_t n) {
          256;
 }
 
-size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 5 * (size_t)n * (size_t)r + 256; }
+size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 4 * (size_t)n * (size_t)r + 256; }
 
 cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -706,6 +751,17 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     invit_kernel<<<(unsigned)((r + 31) / 32), 32, sm, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
                                                            static_cast<double*>(scratch));
     note_launch();
+    if (r >= 2) {
+      // every index may lead a cluster; a cluster never exceeds r members
+      const size_t smc = sizeof(double) * (size_t)r;
+      if (smc > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(cluster_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smc);
+        if (e != cudaSuccess) return e;
+      }
+      cluster_orth_kernel<<<(unsigned)r, EIG_THREADS, smc, s>>>(lam, (int)n, (int)r, U);
+      note_launch();
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
