@@ -436,11 +436,16 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
     if (used_norm) *used_norm = norm_in != nullptr;
     return out;
   }
+  // the basis enters the FP32 SIMT kernel as an FP32 copy [S][T]
+  DBuf M32(sizeof(float) * (size_t)std::max<int64_t>(S * T, 1), s);
+  ck(launch_cast_matrix(U, ms, mt, S, T, M32.as<float>(), s), "basis to FP32");
   if (C.dtype == BHT_F32)
-    ck(launch_ttm_f32<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), U, ms, mt, A, T, B, S, R2, s),
+    ck(launch_ttm_f32<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T, B, S,
+                             R2, s),
        "ttm");
   else
-    ck(launch_ttm_f32<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), U, ms, mt, A, T, B, S, R2, s),
+    ck(launch_ttm_f32<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T, B,
+                              S, R2, s),
        "ttm");
   return out;
 }

@@ -115,10 +115,11 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const T* __restrict__ X, 
 // TTM: out[a][s][b] = sum_t M(s,t) X[a][t][b]
 // grid.x: tiles of the flattened column c = a * B + b, grid.y: tiles of s.
 // ---------------------------------------------------------------------------
-template <typename Tin, typename Tout, typename Acc>
+template <typename Tin, typename Tout, typename Acc, typename Tm>
 __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X, Tout* __restrict__ out,
-                                                      const double* __restrict__ M, int64_t ms, int64_t mt,
+                                                      const Tm* __restrict__ M, int64_t ms, int64_t mt,
                                                       int64_t A, int64_t T, int64_t B, int64_t S, int64_t R2) {
+  constexpr int PER = BK * TILE / NT;  // staged X elements per thread
   __shared__ Acc Ms[BK][TILE + 1];
   __shared__ Acc Xs[BK][TILE + 1];
   const int64_t c0 = (int64_t)blockIdx.x * TILE;
@@ -127,6 +128,17 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool m_along_s = (ms == 1);
   const bool x_along_c = B >= 8;
+  // the column c = a * B + b of every staged X element is fixed across the T stages
+  int xkk[PER], xcc[PER];
+  int64_t xoff[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * NT;
+    if (x_along_c) { xcc[q] = e % TILE; xkk[q] = e / TILE; } else { xkk[q] = e % BK; xcc[q] = e / BK; }
+    const int64_t c = c0 + xcc[q];
+    const int64_t a = c / B, b = c - a * B;
+    xoff[q] = (c < AB) ? a * T * B + b : -1;
+  }
   Acc acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -140,16 +152,10 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
       const int64_t t = t0 + kk, sidx = s0 + ss;
       Ms[kk][ss] = (t < T && sidx < S) ? static_cast<Acc>(M[sidx * ms + t * mt]) : Acc(0);
     }
-    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
-      int kk, cc;
-      if (x_along_c) { cc = e % TILE; kk = e / TILE; } else { kk = e % BK; cc = e / BK; }
-      const int64_t t = t0 + kk, c = c0 + cc;
-      Acc v = Acc(0);
-      if (t < T && c < AB) {
-        const int64_t a = c / B, b = c - a * B;
-        v = static_cast<Acc>(X[(a * T + t) * B + b]);
-      }
-      Xs[kk][cc] = v;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int64_t t = t0 + xkk[q];
+      Xs[xkk[q]][xcc[q]] = (t < T && xoff[q] >= 0) ? static_cast<Acc>(X[xoff[q] + t * B]) : Acc(0);
     }
     __syncthreads();
 #pragma unroll
@@ -389,6 +395,15 @@ __global__ void scale_strided_kernel(double* __restrict__ C, int64_t M, int64_t 
   }
 }
 
+__global__ void cast_matrix_kernel(const double* __restrict__ U, int64_t ms, int64_t mt, int64_t S, int64_t T,
+                                   float* __restrict__ out) {
+  const int64_t total = S * T;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sidx = e / T, t = e - sidx * T;
+    out[e] = static_cast<float>(U[sidx * ms + t * mt]);
+  }
+}
+
 __global__ void fill_identity_kernel(double* __restrict__ A, int64_t n) {
   const int64_t total = n * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
@@ -458,8 +473,8 @@ cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int
   return launch_gram<float, float>(X, G, A, I, B, s);
 }
 
-template <typename Tin, typename Tout, typename Acc>
-cudaError_t launch_ttm(const Tin* X, Tout* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+template <typename Tin, typename Tout, typename Acc, typename Tm>
+cudaError_t launch_ttm(const Tin* X, Tout* out, const Tm* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                        int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
   if (A <= 0 || B <= 0 || S <= 0) return cudaSuccess;
   if (R2 < 1 || (B == 1 && A % R2 != 0) || (B > 1 && R2 != 1)) return cudaErrorInvalidValue;
@@ -468,7 +483,7 @@ cudaError_t launch_ttm(const Tin* X, Tout* out, const double* M, int64_t ms, int
   if (grid.y > 65535) return cudaErrorInvalidValue;
   ProfScope prof(sizeof(Acc) == 8 ? K_TTM_F64 : K_TTM_F32, s, 2.0 * (double)S * (double)T * (double)AB,
                  (double)sizeof(Tin) * (double)AB * (double)T + (double)sizeof(Tout) * (double)AB * (double)S);
-  ttm_simt_kernel<Tin, Tout, Acc><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S, R2);
+  ttm_simt_kernel<Tin, Tout, Acc, Tm><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S, R2);
   note_launch();
   return cudaGetLastError();
 }
@@ -480,7 +495,7 @@ cudaError_t launch_ttm_f64(const Tin* X, Tout* out, const double* M, int64_t ms,
 }
 
 template <typename Tin>
-cudaError_t launch_ttm_f32(const Tin* X, float* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+cudaError_t launch_ttm_f32(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                            int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
   return launch_ttm<Tin, float, float>(X, out, M, ms, mt, A, T, B, S, R2, s);
 }
@@ -603,6 +618,15 @@ cudaError_t launch_unit_cols(double* Q, int64_t ldq, int64_t col0, int64_t ra0, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_cast_matrix(const double* U, int64_t ms, int64_t mt, int64_t S, int64_t T, float* out,
+                               cudaStream_t s) {
+  if (S <= 0 || T <= 0) return cudaSuccess;
+  ProfScope prof(K_COPY, s);
+  cast_matrix_kernel<<<grid_for(S * T), 256, 0, s>>>(U, ms, mt, S, T, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill_identity(double* A, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   ProfScope prof(K_COPY, s);
@@ -650,9 +674,9 @@ template cudaError_t launch_copy_pad3<double, float>(const double*, int64_t, int
                                                      int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_cast<float, double>(const float*, double*, int64_t, cudaStream_t);
 template cudaError_t launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
-template cudaError_t launch_ttm_f32<float>(const float*, float*, const double*, int64_t, int64_t, int64_t, int64_t,
+template cudaError_t launch_ttm_f32<float>(const float*, float*, const float*, int64_t, int64_t, int64_t, int64_t,
                                            int64_t, int64_t, int64_t, cudaStream_t);
-template cudaError_t launch_ttm_f32<double>(const double*, float*, const double*, int64_t, int64_t, int64_t, int64_t,
+template cudaError_t launch_ttm_f32<double>(const double*, float*, const float*, int64_t, int64_t, int64_t, int64_t,
                                             int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_check_finite<double>(const double*, int64_t, int*, cudaStream_t);

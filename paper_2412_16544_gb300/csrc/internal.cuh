@@ -66,11 +66,16 @@ cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t
 // Same Gram with FP32 products, partial sums promoted to FP64 every 16 columns.
 cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s);
 
-// FP32 SIMT mode product; with B == 1 the new axis is written in front of the
-// last R2 rows: out[(o * S + s) * R2 + i] for a = o * R2 + i (R2 = 1: in place).
+// FP32 SIMT mode product with an FP32 matrix M(s, t) = M[s * ms + t * mt]; with
+// B == 1 the new axis is written in front of the last R2 rows:
+// out[(o * S + s) * R2 + i] for a = o * R2 + i (R2 = 1: in place).
 template <typename Tin>
-cudaError_t launch_ttm_f32(const Tin* X, float* out, const double* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
+cudaError_t launch_ttm_f32(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                            int64_t B, int64_t S, int64_t R2, cudaStream_t s);
+
+// out[s * T + t] = (float) U[s * ms + t * mt]
+cudaError_t launch_cast_matrix(const double* U, int64_t ms, int64_t mt, int64_t S, int64_t T, float* out,
+                               cudaStream_t s);
 
 // out[a][s][b] = sum_t M(s, t) X[a][t][b], M(s, t) = M[s * ms + t * mt], s < S, t < T.
 template <typename Tin, typename Tout>
