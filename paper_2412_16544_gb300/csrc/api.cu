@@ -9,6 +9,7 @@
 // B = prod_{i>j} I_i; merging two children's axes into their parent's axis is
 // a C-order reshape and moves no data.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -94,7 +95,7 @@ const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
-                                             "other"};
+                                             "house_f64",      "other"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -186,8 +187,29 @@ static void build_tree(bht_tree& t, int d, const int64_t* dims) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// Stream-ordered allocations from the device's default pool. The pool keeps what it has
+// grown to (release threshold raised once per device, for this process only): the working
+// buffers of one update are allocated and freed many times per call, and a pool that hands
+// memory back at every synchronisation would map it again each time.
+void keep_pool(int dev) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  if (dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 void* dalloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) keep_pool(dev);
   void* p = nullptr;
   ck(cudaMallocAsync(&p, bytes, s), "cudaMallocAsync");
   return p;
@@ -644,6 +666,22 @@ double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int*
   return Q;
 }
 
+int num_sms() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(nsm, 1);
+}
+
+// The Householder route to the complement of k orthonormal columns in R^c costs k sequential
+// reflector steps; the randomized route an eigensolve of size c - k + 8. Householder when k is
+// the smaller and its rows fit the shared memory of at most one CTA per SM.
+bool house_fits(int64_t c, int64_t k) {
+  const int64_t nsm = num_sms();
+  const int64_t rpb = std::max<int64_t>(8, (c + nsm - 1) / nsm);
+  return 2 * k <= c + 8 && sizeof(double) * rpb * (k + 1) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
+}
+
 uint64_t complement_seed(int id, int64_t n_items) {
   return 0x42485452495345ull ^ ((uint64_t)id << 40) ^ (uint64_t)n_items;
 }
@@ -1008,11 +1046,18 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         // the complement shrinks to Q times the complement of Z inside R^c
         double* Qn = own(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(a * (c - rR), 1), s)));
         if (c > rR) {
-          DBuf Yc;
-          Yc.p = complement_of(Zk.as<double>(), c, rR, complement_seed(id, st->n_items), st->d_status, s);
-          Yc.s = s;
-          ck(launch_gemm_f64(a, c - rR, c, 1.0, Q[id], c, 1, Yc.as<double>(), c - rR, 1, 0.0, Qn, c - rR, 1, s),
-             "Q Y");
+          if (house_fits(c, rR)) {
+            // rR Householder reflectors of Z applied to the rows of Q
+            DBuf hw(house_workspace_bytes(c, rR, num_sms()), s);
+            ck(launch_house_complement(Q[id], a, c, Zk.as<double>(), rR, Qn, hw.p, st->d_status, s),
+               "Householder complement");
+          } else {
+            DBuf Yc;
+            Yc.p = complement_of(Zk.as<double>(), c, rR, complement_seed(id, st->n_items), st->d_status, s);
+            Yc.s = s;
+            ck(launch_gemm_f64(a, c - rR, c, 1.0, Q[id], c, 1, Yc.as<double>(), c - rR, 1, 0.0, Qn, c - rR, 1, s),
+               "Q Y");
+          }
         }
         DBuf W(sizeof(double) * r0 * rR + 8, s);
         // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "sync.cuh"
 
 namespace bht {
 
@@ -28,75 +29,6 @@ namespace {
 
 constexpr int EIG_THREADS = 256;
 constexpr int SMALL_N = 16;
-
-struct Barrier {
-  unsigned int count;
-  unsigned int gen;
-};
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier with a 1 s limit; returns false when the wait gave up
-// (the status word is then BHT_ETIMEOUT = 6). With one CTA it is __syncthreads.
-__device__ bool grid_barrier(Barrier* bar, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (gridDim.x == 1) return true;
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned int* vgen = &bar->gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      bar->count = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      const uint64_t t0 = global_ns();
-      while (*vgen == g) {
-        if (*(volatile int*)status != 0) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > 1000000000ull) {
-          atomicExch(status, 6);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    double t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
-    t = warp_sum(t);
-    if (l == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
 
 // ---------------------------------------------------------------------------
 // Householder tridiagonalisation of the symmetric matrix A (n x n, both

@@ -27,8 +27,9 @@ enum KernelClass {
   K_EIG_INVIT = 9,
   K_EIG_BACK = 10,
   K_TTM_F32 = 11,
-  K_OTHER = 12,
-  K_NUM_CLASSES = 13
+  K_HOUSE = 12,
+  K_OTHER = 13,
+  K_NUM_CLASSES = 14
 };
 const char* kernel_class_name(int cls);
 
@@ -72,6 +73,13 @@ cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int
 template <typename Tin>
 cudaError_t launch_ttm_f32(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                            int64_t B, int64_t S, int64_t R2, cudaStream_t s);
+
+// Householder complement: out (a x (c - k)) = Q (a x c) times the last c - k columns of the
+// orthogonal factor of the QR factorisation of Z (c x k, orthonormal columns). work: at least
+// house_workspace_bytes(c, k, #SM) bytes; status: device word of the bounded grid barrier.
+size_t house_workspace_bytes(int64_t c, int64_t k, int nsm);
+cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const double* Z, int64_t k, double* out,
+                                    void* work, int* status, cudaStream_t s);
 
 // out[s * T + t] = (float) U[s * ms + t * mt]
 cudaError_t launch_cast_matrix(const double* U, int64_t ms, int64_t mt, int64_t S, int64_t T, float* out,
