@@ -13,6 +13,7 @@ a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -290,6 +291,24 @@ def run_ours(a, rank, world, local_rank):
 
     # roofline of the dominant kernel class and of the tensor-core mode product (algorithmic work per launch
     # accumulated by the library, CUDA-event durations on the launch stream over the timed region)
+    def traffic_of(name):
+        # per-launch DRAM bytes from a committed ncu capture, only while the kernel source is unchanged
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic.txt")
+        try:
+            lines = open(path).read().splitlines()
+        except OSError:
+            return None
+        for ln in lines:
+            f = ln.split()
+            if len(f) == 4 and not ln.startswith("#") and f[0] == name:
+                src = os.path.join(os.path.dirname(os.path.abspath(__file__)), f[2])
+                try:
+                    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+                except OSError:
+                    return None
+                return float(f[1]) if h == f[3] else None
+        return None
+
     def roof(name):
         t_ms, n_l, flops, nbytes = prof.get(name, (0.0, 0, 0.0, 0.0))
         if not n_l or t_ms <= 0:
@@ -298,7 +317,7 @@ def run_ours(a, rank, world, local_rank):
         if name in ("ttm_tc", "copy", "norm"):
             ach = nbytes / n_l / per_launch_s / 1e9
             return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                    "traffic": None, "kernel": name, "launches_per_step": n_l / a.steps,
+                    "traffic": traffic_of(name), "kernel": name, "launches_per_step": n_l / a.steps,
                     "ms_per_launch": per_launch_s * 1e3, "peak_source": peak_src}
         if name.endswith("f32"):
             peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
@@ -308,7 +327,7 @@ def run_ours(a, rank, world, local_rank):
             src = "FP64 nominal of the profiling recipe (1.25 TFLOP/s)"
         ach = flops / n_l / per_launch_s / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": name, "launches_per_step": n_l / a.steps,
+                "traffic": traffic_of(name), "kernel": name, "launches_per_step": n_l / a.steps,
                 "ms_per_launch": per_launch_s * 1e3, "peak_source": src}
 
     roofline = roof(dom_name)
@@ -324,7 +343,7 @@ def run_ours(a, rank, world, local_rank):
         "dtype": "tf32" if a.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "precision": a.precision, "items_per_step": a.increments * a.items,
                    "bytes_per_step": bytes_per_step, "parallelism": f"{world} independent streams",
-                   "l2": "inputs (671 MB per stream) larger than L2 (129 MB); no flush"},
+                   "l2": f"inputs ({bytes_per_step / 1e6:.0f} MB per stream) larger than L2 (129 MB); no flush"},
         "roofline": roofline, "roofline_ttm_tc": roofline_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "plain_fp64": plain,
