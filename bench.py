@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GB/s of tensor stream compressed (BHT-l2r+HT-RISE) at rel err<=eps, fast vs plain FP64"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -41,23 +41,23 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--increments", type=int, default=20)
     ap.add_argument("--items", type=int, default=32)
-    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--grid", type=int, default=64, help="edge of the cubic snapshot")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_name(a):
-    return (f"advected spectral field {a.n}^3 (|k|<=16, |k|^-5/3), {a.increments} increments x {a.items} "
+    return (f"advected spectral field {a.grid}^3 (|k|<=16, |k|^-5/3), {a.increments} increments x {a.items} "
             f"snapshots, eps_rel={a.eps:g}")
 
 
 def gen_stream(a, seed):
     import bht_synth
-    Y = bht_synth.spectral_field(seed, 0, a.increments * a.items, n=a.n)
-    return Y.reshape(a.increments, a.items, a.n, a.n, a.n)
+    Y = bht_synth.spectral_field(seed, 0, a.increments * a.items, n=a.grid)
+    return Y.reshape(a.increments, a.items, a.grid, a.grid, a.grid)
 
 
 # ---------------------------------------------------------------------------
@@ -154,7 +154,7 @@ def run_reference(a, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-# algorithmic work per kernel class, see the design doc (roofline section)
+# algorithmic work per kernel class is attached by the library to every launch
 PEAK_FP64_TFLOPS = 1.25  # FP64 nominal of the profiling recipe table (no measured FP64 peak is provided)
 
 
@@ -172,7 +172,7 @@ def run_ours(a, rank, world, local_rank):
     Yh = gen_stream(a, seed=rank)                  # each rank compresses its own independent stream
     Yd = torch.from_numpy(Yh).to(dev)              # resident in HBM before the timed region
     bytes_per_step = Yh.nbytes
-    tree = B.bht_tree_create_balanced([a.n] * 3)
+    tree = B.bht_tree_create_balanced([a.grid] * 3)
     stream = torch.cuda.current_stream()
 
     def one_pass(prec, src):
@@ -209,11 +209,8 @@ def run_ours(a, rank, world, local_rank):
         B.bht_profile_enable(0)
         launches = B.bht_launch_count(reset=True)
         prof = B.bht_profile_read(reset=True, work=True)
-        ms = e0.elapsed_time(e1) / steps
+        ms = job_max(dist, e0.elapsed_time(e1) / steps, dev)
         if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         return ms, launches / steps, prof, clocks, states
 
@@ -238,7 +235,7 @@ def run_ours(a, rank, world, local_rank):
     tc_cls = names.index("ttm_tc")
     ms, launches, prof, clocks, states = timed(a.precision, a.steps, a.warmup,
                                                profile_mask=(1 << dom_cls) | (1 << tc_cls))
-    value = bytes_per_step * world / (ms / 1000.0) / 1e9
+    value = job_rate_gbs(bytes_per_step, world, ms / 1000.0)
 
     # accuracy of the last timed pass: per-increment relative error of the reconstruction
     st, skips = states[-1]
@@ -248,7 +245,7 @@ def run_ours(a, rank, world, local_rank):
         rec = B.ht_reconstruct(st, k * a.items, a.items, dtype="float32")
         errs.append(float(torch.linalg.vector_norm(rec - Yd[k]) / torch.linalg.vector_norm(Yd[k])))
     cores = B.bht_num_elements(st)
-    cr = a.increments * a.items * a.n ** 3 / cores
+    cr = a.increments * a.items * a.grid ** 3 / cores
     for s_, _ in states:
         B.bht_state_destroy(s_)
 
@@ -258,20 +255,22 @@ def run_ours(a, rank, world, local_rank):
         ms64, _, _, _, st64 = timed("fp64", 1, 1)
         for s_, _ in st64:
             B.bht_state_destroy(s_)
-        plain = {"value": bytes_per_step * world / (ms64 / 1000.0) / 1e9, "unit": "GB/s", "ms_per_step": ms64}
+        plain = {"value": job_rate_gbs(bytes_per_step, world, ms64 / 1000.0), "unit": "GB/s", "ms_per_step": ms64}
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
     if not a.no_e2e:
         Yp = torch.from_numpy(Yh).pin_memory()
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         st_e, _ = one_pass(a.precision, Yp)
         root = B.bht_get_root(st_e, 0, a.increments * a.items)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": bytes_per_step / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(Yh.nbytes),
-               "d2h_bytes_per_step": int(root.nbytes)}
+        dt = job_max(dist, time.perf_counter() - t0, dev)
+        e2e = {"value": job_rate_gbs(bytes_per_step, world, dt), "unit": "GB/s",
+               "h2d_bytes_per_step": int(Yh.nbytes), "d2h_bytes_per_step": int(root.nbytes)}
         B.bht_state_destroy(st_e)
 
     # CPU baseline: the oracle on a bounded sample, rank 0 only
@@ -357,11 +356,30 @@ def run_ours(a, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def rank_env():
+    """(rank, world size, local rank) from the torchrun environment; (0, 1, 0) when launched alone."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def job_max(dist, value, device="cpu"):
+    """Maximum of a per-rank scalar over the job (the slowest rank sets the job's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate_gbs(bytes_per_rank, world, seconds_max):
+    """Whole-job throughput: every rank compresses its own stream of bytes_per_rank in the job's time."""
+    return bytes_per_rank * world / seconds_max / 1e9
+
+
 def main():
     a = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local_rank = rank_env()
     if a.impl == "reference":
         run_reference(a, rank)
         return
