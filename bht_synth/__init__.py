@@ -179,13 +179,19 @@ def chebyshev_sensor(seed: int, first: int, count: int, n: int = 24, d: int = 5,
     """
     T = _chebyshev_basis(n, degree)
     out = np.empty((count,) + (n,) * d, dtype=dtype)
-    letters = "abcdefghij"[:d]
-    spec = ",".join("q" + l for l in letters) + "->" + letters
+    h = (d + 1) // 2
     for j in range(count):
         rng = _item_rng(seed, first + j)
         c = rng.normal(size=(terms, d, degree + 1))
         f = np.einsum("qmj,jn->qmn", c, T)  # [terms, d, n]
-        item = np.einsum(spec, *[f[:, m, :] for m in range(d)])
+        # the sum of separable products as (Khatri-Rao of the first h modes)^T x (of the rest)
+        left = np.ones((terms, 1))
+        for m in range(h):
+            left = (left[:, :, None] * f[:, m, None, :]).reshape(terms, -1)
+        right = np.ones((terms, 1))
+        for m in range(h, d):
+            right = (right[:, :, None] * f[:, m, None, :]).reshape(terms, -1)
+        item = (left.T @ right).reshape((n,) * d)
         if noise_std:
             item += noise_std * rng.standard_normal(size=item.shape)
         out[j] = item

@@ -472,6 +472,59 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
   return out;
 }
 
+// Mixed-path projection of one axis onto [U | Q] (U [T][r] the node basis, Q [T][c] its orthonormal
+// complement): the r outputs on U are kept, the squares of the c outputs on Q (the energy of the part
+// of C outside span(U) along this axis) are added to *resid without forming them. As [U | Q] is
+// orthogonal, ||C||^2 = ||C x U^T||^2 + ||C x Q^T||^2 exactly; the sum of these residual energies over a
+// full projection is the projection error of eq. relative_error_threshold, free of the cancellation
+// in ||Y||^2 - ||C||^2.
+LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, const double* Q, int64_t c,
+                       bool rotate, const Arith& ar, cudaStream_t s, double* norm_in, bool* used_norm,
+                       double* resid) {
+  if (!ar.mixed || !resid || c <= 0) return ttm_any(C, axis, U, 1, r, r, rotate, ar, s, norm_in, used_norm);
+  int64_t A, T, B;
+  C.view(axis, A, T, B);
+  if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
+  LTensor out;
+  out.N = C.N;
+  out.dims = C.dims;
+  out.node = C.node;
+  out.dims[axis] = r;
+  if (rotate) {
+    std::rotate(out.dims.begin(), out.dims.begin() + axis, out.dims.begin() + axis + 1);
+    std::rotate(out.node.begin(), out.node.begin() + axis, out.node.begin() + axis + 1);
+  }
+  const int64_t R2 = rotate ? A / C.N : 1;
+  if (used_norm) *used_norm = false;
+  out.dtype = BHT_F32;
+  out.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(out.numel(), 1), s);
+  out.ptr = out.own.p;
+  const int nb = 2;
+  const bool aligned = (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0;
+  if (B == 1 && C.dtype == BHT_F32 && aligned && ttm_tc_supported(T, r + c, nb)) {
+    DBuf W(ttm_tc_weights_bytes(T, r + c), s);
+    ck(launch_prep_tc_weights2(U, r, r, Q, c, c, T, true, W.as<float>(), nb, s), "tc weights");
+    ck(launch_ttm_tc_resid(static_cast<const float*>(C.ptr), A, T, W.as<float>(), r + c, r, nb, out.own.as<float>(), R2,
+                           norm_in, nullptr, resid, ar.d_status, s),
+       "tensor-core mode product");
+    if (used_norm) *used_norm = norm_in != nullptr;
+    return out;
+  }
+  // FP32 SIMT on [U | Q] cast to fp32 [r + c][T]
+  DBuf M32(sizeof(float) * (size_t)std::max<int64_t>((r + c) * T, 1), s);
+  ck(launch_cast_matrix(U, 1, r, r, T, M32.as<float>(), s), "basis to FP32");
+  ck(launch_cast_matrix(Q, 1, c, c, T, M32.as<float>() + r * T, s), "complement to FP32");
+  if (C.dtype == BHT_F32)
+    ck(launch_ttm_f32_resid<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T,
+                                   B, r + c, r, R2, resid, s),
+       "ttm");
+  else
+    ck(launch_ttm_f32_resid<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A,
+                                    T, B, r + c, r, R2, resid, s),
+       "ttm");
+  return out;
+}
+
 // Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j], cheapest order first.
 LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
                       const std::vector<int64_t>& rs, const Arith& ar, cudaStream_t s) {
@@ -709,17 +762,18 @@ double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_
 // the front, which after d steps restores the mode order), then the transfer
 // nodes layer by layer. norm_y (nullable): ||Y||^2 when a kernel folded it.
 LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, const Arith& ar, cudaStream_t s,
-                    double* norm_acc = nullptr, bool* norm_done = nullptr) {
+                    double* norm_acc = nullptr, bool* norm_done = nullptr, double* resid = nullptr) {
   const bht_tree& t = st->tree;
   LTensor C = input_tensor(t, Y, dtype, N);
   if (norm_done) *norm_done = false;
+  auto qcols = [&](int id) { return st->rows(id) - st->rank[id]; };
   if (ar.mixed) {
     for (int step = 0; step < t.d; ++step) {
       const int ax = (int)C.dims.size() - 1;
       const int id = C.node[ax];
       bool used = false;
-      LTensor nxt = ttm_any(C, ax, st->U[id], 1, st->rank[id], st->rank[id], true, ar, s,
-                            step == 0 && !ar.tight ? norm_acc : nullptr, &used);
+      LTensor nxt = ttm_proj_resid(C, ax, st->U[id], st->rank[id], st->Q[id], qcols(id), true, ar, s,
+                                   step == 0 && !ar.tight ? norm_acc : nullptr, &used, resid);
       if (step == 0 && norm_done) *norm_done = used;
       C = std::move(nxt);
     }
@@ -746,7 +800,18 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       Us.push_back(st->U[id]);
       rs.push_back(st->rank[id]);
     }
-    C = project_layer(std::move(C), ids, Us, rs, ar, s);
+    if (ar.mixed && resid) {
+      std::vector<std::pair<int, int64_t>> ops;
+      for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
+      for (int k : best_order(C.dims, ops)) {
+        const int id = ids[k];
+        LTensor nxt = ttm_proj_resid(C, C.axis_of(id), st->U[id], rs[k], st->Q[id], qcols(id), false, ar, s,
+                                     nullptr, nullptr, resid);
+        C = std::move(nxt);
+      }
+    } else {
+      C = project_layer(std::move(C), ids, Us, rs, ar, s);
+    }
   }
   return C;  // [N][r11][r12]
 }
@@ -974,21 +1039,25 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   DBuf staging;
   const void* dY = stage_input(Y, dtype, N * item, staging, s);
 
-  // Step 1: project onto the existing cores; ||Y||^2 and ||C||^2 in FP64
+  // Step 1: project onto the existing cores. ||Y||^2 in FP64; the projection error of
+  // eq. relative_error_threshold in FP64 as ||Y||^2 - ||C||^2 (FP64 form), or in the mixed form as the
+  // sum of the energies the projection removes at each node, measured on the node's complement.
   const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
-  DBuf acc(sizeof(double) * 2, s);
-  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 2, s), "memset");
+  DBuf acc(sizeof(double) * 3, s);
+  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 3, s), "memset");
   bool norm_done = false;
-  LTensor Cbar = project_all(st, dY, dtype, N, ar, s, acc.as<double>(), &norm_done);
+  double* resid = ar.mixed ? acc.as<double>() + 2 : nullptr;
+  LTensor Cbar = project_all(st, dY, dtype, N, ar, s, acc.as<double>(), &norm_done, resid);
   if (!norm_done) sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
-  sqnorm_of(Cbar.ptr, Cbar.dtype, Cbar.numel(), acc.as<double>() + 1, s);
-  double h[2];
+  if (!ar.mixed) sqnorm_of(Cbar.ptr, Cbar.dtype, Cbar.numel(), acc.as<double>() + 1, s);
+  double h[3];
   ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H norms");
   ck(cudaStreamSynchronize(s), "sync");
   if (!std::isfinite(h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
   check_status(st, s);
   const double eps_des = eps_rel * std::sqrt(h[0]);
-  const double eps_proj = std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold
+  const double eps_proj = ar.mixed ? std::sqrt(std::max(h[2], 0.0))
+                                   : std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold
   const int64_t r11_old = st->r11(), r12_old = st->r12();
   if (eps_proj <= eps_des) {
     grow_root(st, r11_old, r12_old, r11_old, r12_old, st->n_items + N, s);

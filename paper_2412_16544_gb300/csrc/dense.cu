@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const T* __restrict__ X, 
 template <typename Tin, typename Tout, typename Acc, typename Tm>
 __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X, Tout* __restrict__ out,
                                                       const Tm* __restrict__ M, int64_t ms, int64_t mt,
-                                                      int64_t A, int64_t T, int64_t B, int64_t S, int64_t R2) {
+                                                      int64_t A, int64_t T, int64_t B, int64_t S, int64_t R2,
+                                                      int64_t S_store, double* __restrict__ resid) {
   constexpr int PER = BK * TILE / NT;  // staged X elements per thread
   __shared__ Acc Ms[BK][TILE + 1];
   __shared__ Acc Xs[BK][TILE + 1];
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
     }
     __syncthreads();
   }
+  double rq = 0.0;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const int64_t c = c0 + tx + 16 * v;
@@ -182,11 +184,18 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t sidx = s0 + ty + 16 * u;
-      if (sidx < S) {
-        const int64_t off = (B > 1) ? (a * S + sidx) * B + b : (o * S + sidx) * R2 + i;
+      if (sidx < S_store) {
+        const int64_t off = (B > 1) ? (a * S_store + sidx) * B + b : (o * S_store + sidx) * R2 + i;
         out[off] = static_cast<Tout>(acc[u][v]);
+      } else if (sidx < S) {
+        rq += (double)acc[u][v] * (double)acc[u][v];
       }
     }
+  }
+  if (resid) {
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) rq += __shfl_xor_sync(0xffffffffu, rq, o2);
+    if ((threadIdx.x & 31) == 0 && rq != 0.0) atomicAdd(resid, rq);
   }
 }
 
@@ -475,7 +484,9 @@ cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int
 
 template <typename Tin, typename Tout, typename Acc, typename Tm>
 cudaError_t launch_ttm(const Tin* X, Tout* out, const Tm* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
-                       int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
+                       int64_t B, int64_t S, int64_t R2, cudaStream_t s, int64_t S_store = -1,
+                       double* resid = nullptr) {
+  if (S_store < 0) S_store = S;
   if (A <= 0 || B <= 0 || S <= 0) return cudaSuccess;
   if (R2 < 1 || (B == 1 && A % R2 != 0) || (B > 1 && R2 != 1)) return cudaErrorInvalidValue;
   const int64_t AB = A * B;
@@ -483,7 +494,7 @@ cudaError_t launch_ttm(const Tin* X, Tout* out, const Tm* M, int64_t ms, int64_t
   if (grid.y > 65535) return cudaErrorInvalidValue;
   ProfScope prof(sizeof(Acc) == 8 ? K_TTM_F64 : K_TTM_F32, s, 2.0 * (double)S * (double)T * (double)AB,
                  (double)sizeof(Tin) * (double)AB * (double)T + (double)sizeof(Tout) * (double)AB * (double)S);
-  ttm_simt_kernel<Tin, Tout, Acc, Tm><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S, R2);
+  ttm_simt_kernel<Tin, Tout, Acc, Tm><<<grid, NT, 0, s>>>(X, out, M, ms, mt, A, T, B, S, R2, S_store, resid);
   note_launch();
   return cudaGetLastError();
 }
@@ -498,6 +509,13 @@ template <typename Tin>
 cudaError_t launch_ttm_f32(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                            int64_t B, int64_t S, int64_t R2, cudaStream_t s) {
   return launch_ttm<Tin, float, float>(X, out, M, ms, mt, A, T, B, S, R2, s);
+}
+
+template <typename Tin>
+cudaError_t launch_ttm_f32_resid(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A,
+                                 int64_t T, int64_t B, int64_t S, int64_t S_store, int64_t R2, double* resid,
+                                 cudaStream_t s) {
+  return launch_ttm<Tin, float, float>(X, out, M, ms, mt, A, T, B, S, R2, s, S_store, resid);
 }
 
 template <typename T>
@@ -676,6 +694,10 @@ template cudaError_t launch_cast<float, double>(const float*, double*, int64_t, 
 template cudaError_t launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
 template cudaError_t launch_ttm_f32<float>(const float*, float*, const float*, int64_t, int64_t, int64_t, int64_t,
                                            int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_ttm_f32_resid<float>(const float*, float*, const float*, int64_t, int64_t, int64_t,
+                                                 int64_t, int64_t, int64_t, int64_t, int64_t, double*, cudaStream_t);
+template cudaError_t launch_ttm_f32_resid<double>(const double*, float*, const float*, int64_t, int64_t, int64_t,
+                                                  int64_t, int64_t, int64_t, int64_t, int64_t, double*, cudaStream_t);
 template cudaError_t launch_ttm_f32<double>(const double*, float*, const float*, int64_t, int64_t, int64_t, int64_t,
                                             int64_t, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);

@@ -81,6 +81,13 @@ size_t house_workspace_bytes(int64_t c, int64_t k, int nsm);
 cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const double* Z, int64_t k, double* out,
                                     void* work, int* status, cudaStream_t s);
 
+// The same with S computed output columns of which the first S_store are stored (the new axis has
+// S_store entries); the squares of the others are added to *resid (nullable, FP64).
+template <typename Tin>
+cudaError_t launch_ttm_f32_resid(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A,
+                                 int64_t T, int64_t B, int64_t S, int64_t S_store, int64_t R2, double* resid,
+                                 cudaStream_t s);
+
 // out[s * T + t] = (float) U[s * ms + t * mt]
 cudaError_t launch_cast_matrix(const double* U, int64_t ms, int64_t mt, int64_t S, int64_t T, float* out,
                                cudaStream_t s);
@@ -172,6 +179,15 @@ cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_
                                    int nb, cudaStream_t s);
 cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
                           int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s);
+// Weights of the concatenated matrix M = [U | U2] (S1 + S2 output columns; U [K][S1] with row stride
+// ldu when transpose, U2 likewise).
+cudaError_t launch_prep_tc_weights2(const double* U, int64_t S1, int64_t ldu, const double* U2, int64_t S2,
+                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s);
+// S computed output columns of which the first S_store are stored (the output's new axis has S_store
+// entries); the squares of the other S - S_store columns are added to *resid (nullable, FP64).
+cudaError_t launch_ttm_tc_resid(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int64_t S_store,
+                                int nb, float* out, int64_t R2, double* norm_in, double* norm_out, double* resid,
+                                int* status, cudaStream_t s);
 
 // A (n x n) += alpha I
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s);

@@ -148,7 +148,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 struct TcParams {
   int64_t rows;    // rows of X
   int nkc;         // K chunks of 32
-  int S;           // output extent
+  int S;           // computed output columns
+  int S_store;     // stored output columns (the first S_store); the squares of the rest go to resid
   int S_pad;       // rows of one weight plane (multiple of 16)
   int S_tile;      // MMA N per work unit (multiple of 16, <= 256)
   int n_ntiles;    // ceil(S_pad / S_tile)
@@ -158,6 +159,7 @@ struct TcParams {
   float* out;
   double* norm_in;
   double* norm_out;
+  double* resid;
   int* status;
 };
 
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
   } else {
     // ---------------- epilogue ----------------
     const int q = warp - 4;  // TMEM lane quarter
-    double sq = 0.0;
+    double sq = 0.0, rq = 0.0;
     uint32_t it = 0;
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++it) {
       const int64_t mt = u / P.n_ntiles;
@@ -324,21 +326,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
         i = row - o * P.R2;
       }
       const int s0 = nt * P.S_tile;
-      float* dst = P.out + (o * P.S) * P.R2 + i;
+      float* dst = P.out + (o * P.S_store) * P.R2 + i;
       for (int c0 = 0; c0 < P.S_tile && s0 + c0 < P.S; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * P.S_tile + c0, v);
         if (valid) {
-          float part = 0.f;  // 16 squares in FP32, folded into FP64 once
+          float part = 0.f, rpart = 0.f;  // 16 squares in FP32, folded into FP64 once
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int s = s0 + c0 + j;
-            if (s < P.S) {
+            if (s < P.S_store) {
               dst[(int64_t)s * P.R2] = v[j];
               part = fmaf(v[j], v[j], part);
+            } else if (s < P.S) {
+              rpart = fmaf(v[j], v[j], rpart);
             }
           }
           if (P.norm_out) sq += (double)part;
+          if (P.resid) rq += (double)rpart;
         }
       }
       fence_before();
@@ -349,6 +354,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
       sq = warp_sum_d(sq);
       if (lane == 0) atomicAdd(P.norm_out, sq);
     }
+    if (P.resid) {
+      rq = warp_sum_d(rq);
+      if (lane == 0) atomicAdd(P.resid, rq);
+    }
   }
   fence_before();
   __syncthreads();
@@ -358,14 +367,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
   }
 }
 
-// W[b][s][k] (b = 0: RN-rounded TF32 of U^T; b = 1: RN-rounded TF32 of the remainder), zero padded.
-__global__ void prep_weights_kernel(const double* __restrict__ U, int64_t K, int64_t S, int64_t ldu, int transpose,
+// W[b][s][k] (b = 0: RN-rounded TF32 of M; b = 1: RN-rounded TF32 of the remainder), zero padded,
+// with M(s, k) from U for s < S1 and from U2 for S1 <= s < S1 + S2.
+__global__ void prep_weights_kernel(const double* __restrict__ U, const double* __restrict__ U2, int64_t K,
+                                    int64_t S1, int64_t S2, int64_t ldu, int64_t ldu2, int transpose,
                                     float* __restrict__ W, int S_pad, int K_pad, int nb) {
   const int64_t total = (int64_t)S_pad * K_pad;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = e / K_pad, k = e - s * K_pad;
     float x = 0.f;
-    if (s < S && k < K) x = (float)(transpose ? U[k * ldu + s] : U[s * ldu + k]);
+    if (k < K) {
+      if (s < S1)
+        x = (float)(transpose ? U[k * ldu + s] : U[s * ldu + k]);
+      else if (s < S1 + S2)
+        x = (float)(transpose ? U2[k * ldu2 + (s - S1)] : U2[(s - S1) * ldu2 + k]);
+    }
     uint32_t h;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
     const float xh = __uint_as_float(h);
@@ -417,16 +433,28 @@ size_t ttm_tc_weights_bytes(int64_t K, int64_t S) {
 
 cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_t ldu, bool transpose, float* W,
                                    int nb, cudaStream_t s) {
+  return launch_prep_tc_weights2(U, S, ldu, nullptr, 0, 1, K, transpose, W, nb, s);
+}
+
+cudaError_t launch_prep_tc_weights2(const double* U, int64_t S1, int64_t ldu, const double* U2, int64_t S2,
+                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s) {
+  const int64_t S = S1 + S2;
   const int S_pad = (int)((S + 15) / 16 * 16), K_pad = (int)((K + 31) / 32 * 32);
   ProfScope prof(K_COPY, s);
-  prep_weights_kernel<<<64, 256, 0, s>>>(U, K, S, ldu, transpose ? 1 : 0, W, S_pad, K_pad, nb);
+  prep_weights_kernel<<<64, 256, 0, s>>>(U, U2, K, S1, S2, ldu, ldu2, transpose ? 1 : 0, W, S_pad, K_pad, nb);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int nb, float* out,
                           int64_t R2, double* norm_in, double* norm_out, int* status, cudaStream_t s) {
-  if (!ttm_tc_supported(K, S, nb) || rows <= 0 || R2 <= 0) return cudaErrorInvalidValue;
+  return launch_ttm_tc_resid(X, rows, K, W, S, S, nb, out, R2, norm_in, norm_out, nullptr, status, s);
+}
+
+cudaError_t launch_ttm_tc_resid(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int64_t S_store,
+                                int nb, float* out, int64_t R2, double* norm_in, double* norm_out, double* resid,
+                                int* status, cudaStream_t s) {
+  if (!ttm_tc_supported(K, S, nb) || rows <= 0 || R2 <= 0 || S_store < 0 || S_store > S) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || (reinterpret_cast<uintptr_t>(W) & 15) != 0)
     return cudaErrorInvalidValue;
   const int S_pad = (int)((S + 15) / 16 * 16), K_pad = (int)((K + 31) / 32 * 32);
@@ -449,9 +477,10 @@ cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nunits = ((rows + BM - 1) / BM) * n_ntiles;
   const int grid = (int)std::min<int64_t>(nunits, nsm);
-  TcParams P{rows, nkc, (int)S, S_pad, S_tile, n_ntiles, nb, nslot, R2, out, norm_in, norm_out, status};
+  TcParams P{rows, nkc, (int)S, (int)S_store, S_pad, S_tile, n_ntiles, nb, nslot, R2, out, norm_in, norm_out, resid,
+             status};
   ProfScope prof(K_TTM_TC, s, 2.0 * (double)rows * (double)K * (double)S,
-                 4.0 * (double)rows * ((double)K + (double)S));
+                 4.0 * (double)rows * ((double)K + (double)S_store));
   ttm_tc_kernel<<<grid, TC_THREADS, smem, s>>>(mx, mw, P);
   note_launch();
   return cudaGetLastError();
