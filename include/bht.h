@@ -77,23 +77,44 @@ typedef enum { BHT_F32 = 0, BHT_F64 = 1 } bht_dtype;
  *                   norms and the skip test stay in FP64. */
 typedef enum { BHT_PREC_FP64 = 0, BHT_PREC_MIXED = 1 } bht_precision;
 
+typedef struct bht_tree bht_tree;
+typedef struct bht_state bht_state;
+/* Rank / expansion predictor (no counterpart in the paper): a three-layer perceptron with bf16
+ * weights and activations, see bht_mlp_create. */
+typedef struct bht_mlp bht_mlp;
+
+/* Options of bht_l2r / htrise_update; NULL means all defaults (FP64, no predictor). */
 typedef struct {
   int32_t precision;      /* bht_precision */
   int32_t reserved0;
-  int64_t reserved1;
+  /* htrise_update only. With a predictor, every node whose residual Gram matrix is formed gets its
+   * 66 sketch features and a prediction; a node predicted not to expand skips its residual
+   * eigensolve when the exact residual energy trace(R R^T) <= eps_nw^2 confirms that the truncation
+   * of eq. svd_on_residual keeps nothing (the judge), and is truncated as usual otherwise (the
+   * fallback). The result is the same as without the predictor. */
+  const bht_mlp* predictor;
+  /* Optional host outputs, one row per tree node (node ids as bht_get_ranks), written for every
+   * node whose residual was formed and left untouched for the others: node_features [nodes][66]
+   * (fp32) and node_labels [nodes][2] (int64: residual rank r_R kept, residual dimension). They
+   * are the training pairs the method generates for the predictor. */
+  float* node_features;
+  int64_t* node_labels;
 } bht_opts;
-
-typedef struct bht_tree bht_tree;
-typedef struct bht_state bht_state;
 
 /* Outcome of one htrise_update call. */
 typedef struct {
   int32_t skipped;        /* 1: projection error <= eps_des, only the root grew (Algorithm 2) */
   int32_t reserved;
-  double eps_proj;        /* sqrt(max(||Y||^2 - ||C_1||^2, 0)), eq. relative_error_threshold */
+  double eps_proj;        /* projection error of eq. relative_error_threshold (FP64: sqrt(max(||Y||^2 -
+                             ||C_1||^2, 0)); mixed: square root of the energy removed on the nodes'
+                             complements) */
   double eps_des;         /* eps_rel * ||Y||_F of the new batch */
   double norm_y;          /* ||Y||_F of the new batch */
   int64_t n_items_total;  /* items in the accumulation after the call */
+  int32_t pred_nodes;     /* nodes the predictor saw */
+  int32_t pred_skipped;   /* of those, residual eigensolves skipped (prediction confirmed by the judge) */
+  int32_t pred_fallback;  /* predicted "no expansion" but the judge found residual energy above eps_nw^2 */
+  int32_t pred_missed;    /* predicted "expands" but the truncation kept nothing */
 } bht_update_info;
 
 /* Balanced binary dimension tree over d >= 2 modes of sizes dims[0..d-1]
@@ -202,6 +223,34 @@ bht_status bht_profile_enable(uint32_t class_mask);
 bht_status bht_profile_read(double* ms, int64_t* launches, double* flops, double* bytes, int32_t n,
                             int32_t reset);
 const char* bht_kernel_class_name(int32_t cls);
+
+/* ---------------------------------------------------------------------------------------------
+ * Rank / expansion predictor (no counterpart in the paper). Parameters as one fp32 vector, flattened
+ * W1 [hidden][f_in], b1 [hidden], W2 [hidden][hidden], b2 [hidden], W3 [2][hidden], b3 [2]; the library
+ * keeps an FP32 master copy, Adam moments, the last gradient and a bf16 copy on the current device.
+ * Forward: x~ = bf16(x); h1 = bf16(relu(bf16(W1) x~ + b1)); h2 = bf16(relu(bf16(W2) h1 + b2));
+ * o = bf16(W3) h2 + b3 (FP32 accumulation); o0 = rank as a fraction of the node's residual dimension,
+ * o1 = logit of "the batch expands the node". Loss: mean over the batch of (o0 - t0)^2 +
+ * log(1 + exp(o1)) - t1 o1. Pointers may be host or device.
+ * ------------------------------------------------------------------------------------------- */
+bht_status bht_mlp_create(int32_t f_in, int32_t hidden, const float* params, bht_mlp** out);
+bht_status bht_mlp_destroy(bht_mlp* net);
+bht_status bht_mlp_num_params(const bht_mlp* net, int64_t* n);
+/* Parameters (cap >= n) and, when grad_out is not NULL, the gradient of the last loss_grad call. */
+bht_status bht_mlp_get_params(const bht_mlp* net, float* out, int64_t cap, float* grad_out);
+/* out [B][2] = o for the inputs X [B][f_in]. */
+bht_status bht_mlp_forward(const bht_mlp* net, const float* X, int64_t B, float* out, void* stream);
+/* Loss of X [B][f_in] against targets T [B][2] into *loss (host, nullable); its gradient with
+ * respect to the bf16 weights (straight through the rounding) is kept for bht_mlp_adam_step. */
+bht_status bht_mlp_loss_grad(bht_mlp* net, const float* X, const float* T, int64_t B, double* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradient. */
+bht_status bht_mlp_adam_step(bht_mlp* net, double lr, void* stream);
+/* The predictor's 66 inputs for a node whose Gram matrix is G (c x c, FP64, symmetric positive
+ * semidefinite, host or device): f[i] = log10(s_i / s_1), i < 64, for the descending singular values
+ * of a Gaussian sketch of width 128 (-16 where there are none), f[64] = log10(tol / norm),
+ * f[65] = log2(c) / 10. seed selects the sketch. */
+bht_status bht_sketch_features(const double* G, int64_t c, double tol, double norm, uint64_t seed, float* feat,
+                               void* stream);
 
 const char* bht_last_error(void);
 const char* bht_version(void);

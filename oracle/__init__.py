@@ -13,3 +13,4 @@ from .bht_oracle import (  # noqa: F401
     BHTState, UpdateInfo, bht_l2r, htrise_update, project, reconstruct,
     compression_ratio, layer_shape,
 )
+from . import mlp_oracle  # noqa: F401

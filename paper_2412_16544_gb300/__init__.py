@@ -34,12 +34,15 @@ class BHTError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int64)]
+    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("predictor", ctypes.c_void_p),
+                ("node_features", ctypes.c_void_p), ("node_labels", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("skipped", ctypes.c_int32), ("reserved", ctypes.c_int32), ("eps_proj", ctypes.c_double),
-                ("eps_des", ctypes.c_double), ("norm_y", ctypes.c_double), ("n_items_total", ctypes.c_int64)]
+                ("eps_des", ctypes.c_double), ("norm_y", ctypes.c_double), ("n_items_total", ctypes.c_int64),
+                ("pred_nodes", ctypes.c_int32), ("pred_skipped", ctypes.c_int32), ("pred_fallback", ctypes.c_int32),
+                ("pred_missed", ctypes.c_int32)]
 
 
 def _load():
@@ -69,6 +72,14 @@ def _load():
         "bht_sym_eig": [vp, i64, vp, vp, i64, vp],
         "bht_mode_product_noalloc": [vp, i64, i64, vp, i64, vp, i64, vp, vp],
         "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
+        "bht_mlp_create": [i32, i32, vp, P(vp)],
+        "bht_mlp_destroy": [vp],
+        "bht_mlp_num_params": [vp, P(i64)],
+        "bht_mlp_get_params": [vp, vp, i64, vp],
+        "bht_mlp_forward": [vp, vp, i64, vp, vp],
+        "bht_mlp_loss_grad": [vp, vp, vp, i64, P(dbl), vp],
+        "bht_mlp_adam_step": [vp, dbl, vp],
+        "bht_sketch_features": [vp, i64, dbl, dbl, ctypes.c_uint64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -87,7 +98,9 @@ _lib = _load()
 EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
-            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc"]
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
+            "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
+            "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features"]
 KERNEL_CLASSES = 16
 
 
@@ -148,11 +161,14 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def _opts(precision):
-    if precision is None:
+def _opts(precision, predictor=None, node_features=None, node_labels=None):
+    if precision is None and predictor is None and node_features is None and node_labels is None:
         return None
-    code = {"fp64": BHT_PREC_FP64, "mixed": BHT_PREC_MIXED}.get(precision, precision)
-    return ctypes.byref(_Opts(int(code), 0, 0))
+    code = {"fp64": BHT_PREC_FP64, "mixed": BHT_PREC_MIXED, None: BHT_PREC_FP64}.get(precision, precision)
+    o = _Opts(int(code), 0, predictor.value if predictor is not None else None,
+              node_features.ctypes.data if node_features is not None else None,
+              node_labels.ctypes.data if node_labels is not None else None)
+    return ctypes.byref(o)
 
 
 # ---------------------------------------------------------------------------
@@ -166,6 +182,10 @@ class UpdateInfo:
     eps_des: float
     norm_y: float
     n_items_total: int
+    pred_nodes: int = 0
+    pred_skipped: int = 0
+    pred_fallback: int = 0
+    pred_missed: int = 0
 
 
 def bht_tree_create_balanced(dims) -> ctypes.c_void_p:
@@ -194,13 +214,21 @@ def bht_l2r(tree, Y, eps_rel: float, precision=None, stream=None) -> ctypes.c_vo
     return h
 
 
-def htrise_update(state, Y, eps_rel: float, precision=None, stream=None) -> UpdateInfo:
+def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predictor=None, node_features=None,
+                  node_labels=None) -> UpdateInfo:
+    """node_features (float32 [nodes][66]) and node_labels (int64 [nodes][2]): host numpy arrays the call
+    fills for the nodes whose residual it forms (the predictor's training pairs)."""
     ptr, code, shape, keep = _buffer(Y)
     info = _Info()
-    _check(_lib.htrise_update(state, ptr, code, int(shape[0]), float(eps_rel), _opts(precision),
-                              _stream(stream), ctypes.byref(info)), "htrise_update")
+    for a, dt in ((node_features, np.float32), (node_labels, np.int64)):
+        if a is not None and (a.dtype != dt or not a.flags.c_contiguous):
+            raise ValueError("node_features must be float32 and node_labels int64, C-contiguous")
+    _check(_lib.htrise_update(state, ptr, code, int(shape[0]), float(eps_rel),
+                              _opts(precision, predictor, node_features, node_labels), _stream(stream),
+                              ctypes.byref(info)), "htrise_update")
     del keep
-    return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total)
+    return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total,
+                      info.pred_nodes, info.pred_skipped, info.pred_fallback, info.pred_missed)
 
 
 def bht_get_dims(state):
@@ -339,3 +367,71 @@ def bht_version() -> str:
 
 def bht_last_error() -> str:
     return _lib.bht_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+# rank / expansion predictor
+# ---------------------------------------------------------------------------
+
+def bht_mlp_create(params, f_in: int = 66, hidden: int = 128) -> ctypes.c_void_p:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(_lib.bht_mlp_create(int(f_in), int(hidden), ctypes.c_void_p(p.ctypes.data), ctypes.byref(h)),
+           "bht_mlp_create")
+    return h
+
+
+def bht_mlp_destroy(net) -> None:
+    _check(_lib.bht_mlp_destroy(net), "bht_mlp_destroy")
+
+
+def bht_mlp_num_params(net) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.bht_mlp_num_params(net, ctypes.byref(n)), "bht_mlp_num_params")
+    return n.value
+
+
+def bht_mlp_get_params(net, grad: bool = False):
+    n = bht_mlp_num_params(net)
+    p = np.empty(n, dtype=np.float32)
+    g = np.empty(n, dtype=np.float32) if grad else None
+    _check(_lib.bht_mlp_get_params(net, ctypes.c_void_p(p.ctypes.data), n,
+                                   ctypes.c_void_p(g.ctypes.data) if grad else None), "bht_mlp_get_params")
+    return (p, g) if grad else p
+
+
+def bht_mlp_forward(net, X, stream=None) -> np.ndarray:
+    ptr, code, shape, keep = _buffer(X)
+    if code != BHT_F32:
+        raise ValueError("predictor inputs are float32")
+    out = np.empty((shape[0], 2), dtype=np.float32)
+    _check(_lib.bht_mlp_forward(net, ptr, int(shape[0]), ctypes.c_void_p(out.ctypes.data), _stream(stream)),
+           "bht_mlp_forward")
+    del keep
+    return out
+
+
+def bht_mlp_loss_grad(net, X, T, stream=None) -> float:
+    px, cx, sx, kx = _buffer(X)
+    pt, ct, st_, kt = _buffer(T)
+    if cx != BHT_F32 or ct != BHT_F32:
+        raise ValueError("predictor inputs and targets are float32")
+    loss = ctypes.c_double()
+    _check(_lib.bht_mlp_loss_grad(net, px, pt, int(sx[0]), ctypes.byref(loss), _stream(stream)), "bht_mlp_loss_grad")
+    del kx, kt
+    return loss.value
+
+
+def bht_mlp_adam_step(net, lr: float, stream=None) -> None:
+    _check(_lib.bht_mlp_adam_step(net, float(lr), _stream(stream)), "bht_mlp_adam_step")
+
+
+def bht_sketch_features(G, tol: float, norm: float, seed: int = 0, stream=None) -> np.ndarray:
+    ptr, code, shape, keep = _buffer(G)
+    if code != BHT_F64:
+        raise ValueError("G is float64")
+    f = np.empty(66, dtype=np.float32)
+    _check(_lib.bht_sketch_features(ptr, int(shape[0]), float(tol), float(norm), int(seed),
+                                    ctypes.c_void_p(f.ctypes.data), _stream(stream)), "bht_sketch_features")
+    del keep
+    return f

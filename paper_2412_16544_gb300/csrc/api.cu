@@ -95,7 +95,7 @@ const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
-                                             "house_f64",      "other"};
+                                             "house_f64",      "mlp",            "other"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -279,6 +279,23 @@ struct bht_state {
   }
   int64_t r11() const { return rank[tree.nodes[0].child[0]]; }
   int64_t r12() const { return rank[tree.nodes[0].child[1]]; }
+};
+
+// Rank / expansion predictor: FP32 master parameters, Adam moments, the last gradient and the bf16
+// copy the kernels read, all on the device where it was created. Layout of the flat parameter
+// vector: W1 [H][F], b1 [H], W2 [H][H], b2 [H], W3 [2][H], b3 [2].
+struct bht_mlp {
+  int f_in = 66, hidden = 128;
+  int64_t P = 0;
+  float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  __nv_bfloat16* wq = nullptr;
+  int64_t steps = 0;
+  int64_t oW1() const { return 0; }
+  int64_t ob1() const { return (int64_t)hidden * f_in; }
+  int64_t oW2() const { return ob1() + hidden; }
+  int64_t ob2() const { return oW2() + (int64_t)hidden * hidden; }
+  int64_t oW3() const { return ob2() + hidden; }
+  int64_t ob3() const { return oW3() + 2 * (int64_t)hidden; }
 };
 
 namespace {
@@ -571,10 +588,12 @@ void eig_values64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t
 // discarded energy after r kept values is trace - sum_{i<r} lam_i, so eigenvalues are bisected from the
 // top, in chunks that double, until some r >= rmin meets tail <= eps_nw2 (or all are known).
 // Called after the tridiagonalisation has finished (the stream was synchronised).
-int64_t eig_rank64(EigOut& eo, double eps_nw2, int64_t rmin, int64_t rmax, cudaStream_t s) {
+int64_t eig_rank64(EigOut& eo, double eps_nw2, int64_t rmin, int64_t rmax, cudaStream_t s,
+                   double trace = std::nan("")) {
   const int64_t n = eo.n;
   double tr = 0.0;
   for (double v : eo.h_diag) tr += v;
+  if (std::isfinite(trace)) tr = trace;  // the trace of the Gram matrix itself, when the caller has it
   eo.trace = tr;
   rmax = std::min(rmax, n);
   // every eigenvalue in one launch: a Sturm sweep is latency-bound, so fewer eigenvalues do not cost less
@@ -814,6 +833,32 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
     }
   }
   return C;  // [N][r11][r12]
+}
+
+// Predictor forward pass on X (device, [B][F] fp32) into out (device, [B][2] fp32). With `keep`
+// the intermediates stay in the given buffers for the backward pass.
+struct MlpActs {
+  DBuf xq, pre1, h1, pre2, h2, out;
+};
+
+void mlp_forward(const bht_mlp* net, const float* X, int64_t B, MlpActs& A, cudaStream_t s) {
+  const int F = net->f_in, H = net->hidden;
+  A.xq = DBuf(sizeof(__nv_bfloat16) * B * F, s);
+  A.pre1 = DBuf(sizeof(float) * B * H, s);
+  A.h1 = DBuf(sizeof(__nv_bfloat16) * B * H, s);
+  A.pre2 = DBuf(sizeof(float) * B * H, s);
+  A.h2 = DBuf(sizeof(__nv_bfloat16) * B * H, s);
+  A.out = DBuf(sizeof(float) * B * 2, s);
+  ck(launch_mlp_round_input(X, B * F, A.xq.as<__nv_bfloat16>(), s), "mlp input");
+  ck(launch_mlp_linear(A.xq.as<__nv_bfloat16>(), B, F, net->wq + net->oW1(), net->w + net->ob1(), H,
+                       A.pre1.as<float>(), A.h1.as<__nv_bfloat16>(), nullptr, s),
+     "mlp layer 1");
+  ck(launch_mlp_linear(A.h1.as<__nv_bfloat16>(), B, H, net->wq + net->oW2(), net->w + net->ob2(), H,
+                       A.pre2.as<float>(), A.h2.as<__nv_bfloat16>(), nullptr, s),
+     "mlp layer 2");
+  ck(launch_mlp_linear(A.h2.as<__nv_bfloat16>(), B, H, net->wq + net->oW3(), net->w + net->ob3(), 2, nullptr, nullptr,
+                       A.out.as<float>(), s),
+     "mlp layer 3");
 }
 
 Arith make_arith(int precision, double eps_rel, int* d_status) {
@@ -1064,13 +1109,17 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
     copy_convert(Cbar, st->root + st->n_items * r11_old * r12_old, BHT_F64, s);
     st->n_items += N;
     ck(cudaStreamSynchronize(s), "sync");
-    if (info) *info = bht_update_info{1, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items};
+    if (info) *info = bht_update_info{1, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items, 0, 0, 0, 0};
     return BHT_OK;
   }
   Cbar = LTensor();
 
   // Steps 2-3 layer by layer; the new cores live in a shadow copy until commit
   const double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
+  const bool want_feat = opts && (opts->predictor || opts->node_features);
+  struct {
+    int32_t nodes = 0, skipped = 0, fallback = 0, missed = 0;
+  } pstat;
   std::vector<int64_t> rank = st->rank;
   std::vector<double*> U = st->U, Q = st->Q;
   std::vector<double*> fresh;  // buffers created by this call
@@ -1082,6 +1131,9 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
       const auto& ids = t.layers[layer];
       std::vector<EigOut> eo(ids.size());
       std::vector<int64_t> alpha(ids.size()), rold(ids.size()), qc(ids.size());
+      std::vector<DBuf> Gs(ids.size()), sk;
+      DBuf trd(sizeof(double) * ids.size(), s), feats(sizeof(float) * 66 * ids.size(), s);
+      ck(cudaMemsetAsync(trd.p, 0, sizeof(double) * ids.size(), s), "memset");
       for (size_t k = 0; k < ids.size(); ++k) {
         const int ax = C.axis_of(ids[k]);
         const int64_t a = C.dims[ax];
@@ -1093,10 +1145,56 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         // I - U U^T = Q Q^T, so R R^T = Q (W W^T) Q^T for W = Q^T C_(j): the nonzero eigenpairs of the
         // residual Gram are those of the qc x qc Gram W W^T, mapped through Q.
         LTensor W = ttm_any(C, ax, Q[ids[k]], 1, qc[k], qc[k], false, ar, s);
-        DBuf G(sizeof(double) * qc[k] * qc[k], s);
-        gram_any(W, ax, G.as<double>(), ar, s);
-        eig_tridiag64(G.as<double>(), qc[k], eo[k], st->d_status, s);
+        Gs[k] = DBuf(sizeof(double) * qc[k] * qc[k], s);
+        gram_any(W, ax, Gs[k].as<double>(), ar, s);
+        // the exact residual energy ||R||^2 = trace(R R^T), read with the status word below
+        ck(launch_trace(Gs[k].as<double>(), qc[k], trd.as<double>() + k, s), "residual energy");
+        if (want_feat) {
+          sk.push_back(DBuf(sketch_workspace_bytes(qc[k], 128), s));
+          ck(launch_sketch_features(Gs[k].as<double>(), qc[k], 128, std::sqrt(eps_nw2), trd.as<double>() + k,
+                                    complement_seed(ids[k], st->n_items) ^ 0x736b65746368ull, sk.back().p,
+                                    feats.as<float>() + 66 * k, s),
+             "sketch features");
+        }
       }
+      std::vector<double> tr(ids.size(), 0.0);
+      ck(cudaMemcpyAsync(tr.data(), trd.p, sizeof(double) * ids.size(), cudaMemcpyDeviceToHost, s), "D2H energies");
+      // the predictor's view of the layer: a node predicted not to expand skips its eigensolve when the
+      // judge (the exact residual energy) confirms that the truncation keeps nothing
+      std::vector<char> skip_eig(ids.size(), 0), pred_expand(ids.size(), 1);
+      if (want_feat) {
+        std::vector<float> hf(66 * ids.size());
+        ck(cudaMemcpyAsync(hf.data(), feats.p, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, s), "D2H features");
+        std::vector<float> ho(2 * ids.size(), 0.f);
+        if (opts->predictor) {
+          MlpActs A;
+          mlp_forward(opts->predictor, feats.as<float>(), (int64_t)ids.size(), A, s);
+          ck(cudaMemcpyAsync(ho.data(), A.out.p, sizeof(float) * ho.size(), cudaMemcpyDeviceToHost, s), "D2H preds");
+          ck(cudaStreamSynchronize(s), "sync");
+        } else {
+          ck(cudaStreamSynchronize(s), "sync");
+        }
+        for (size_t k = 0; k < ids.size(); ++k) {
+          if (qc[k] <= 0) continue;
+          if (opts->node_features)
+            std::memcpy(opts->node_features + 66 * (size_t)ids[k], hf.data() + 66 * k, sizeof(float) * 66);
+          if (!opts->predictor) continue;
+          ++pstat.nodes;
+          pred_expand[k] = ho[2 * k + 1] > 0.f;
+          if (!pred_expand[k]) {
+            if (tr[k] <= eps_nw2) {
+              skip_eig[k] = 1;
+              ++pstat.skipped;
+            } else {
+              ++pstat.fallback;
+            }
+          }
+        }
+      } else {
+        ck(cudaStreamSynchronize(s), "sync");
+      }
+      for (size_t k = 0; k < ids.size(); ++k)
+        if (qc[k] > 0 && !skip_eig[k]) eig_tridiag64(Gs[k].as<double>(), qc[k], eo[k], st->d_status, s);
       check_status(st, s);
       std::vector<int> grown_parents;
       for (size_t k = 0; k < ids.size(); ++k) {
@@ -1104,7 +1202,12 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         const int64_t a = alpha[k], r0 = rold[k], c = qc[k];
         if (c <= 0) continue;
         // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
-        const int64_t rR = eig_rank64(eo[k], eps_nw2, 0, c, s);
+        const int64_t rR = skip_eig[k] ? 0 : eig_rank64(eo[k], eps_nw2, 0, c, s, tr[k]);
+        if (opts && opts->node_labels) {
+          opts->node_labels[2 * (size_t)id] = rR;
+          opts->node_labels[2 * (size_t)id + 1] = c;
+        }
+        if (opts && opts->predictor && pred_expand[k] && rR == 0) ++pstat.missed;
         if (rR == 0) continue;
         DBuf Zk;
         Zk.p = eig_vectors64(eo[k], rR, s);  // [c][rR]
@@ -1201,7 +1304,9 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   st->rank = rank;
   st->n_items += N;
   ck(cudaStreamSynchronize(s), "sync");
-  if (info) *info = bht_update_info{0, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items};
+  if (info)
+    *info = bht_update_info{0, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items, pstat.nodes, pstat.skipped,
+                            pstat.fallback, pstat.missed};
   BHT_API_END
 }
 
@@ -1344,6 +1449,139 @@ bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, 
   ck(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   ck(cudaStreamSynchronize(s), "sync");
   if (h) fail((bht_status)h, "a bounded device-side wait gave up (eigensolver)");
+  BHT_API_END
+}
+
+bht_status bht_mlp_create(int32_t f_in, int32_t hidden, const float* params, bht_mlp** out) {
+  BHT_API_BEGIN
+  if (!params || !out) fail(BHT_EINVAL, "null argument");
+  if (f_in < 1 || f_in > 4096 || hidden < 1 || hidden > 4096) fail(BHT_EINVAL, "f_in and hidden must be in [1, 4096]");
+  bht_mlp* net = new bht_mlp();
+  net->f_in = f_in;
+  net->hidden = hidden;
+  net->P = (int64_t)hidden * f_in + hidden + (int64_t)hidden * hidden + hidden + 2 * (int64_t)hidden + 2;
+  const size_t fb = sizeof(float) * (size_t)net->P;
+  cudaError_t e = cudaMalloc(&net->w, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->m, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->v, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->g, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->wq, sizeof(__nv_bfloat16) * (size_t)net->P);
+  if (e == cudaSuccess) e = cudaMemcpy(net->w, params, fb, is_device_ptr(params) ? cudaMemcpyDeviceToDevice
+                                                                                  : cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(net->m, 0, fb);
+  if (e == cudaSuccess) e = cudaMemset(net->v, 0, fb);
+  if (e == cudaSuccess) e = cudaMemset(net->g, 0, fb);
+  if (e == cudaSuccess) e = launch_mlp_to_bf16(net->w, net->P, net->wq, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bht_mlp_destroy(net);
+    fail(BHT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = net;
+  BHT_API_END
+}
+
+bht_status bht_mlp_destroy(bht_mlp* net) {
+  if (!net) return BHT_OK;
+  cudaFree(net->w);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  cudaFree(net->g);
+  cudaFree(net->wq);
+  delete net;
+  return BHT_OK;
+}
+
+bht_status bht_mlp_num_params(const bht_mlp* net, int64_t* n) {
+  if (!net || !n) return BHT_EINVAL;
+  *n = net->P;
+  return BHT_OK;
+}
+
+bht_status bht_mlp_get_params(const bht_mlp* net, float* out, int64_t cap, float* grad_out) {
+  BHT_API_BEGIN
+  if (!net || !out) fail(BHT_EINVAL, "null argument");
+  if (cap < net->P) fail(BHT_ECAPACITY, "cap < number of parameters");
+  ck(cudaMemcpy(out, net->w, sizeof(float) * net->P, cudaMemcpyDefault), "copy parameters");
+  if (grad_out) ck(cudaMemcpy(grad_out, net->g, sizeof(float) * net->P, cudaMemcpyDefault), "copy gradient");
+  BHT_API_END
+}
+
+bht_status bht_mlp_forward(const bht_mlp* net, const float* X, int64_t B, float* out, void* stream) {
+  BHT_API_BEGIN
+  if (!net || !X || !out) fail(BHT_EINVAL, "null argument");
+  if (B < 1) fail(BHT_EINVAL, "B must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf staging;
+  const float* dX = static_cast<const float*>(stage_input(X, BHT_F32, B * net->f_in, staging, s));
+  MlpActs A;
+  mlp_forward(net, dX, B, A, s);
+  ck(cudaMemcpyAsync(out, A.out.p, sizeof(float) * 2 * B, cudaMemcpyDefault, s), "copy out");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_mlp_loss_grad(bht_mlp* net, const float* X, const float* T, int64_t B, double* loss, void* stream) {
+  BHT_API_BEGIN
+  if (!net || !X || !T) fail(BHT_EINVAL, "null argument");
+  if (B < 1) fail(BHT_EINVAL, "B must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int F = net->f_in, H = net->hidden;
+  DBuf sx, st;
+  const float* dX = static_cast<const float*>(stage_input(X, BHT_F32, B * F, sx, s));
+  const float* dT = static_cast<const float*>(stage_input(T, BHT_F32, B * 2, st, s));
+  MlpActs A;
+  mlp_forward(net, dX, B, A, s);
+  DBuf dO(sizeof(float) * B * 2, s), da2(sizeof(float) * B * H, s), da1(sizeof(float) * B * H, s);
+  DBuf L(sizeof(double), s);
+  ck(cudaMemsetAsync(L.p, 0, sizeof(double), s), "memset");
+  ck(launch_mlp_loss(A.out.as<float>(), dT, B, dO.as<float>(), L.as<double>(), s), "mlp loss");
+  ck(launch_mlp_outer(dO.as<float>(), B, 2, A.h2.as<__nv_bfloat16>(), H, net->g + net->oW3(), net->g + net->ob3(), s),
+     "dW3");
+  ck(launch_mlp_backprop(dO.as<float>(), B, 2, net->wq + net->oW3(), H, A.pre2.as<float>(), da2.as<float>(), s),
+     "da2");
+  ck(launch_mlp_outer(da2.as<float>(), B, H, A.h1.as<__nv_bfloat16>(), H, net->g + net->oW2(), net->g + net->ob2(), s),
+     "dW2");
+  ck(launch_mlp_backprop(da2.as<float>(), B, H, net->wq + net->oW2(), H, A.pre1.as<float>(), da1.as<float>(), s),
+     "da1");
+  ck(launch_mlp_outer(da1.as<float>(), B, H, A.xq.as<__nv_bfloat16>(), F, net->g + net->oW1(), net->g + net->ob1(), s),
+     "dW1");
+  double h = 0.0;
+  ck(cudaMemcpyAsync(&h, L.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H loss");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (loss) *loss = h;
+  BHT_API_END
+}
+
+bht_status bht_mlp_adam_step(bht_mlp* net, double lr, void* stream) {
+  BHT_API_BEGIN
+  if (!net) fail(BHT_EINVAL, "null argument");
+  if (!(lr > 0.0) || !std::isfinite(lr)) fail(BHT_EINVAL, "lr must be positive");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  net->steps += 1;
+  const double c1 = 1.0 / (1.0 - std::pow(0.9, (double)net->steps));
+  const double c2 = 1.0 / (1.0 - std::pow(0.999, (double)net->steps));
+  ck(launch_mlp_adam(net->w, net->m, net->v, net->g, net->P, (float)lr, (float)c1, (float)c2, s), "adam");
+  ck(launch_mlp_to_bf16(net->w, net->P, net->wq, s), "bf16 copy");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_sketch_features(const double* G, int64_t c, double tol, double norm, uint64_t seed, float* feat,
+                               void* stream) {
+  BHT_API_BEGIN
+  if (!G || !feat) fail(BHT_EINVAL, "null argument");
+  if (c < 1 || c > 4096) fail(BHT_EINVAL, "c must be in [1, 4096]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf sg;
+  const double* dG = static_cast<const double*>(stage_input(G, BHT_F64, c * c, sg, s));
+  DBuf work(sketch_workspace_bytes(c, 128), s), f(sizeof(float) * 66, s), n2(sizeof(double), s);
+  const double norm2 = norm * norm;
+  ck(cudaMemcpyAsync(n2.p, &norm2, sizeof(double), cudaMemcpyHostToDevice, s), "H2D norm");
+  ck(launch_sketch_features(dG, c, 128, tol, n2.as<double>(), seed, work.p, f.as<float>(), s), "sketch features");
+  ck(cudaMemcpyAsync(feat, f.p, sizeof(float) * 66, cudaMemcpyDefault, s), "copy features");
+  ck(cudaStreamSynchronize(s), "sync");
   BHT_API_END
 }
 

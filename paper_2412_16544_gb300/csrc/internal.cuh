@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace bht {
@@ -28,8 +29,9 @@ enum KernelClass {
   K_EIG_BACK = 10,
   K_TTM_F32 = 11,
   K_HOUSE = 12,
-  K_OTHER = 13,
-  K_NUM_CLASSES = 14
+  K_MLP = 13,
+  K_OTHER = 14,
+  K_NUM_CLASSES = 15
 };
 const char* kernel_class_name(int cls);
 
@@ -87,6 +89,27 @@ template <typename Tin>
 cudaError_t launch_ttm_f32_resid(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A,
                                  int64_t T, int64_t B, int64_t S, int64_t S_store, int64_t R2, double* resid,
                                  cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Rank / expansion predictor (mlp.cu): bf16 weights and activations, FP32 accumulation.
+// ---------------------------------------------------------------------------
+cudaError_t launch_mlp_round_input(const float* X, int64_t n, __nv_bfloat16* out, cudaStream_t s);
+cudaError_t launch_mlp_linear(const __nv_bfloat16* in, int64_t B, int nin, const __nv_bfloat16* W, const float* bias,
+                              int nout, float* pre, __nv_bfloat16* act, float* out, cudaStream_t s);
+cudaError_t launch_mlp_loss(const float* o, const float* T, int64_t B, float* dO, double* loss, cudaStream_t s);
+cudaError_t launch_mlp_outer(const float* A, int64_t B, int R, const __nv_bfloat16* Bm, int C, float* G, float* gb,
+                             cudaStream_t s);
+cudaError_t launch_mlp_backprop(const float* dA, int64_t B, int J, const __nv_bfloat16* W, int I, const float* pre,
+                                float* D, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* w, float* m, float* v, const float* g, int64_t n, float lr, float c1, float c2,
+                            cudaStream_t s);
+cudaError_t launch_mlp_to_bf16(const float* w, int64_t n, __nv_bfloat16* out, cudaStream_t s);
+// 66 features of the node whose Gram matrix is G (c x c, FP64): log10 of the sketched singular values
+// relative to the largest (64), log10(tol / sqrt(*norm2)) with norm2 on the device, log2(c) / 10.
+// work: sketch_workspace_bytes(c, k).
+size_t sketch_workspace_bytes(int64_t c, int k);
+cudaError_t launch_sketch_features(const double* G, int64_t c, int k, double tol, const double* norm2, uint64_t seed,
+                                   void* work, float* feat, cudaStream_t s);
 
 // out[s * T + t] = (float) U[s * ms + t * mt]
 cudaError_t launch_cast_matrix(const double* U, int64_t ms, int64_t mt, int64_t S, int64_t T, float* out,
