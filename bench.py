@@ -38,30 +38,49 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default=os.environ.get("BHT_BENCH_PRECISION", "mixed"))
-    ap.add_argument("--eps", type=float, default=1e-2)
-    ap.add_argument("--increments", type=int, default=20)
-    ap.add_argument("--items", type=int, default=32)
+    ap.add_argument("--eps", type=float, default=None, help="default: 1e-2 (spectral, sensor), 1e-3 (bumps, multivar)")
+    ap.add_argument("--increments", type=int, default=None, help="default: 20 (spectral), 4 (bumps, sensor, multivar)")
+    ap.add_argument("--items", type=int, default=None, help="default: 32 (spectral), 8 (bumps), 64 (sensor)")
     ap.add_argument("--grid", type=int, default=64, help="edge of the cubic snapshot")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--workload", choices=["spectral", "multivar"], default="spectral",
-                    help="spectral: one 64^3 field stream (the headline); multivar: 16 independent streams of "
+    ap.add_argument("--workload", choices=["spectral", "bumps", "sensor", "multivar"], default="spectral",
+                    help="spectral: the 64^3 advected field stream (the headline); bumps: 16^3 Gaussian bumps, FP64 "
+                         "items; sensor: 24^5 Chebyshev sensor responses; multivar: 16 independent streams of "
                          "5 x 48^3 items with increment sizes U{1..64}, compressed concurrently")
     ap.add_argument("--streams", type=int, default=16)
-    return ap.parse_args(argv)
+    a = ap.parse_args(argv)
+    defaults = {"spectral": (1e-2, 20, 32), "bumps": (1e-3, 4, 8), "sensor": (1e-2, 4, 64), "multivar": (1e-3, 4, 0)}
+    eps, inc, items = defaults[a.workload]
+    a.eps = eps if a.eps is None else a.eps
+    a.increments = inc if a.increments is None else a.increments
+    a.items = items if a.items is None else a.items
+    return a
+
+
+def item_dims(a):
+    return {"spectral": (a.grid,) * 3, "bumps": (16, 16, 16), "sensor": (24,) * 5}[a.workload]
 
 
 def workload_name(a):
-    return (f"advected spectral field {a.grid}^3 (|k|<=16, |k|^-5/3), {a.increments} increments x {a.items} "
-            f"snapshots, eps_rel={a.eps:g}")
+    what = {"spectral": f"advected spectral field {a.grid}^3 (|k|<=16, |k|^-5/3)",
+            "bumps": "16^3 Gaussian bumps (5 separable terms, FP64 items)",
+            "sensor": "24^5 Chebyshev sensor responses (20 separable degree-6 terms + 0.01 N(0,1))"}[a.workload]
+    return f"{what}, {a.increments} increments x {a.items} items, eps_rel={a.eps:g}"
 
 
 def gen_stream(a, seed):
     import bht_synth
-    Y = bht_synth.spectral_field(seed, 0, a.increments * a.items, n=a.grid)
-    return Y.reshape(a.increments, a.items, a.grid, a.grid, a.grid)
+    n = a.increments * a.items
+    if a.workload == "bumps":
+        Y = bht_synth.gaussian_bumps(seed, 0, n)
+    elif a.workload == "sensor":
+        Y = bht_synth.chebyshev_sensor(seed, 0, n)
+    else:
+        Y = bht_synth.spectral_field(seed, 0, n, n=a.grid)
+    return Y.reshape((a.increments, a.items) + item_dims(a))
 
 
 # ---------------------------------------------------------------------------
@@ -176,7 +195,7 @@ def run_ours(a, rank, world, local_rank):
     Yh = gen_stream(a, seed=rank)                  # each rank compresses its own independent stream
     Yd = torch.from_numpy(Yh).to(dev)              # resident in HBM before the timed region
     bytes_per_step = Yh.nbytes
-    tree = B.bht_tree_create_balanced([a.grid] * 3)
+    tree = B.bht_tree_create_balanced(list(item_dims(a)))
     stream = torch.cuda.current_stream()
 
     def one_pass(prec, src):
@@ -186,6 +205,9 @@ def run_ours(a, rank, world, local_rank):
             info = B.htrise_update(st, src[k], a.eps, precision=prec)
             skips += int(info.skipped)
         return st, skips
+
+    L2_BYTES = 129 * 1024 * 1024
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if bytes_per_step <= L2_BYTES else None
 
     def timed(prec, steps, warmup, profile_mask=0):
         for _ in range(warmup):
@@ -201,19 +223,23 @@ def run_ours(a, rank, world, local_rank):
         sampler = ClockSampler(local_rank)
         sampler.start()
         time.sleep(0.3)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         states = []
-        e0.record(stream)
+        total_ms = 0.0
         for _ in range(steps):
+            if flush is not None:
+                flush.add_(1)  # a write larger than L2 between timed steps (small workloads only)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             st, skips = one_pass(prec, Yd)
+            e1.record(stream)
             states.append((st, skips))
-        e1.record(stream)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
         clocks = sampler.stop()
         B.bht_profile_enable(0)
         launches = B.bht_launch_count(reset=True)
         prof = B.bht_profile_read(reset=True, work=True)
-        ms = job_max(dist, e0.elapsed_time(e1) / steps, dev)
+        ms = job_max(dist, total_ms / steps, dev)
         if dist is not None:
             dist.barrier()
         return ms, launches / steps, prof, clocks, states
@@ -249,7 +275,7 @@ def run_ours(a, rank, world, local_rank):
         rec = B.ht_reconstruct(st, k * a.items, a.items, dtype="float32")
         errs.append(float(torch.linalg.vector_norm(rec - Yd[k]) / torch.linalg.vector_norm(Yd[k])))
     cores = B.bht_num_elements(st)
-    cr = a.increments * a.items * a.grid ** 3 / cores
+    cr = Yh.size / cores
     for s_, _ in states:
         B.bht_state_destroy(s_)
 
@@ -301,15 +327,16 @@ def run_ours(a, rank, world, local_rank):
             lines = open(path).read().splitlines()
         except OSError:
             return None
+        tag = f"spectral{a.grid}" if a.workload == "spectral" and a.eps == 1e-2 else None
         for ln in lines:
             f = ln.split()
-            if len(f) == 4 and not ln.startswith("#") and f[0] == name:
-                src = os.path.join(os.path.dirname(os.path.abspath(__file__)), f[2])
+            if len(f) == 5 and not ln.startswith("#") and f[0] == tag and f[1] == name:
+                src = os.path.join(os.path.dirname(os.path.abspath(__file__)), f[3])
                 try:
                     h = hashlib.sha256(open(src, "rb").read()).hexdigest()
                 except OSError:
                     return None
-                return float(f[1]) if h == f[3] else None
+                return float(f[2]) if h == f[4] else None
         return None
 
     def roof(name):
@@ -346,7 +373,10 @@ def run_ours(a, rank, world, local_rank):
         "dtype": "tf32" if a.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "precision": a.precision, "items_per_step": a.increments * a.items,
                    "bytes_per_step": bytes_per_step, "parallelism": f"{world} independent streams",
-                   "l2": f"inputs ({bytes_per_step / 1e6:.0f} MB per stream) larger than L2 (129 MB); no flush"},
+                   "l2": (f"inputs ({bytes_per_step / 1e6:.0f} MB per stream) larger than L2 (129 MB); no flush"
+                          if flush is None else
+                          f"inputs ({bytes_per_step / 1e6:.1f} MB) smaller than L2: a 258 MB write flushes L2 "
+                          f"before every timed step (outside the timed region)")},
         "roofline": roofline, "roofline_ttm_tc": roofline_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "plain_fp64": plain,
@@ -368,8 +398,8 @@ def run_multistream(a):
     import bht_synth
     import paper_2412_16544_gb300 as B
 
-    eps = a.eps if a.eps != 1e-2 else 1e-3
-    incs = a.increments if a.increments != 20 else 4
+    eps = a.eps
+    incs = a.increments
     data, total = [], 0
     for sidx in range(a.streams):
         sizes = [int(x) for x in bht_synth.increment_sizes(sidx, incs)]
