@@ -9,7 +9,9 @@
 // B = prod_{i>j} I_i; merging two children's axes into their parent's axis is
 // a C-order reshape and moves no data.
 #include <algorithm>
+#include <exception>
 #include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -84,6 +86,40 @@ void prof_resolve() {
     g_prof_pool.push_back(r.b);
   }
   g_prof_pending.clear();
+}
+
+// The thread-local counters of a worker thread (launches, per-class profile), carried back to the
+// thread that made the library call.
+struct ThreadCounters {
+  int64_t launches = 0;
+  double ms[bht::K_NUM_CLASSES] = {}, flops[bht::K_NUM_CLASSES] = {}, bytes[bht::K_NUM_CLASSES] = {};
+  int64_t n[bht::K_NUM_CLASSES] = {};
+};
+
+ThreadCounters take_thread_counters() {
+  prof_resolve();
+  ThreadCounters c;
+  c.launches = g_launches;
+  g_launches = 0;
+  for (int i = 0; i < bht::K_NUM_CLASSES; ++i) {
+    c.ms[i] = g_prof_ms[i];
+    c.n[i] = g_prof_n[i];
+    c.flops[i] = g_prof_flops[i];
+    c.bytes[i] = g_prof_bytes[i];
+    g_prof_ms[i] = g_prof_flops[i] = g_prof_bytes[i] = 0.0;
+    g_prof_n[i] = 0;
+  }
+  return c;
+}
+
+void add_thread_counters(const ThreadCounters& c) {
+  g_launches += c.launches;
+  for (int i = 0; i < bht::K_NUM_CLASSES; ++i) {
+    g_prof_ms[i] += c.ms[i];
+    g_prof_n[i] += c.n[i];
+    g_prof_flops[i] += c.flops[i];
+    g_prof_bytes[i] += c.bytes[i];
+  }
 }
 }  // namespace
 
@@ -835,6 +871,68 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
   return C;  // [N][r11][r12]
 }
 
+// Run work(k, stream_k) for the n nodes of a tree layer at the same time: one host thread and one
+// CUDA stream per node, each starting after the work already queued on s; s then waits for all of
+// them. The nodes of a layer are independent (their Gram matrices, eigensolves and bases touch only
+// their own state), and a node's chain is a sequence of small FP64 kernels separated by host
+// decisions, so running the chains side by side fills SMs one chain alone leaves idle. Errors are
+// rethrown in the calling thread; launch counts and profiles are added to its counters.
+template <typename F>
+void run_nodes(int n, cudaStream_t s, F&& work) {
+  if (n <= 0) return;
+  if (n == 1) {
+    work(0, s);
+    return;
+  }
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "cudaGetDevice");
+  const uint32_t mask = g_prof_mask;
+  cudaEvent_t ready = nullptr;
+  ck(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "event");
+  ck(cudaEventRecord(ready, s), "event record");
+  std::vector<cudaStream_t> ss(n, nullptr);
+  std::vector<cudaEvent_t> done(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    ck(cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking), "stream");
+    ck(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming), "event");
+    ck(cudaStreamWaitEvent(ss[k], ready, 0), "stream wait");
+  }
+  std::vector<int> err_status(n, BHT_OK);
+  std::vector<std::string> err_msg(n);
+  std::vector<ThreadCounters> cnt(n);
+  std::vector<std::thread> th;
+  for (int k = 0; k < n; ++k) {
+    th.emplace_back([&, k] {
+      cudaSetDevice(dev);
+      g_prof_mask = mask;
+      try {
+        work(k, ss[k]);
+      } catch (const Fail& f) {
+        err_status[k] = f.st;
+        err_msg[k] = g_err;
+      } catch (const std::bad_alloc&) {
+        err_status[k] = BHT_ENOMEM;
+        err_msg[k] = "host allocation failed";
+      } catch (...) {
+        err_status[k] = BHT_ECUDA;
+        err_msg[k] = "unexpected host exception";
+      }
+      cudaEventRecord(done[k], ss[k]);
+      cnt[k] = take_thread_counters();
+    });
+  }
+  for (auto& t : th) t.join();
+  for (int k = 0; k < n; ++k) {
+    add_thread_counters(cnt[k]);
+    cudaStreamWaitEvent(s, done[k], 0);
+    cudaEventDestroy(done[k]);
+    cudaStreamDestroy(ss[k]);
+  }
+  cudaEventDestroy(ready);
+  for (int k = 0; k < n; ++k)
+    if (err_status[k] != BHT_OK) fail((bht_status)err_status[k], err_msg[k]);
+}
+
 // Predictor forward pass on X (device, [B][F] fp32) into out (device, [B][2] fp32). With `keep`
 // the intermediates stay in the given buffers for the backward pass.
 struct MlpActs {
@@ -1031,28 +1129,34 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
     for (int layer = t.p; layer >= 1; --layer) {
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
-      // HOSVD of the layer: every node from the same intermediate
-      std::vector<EigOut> eo(ids.size());
-      for (size_t k = 0; k < ids.size(); ++k) {
-        const int ax = C.axis_of(ids[k]);
+      // HOSVD of the layer: every node from the same intermediate, the nodes side by side
+      run_nodes((int)ids.size(), s, [&](int k, cudaStream_t sk) {
+        const int id = ids[k];
+        const int ax = C.axis_of(id);
         const int64_t I = C.dims[ax];
-        DBuf G(sizeof(double) * I * I, s);
-        gram_any(C, ax, G.as<double>(), ar, s);
-        eig_tridiag64(G.as<double>(), I, eo[k], st->d_status, s);
-      }
-      check_status(st, s);
+        DBuf status(sizeof(int), sk);
+        ck(cudaMemsetAsync(status.p, 0, sizeof(int), sk), "memset status");
+        Arith ark = ar;
+        ark.d_status = status.as<int>();
+        EigOut eo;
+        {
+          DBuf G(sizeof(double) * I * I, sk);
+          gram_any(C, ax, G.as<double>(), ark, sk);
+          eig_tridiag64(G.as<double>(), I, eo, status.as<int>(), sk);
+          check_status_word(status.as<int>(), sk);
+        }
+        const int64_t r = eig_rank64(eo, eps_nw2, 1, I, sk);  // eq. ht_leaf_svd, r >= 1
+        double* U = eig_vectors64(eo, r, sk);
+        st->U[id] = U;
+        st->rank[id] = r;
+        // kept for HT-RISE: the residual of a later batch lives in span(Q) (eq. compute_residual)
+        st->Q[id] = complement_of(U, I, r, complement_seed(id, 0), status.as<int>(), sk);
+      });
       std::vector<const double*> Us;
       std::vector<int64_t> rs;
-      for (size_t k = 0; k < ids.size(); ++k) {
-        const int64_t n = eo[k].n;
-        const int64_t r = eig_rank64(eo[k], eps_nw2, 1, n, s);  // eq. ht_leaf_svd, r >= 1
-        double* U = eig_vectors64(eo[k], r, s);
-        st->U[ids[k]] = U;
-        st->rank[ids[k]] = r;
-        // kept for HT-RISE: the residual of a later batch lives in span(Q) (eq. compute_residual)
-        st->Q[ids[k]] = complement_of(U, n, r, complement_seed(ids[k], 0), st->d_status, s);
-        Us.push_back(U);
-        rs.push_back(r);
+      for (int id : ids) {
+        Us.push_back(st->U[id]);
+        rs.push_back(st->rank[id]);
       }
       C = project_layer(std::move(C), ids, Us, rs, ar, s);
     }
@@ -1129,52 +1233,59 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
     for (int layer = t.p; layer >= 1; --layer) {
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
-      std::vector<EigOut> eo(ids.size());
-      std::vector<int64_t> alpha(ids.size()), rold(ids.size()), qc(ids.size());
-      std::vector<DBuf> Gs(ids.size()), sk;
-      DBuf trd(sizeof(double) * ids.size(), s), feats(sizeof(float) * 66 * ids.size(), s);
-      ck(cudaMemsetAsync(trd.p, 0, sizeof(double) * ids.size(), s), "memset");
-      for (size_t k = 0; k < ids.size(); ++k) {
+      const int nn = (int)ids.size();
+      std::vector<int64_t> alpha(nn), rold(nn), qc(nn);
+      std::vector<DBuf> Gs(nn), skw(nn), stat(nn);
+      DBuf trd(sizeof(double) * nn, s), feats(sizeof(float) * 66 * nn, s);
+      ck(cudaMemsetAsync(trd.p, 0, sizeof(double) * nn, s), "memset");
+      for (int k = 0; k < nn; ++k) {
         const int ax = C.axis_of(ids[k]);
-        const int64_t a = C.dims[ax];
-        alpha[k] = a;
+        alpha[k] = C.dims[ax];
         rold[k] = rank[ids[k]];
-        qc[k] = a - rold[k];
-        if (qc[k] <= 0) continue;  // U spans R^alpha: the residual vanishes
-        // residual R = (I - U U^T) C_(j) (eq. compute_residual). With Q the orthonormal complement of U,
-        // I - U U^T = Q Q^T, so R R^T = Q (W W^T) Q^T for W = Q^T C_(j): the nonzero eigenpairs of the
-        // residual Gram are those of the qc x qc Gram W W^T, mapped through Q.
-        LTensor W = ttm_any(C, ax, Q[ids[k]], 1, qc[k], qc[k], false, ar, s);
+        qc[k] = alpha[k] - rold[k];  // <= 0: U spans R^alpha and the residual vanishes
+        stat[k] = DBuf(sizeof(int), s);
+        ck(cudaMemsetAsync(stat[k].p, 0, sizeof(int), s), "memset status");
+        if (qc[k] <= 0) continue;
         Gs[k] = DBuf(sizeof(double) * qc[k] * qc[k], s);
-        gram_any(W, ax, Gs[k].as<double>(), ar, s);
-        // the exact residual energy ||R||^2 = trace(R R^T), read with the status word below
-        ck(launch_trace(Gs[k].as<double>(), qc[k], trd.as<double>() + k, s), "residual energy");
-        if (want_feat) {
-          sk.push_back(DBuf(sketch_workspace_bytes(qc[k], 128), s));
-          ck(launch_sketch_features(Gs[k].as<double>(), qc[k], 128, std::sqrt(eps_nw2), trd.as<double>() + k,
-                                    complement_seed(ids[k], st->n_items) ^ 0x736b65746368ull, sk.back().p,
-                                    feats.as<float>() + 66 * k, s),
-             "sketch features");
-        }
+        if (want_feat) skw[k] = DBuf(sketch_workspace_bytes(qc[k], 128), s);
       }
-      std::vector<double> tr(ids.size(), 0.0);
-      ck(cudaMemcpyAsync(tr.data(), trd.p, sizeof(double) * ids.size(), cudaMemcpyDeviceToHost, s), "D2H energies");
+      // phase 1, the nodes side by side: residual Gram matrices, their exact energies and features.
+      // Residual R = (I - U U^T) C_(j) (eq. compute_residual). With Q the orthonormal complement of U,
+      // I - U U^T = Q Q^T, so R R^T = Q (W W^T) Q^T for W = Q^T C_(j): the nonzero eigenpairs of the
+      // residual Gram are those of the qc x qc Gram W W^T, mapped through Q.
+      run_nodes(nn, s, [&](int k, cudaStream_t sk) {
+        if (qc[k] <= 0) return;
+        const int id = ids[k];
+        const int ax = C.axis_of(id);
+        Arith ark = ar;
+        ark.d_status = stat[k].as<int>();
+        LTensor W = ttm_any(C, ax, Q[id], 1, qc[k], qc[k], false, ark, sk);
+        gram_any(W, ax, Gs[k].as<double>(), ark, sk);
+        ck(launch_trace(Gs[k].as<double>(), qc[k], trd.as<double>() + k, sk), "residual energy");
+        if (want_feat)
+          ck(launch_sketch_features(Gs[k].as<double>(), qc[k], 128, std::sqrt(eps_nw2), trd.as<double>() + k,
+                                    complement_seed(id, st->n_items) ^ 0x736b65746368ull, skw[k].p,
+                                    feats.as<float>() + 66 * k, sk),
+             "sketch features");
+      });
+      std::vector<double> tr(nn, 0.0);
+      ck(cudaMemcpyAsync(tr.data(), trd.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s), "D2H energies");
       // the predictor's view of the layer: a node predicted not to expand skips its eigensolve when the
       // judge (the exact residual energy) confirms that the truncation keeps nothing
-      std::vector<char> skip_eig(ids.size(), 0), pred_expand(ids.size(), 1);
+      std::vector<char> skip_eig(nn, 0), pred_expand(nn, 1);
       if (want_feat) {
-        std::vector<float> hf(66 * ids.size());
+        std::vector<float> hf(66 * (size_t)nn);
         ck(cudaMemcpyAsync(hf.data(), feats.p, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, s), "D2H features");
-        std::vector<float> ho(2 * ids.size(), 0.f);
+        std::vector<float> ho(2 * (size_t)nn, 0.f);
         if (opts->predictor) {
           MlpActs A;
-          mlp_forward(opts->predictor, feats.as<float>(), (int64_t)ids.size(), A, s);
+          mlp_forward(opts->predictor, feats.as<float>(), nn, A, s);
           ck(cudaMemcpyAsync(ho.data(), A.out.p, sizeof(float) * ho.size(), cudaMemcpyDeviceToHost, s), "D2H preds");
           ck(cudaStreamSynchronize(s), "sync");
         } else {
           ck(cudaStreamSynchronize(s), "sync");
         }
-        for (size_t k = 0; k < ids.size(); ++k) {
+        for (int k = 0; k < nn; ++k) {
           if (qc[k] <= 0) continue;
           if (opts->node_features)
             std::memcpy(opts->node_features + 66 * (size_t)ids[k], hf.data() + 66 * k, sizeof(float) * 66);
@@ -1193,62 +1304,80 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
       } else {
         ck(cudaStreamSynchronize(s), "sync");
       }
-      for (size_t k = 0; k < ids.size(); ++k)
-        if (qc[k] > 0 && !skip_eig[k]) eig_tridiag64(Gs[k].as<double>(), qc[k], eo[k], st->d_status, s);
-      check_status(st, s);
-      std::vector<int> grown_parents;
-      for (size_t k = 0; k < ids.size(); ++k) {
+      // phase 2, the nodes side by side: eigensolve, truncation and expansion
+      std::mutex own_mu;
+      auto own_locked = [&](double* p) {
+        std::lock_guard<std::mutex> lock(own_mu);
+        fresh.push_back(p);
+        return p;
+      };
+      std::vector<int64_t> rRs(nn, 0);
+      run_nodes(nn, s, [&](int k, cudaStream_t sk) {
         const int id = ids[k];
         const int64_t a = alpha[k], r0 = rold[k], c = qc[k];
-        if (c <= 0) continue;
+        if (c <= 0) return;
+        int* status = stat[k].as<int>();
         // eq. svd_on_residual: r_R >= 0 with tail <= eps_nw^2, at most alpha - r_old new directions
-        const int64_t rR = skip_eig[k] ? 0 : eig_rank64(eo[k], eps_nw2, 0, c, s, tr[k]);
+        EigOut eo;
+        int64_t rR = 0;
+        if (!skip_eig[k]) {
+          eig_tridiag64(Gs[k].as<double>(), c, eo, status, sk);
+          check_status_word(status, sk);
+          rR = eig_rank64(eo, eps_nw2, 0, c, sk, tr[k]);
+        }
+        if (skip_eig[k]) check_status_word(status, sk);  // the phase-1 kernels' bounded waits
+        rRs[k] = rR;
         if (opts && opts->node_labels) {
           opts->node_labels[2 * (size_t)id] = rR;
           opts->node_labels[2 * (size_t)id + 1] = c;
         }
-        if (opts && opts->predictor && pred_expand[k] && rR == 0) ++pstat.missed;
-        if (rR == 0) continue;
+        if (rR == 0) return;
         DBuf Zk;
-        Zk.p = eig_vectors64(eo[k], rR, s);  // [c][rR]
-        Zk.s = s;
-        DBuf UR(sizeof(double) * a * rR, s);
-        ck(launch_gemm_f64(a, rR, c, 1.0, Q[id], c, 1, Zk.as<double>(), rR, 1, 0.0, UR.as<double>(), rR, 1, s),
+        Zk.p = eig_vectors64(eo, rR, sk);  // [c][rR]
+        Zk.s = sk;
+        DBuf UR(sizeof(double) * a * rR, sk);
+        ck(launch_gemm_f64(a, rR, c, 1.0, Q[id], c, 1, Zk.as<double>(), rR, 1, 0.0, UR.as<double>(), rR, 1, sk),
            "U_R = Q Z");
         // the complement shrinks to Q times the complement of Z inside R^c
-        double* Qn = own(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(a * (c - rR), 1), s)));
+        double* Qn = own_locked(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(a * (c - rR), 1), sk)));
         if (c > rR) {
           if (house_fits(c, rR)) {
             // rR Householder reflectors of Z applied to the rows of Q
-            DBuf hw(house_workspace_bytes(c, rR, num_sms()), s);
-            ck(launch_house_complement(Q[id], a, c, Zk.as<double>(), rR, Qn, hw.p, st->d_status, s),
+            DBuf hw(house_workspace_bytes(c, rR, num_sms()), sk);
+            ck(launch_house_complement(Q[id], a, c, Zk.as<double>(), rR, Qn, hw.p, status, sk),
                "Householder complement");
           } else {
             DBuf Yc;
-            Yc.p = complement_of(Zk.as<double>(), c, rR, complement_seed(id, st->n_items), st->d_status, s);
-            Yc.s = s;
-            ck(launch_gemm_f64(a, c - rR, c, 1.0, Q[id], c, 1, Yc.as<double>(), c - rR, 1, 0.0, Qn, c - rR, 1, s),
+            Yc.p = complement_of(Zk.as<double>(), c, rR, complement_seed(id, st->n_items), status, sk);
+            Yc.s = sk;
+            ck(launch_gemm_f64(a, c - rR, c, 1.0, Q[id], c, 1, Yc.as<double>(), c - rR, 1, 0.0, Qn, c - rR, 1, sk),
                "Q Y");
           }
         }
-        DBuf W(sizeof(double) * r0 * rR + 8, s);
+        DBuf W(sizeof(double) * r0 * rR + 8, sk);
         // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)
         for (int pass = 0; pass < 2 && r0 > 0; ++pass) {
-          ck(launch_gemm_f64(r0, rR, a, 1.0, U[id], 1, r0, UR.as<double>(), rR, 1, 0.0, W.as<double>(), rR, 1, s),
+          ck(launch_gemm_f64(r0, rR, a, 1.0, U[id], 1, r0, UR.as<double>(), rR, 1, 0.0, W.as<double>(), rR, 1, sk),
              "U^T U_R");
-          ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, s),
+          ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, sk),
              "U_R -= U W");
         }
-        orthonormalise(UR.as<double>(), a, rR, s, 3);
+        orthonormalise(UR.as<double>(), a, rR, sk, 3);
         // expandCore: U^k = [U^{k-1}, U_R] (eq. concatenating_orthonormal_vectors)
         const int64_t rn = r0 + rR;
-        double* Un = own(static_cast<double*>(dalloc(sizeof(double) * a * rn, s)));
-        if (r0 > 0) ck(launch_copy_cols(U[id], r0, a, r0, Un, rn, s), "expand old");
-        ck(launch_copy_cols(UR.as<double>(), rR, a, rR, Un + r0, rn, s), "expand new");
+        double* Un = own_locked(static_cast<double*>(dalloc(sizeof(double) * a * rn, sk)));
+        if (r0 > 0) ck(launch_copy_cols(U[id], r0, a, r0, Un, rn, sk), "expand old");
+        ck(launch_copy_cols(UR.as<double>(), rR, a, rR, Un + r0, rn, sk), "expand new");
+        check_status_word(status, sk);
         U[id] = Un;
         Q[id] = Qn;
         rank[id] = rn;
-        const int par = t.nodes[id].parent;
+      });
+      std::vector<int> grown_parents;
+      for (int k = 0; k < nn; ++k) {
+        if (qc[k] > 0 && opts && opts->predictor && pred_expand[k] && rRs[k] == 0) ++pstat.missed;
+        if (rRs[k] == 0) continue;
+        const int par = t.nodes[ids[k]].parent;
         if (par > 0 && std::find(grown_parents.begin(), grown_parents.end(), par) == grown_parents.end())
           grown_parents.push_back(par);
       }

@@ -112,6 +112,121 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const T* __restrict__ X, 
 }
 
 // ---------------------------------------------------------------------------
+// Gram of a short middle index (I <= 64) over a long column index: HBM-bound, so
+// the column chunks are read once, coalesced, by persistent CTAs. A chunk holds
+// CHC consecutive columns k = a * B + b: CHC values of b inside one a when
+// B >= CHC, CHC / B whole slabs when B < CHC, CHC consecutive a when B == 1. It
+// is staged transposed, Xs[c][i], so four consecutive i are one 16-byte
+// shared load. Thread (tile, group) accumulates the 4 x 4 block (ti, tj),
+// ti <= tj, of G over the chunk columns of its group in FP32; the FP32 partials
+// are added to FP64 registers every GRAM_FOLD chunks, summed over the groups
+// at the end and added to G with FP64 atomics (both triangles).
+// ---------------------------------------------------------------------------
+constexpr int CHC = 128;
+constexpr int GRAM_FOLD = 2;
+
+__global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict__ X, int64_t A, int I, int64_t B,
+                                                        double* __restrict__ G) {
+  const int Ip = (I + 3) & ~3, T4 = Ip / 4, ntiles = T4 * (T4 + 1) / 2;
+  const int groups = max(1, (int)blockDim.x / ntiles);
+  extern __shared__ __align__(16) float gs[];  // Xs[CHC][Ip], then the FP64 reduction area
+  float* Xs = gs;
+  const int tid = threadIdx.x;
+  const int tile = tid % ntiles, grp = tid / ntiles;
+  const bool active = grp < groups;
+  int ti = 0, tj = 0;
+  {
+    int t = tile;
+    while (t >= T4 - ti) { t -= T4 - ti; ++ti; }
+    tj = ti + t;
+  }
+  // chunk geometry
+  int64_t nb, na;
+  if (B == 1) { nb = 1; na = CHC; }
+  else if (B >= CHC) { nb = CHC; na = 1; }
+  else { nb = B; na = CHC / B; }
+  const int64_t chunks_b = (B == 1) ? 1 : (B + nb - 1) / nb;      // chunks along b in one slab group
+  const int64_t groups_a = (A + na - 1) / na;
+  const int64_t nchunks = groups_a * chunks_b;
+  double acc64[4][4];
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { acc64[u][v] = 0.0; acc[u][v] = 0.f; }
+  int since = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t ga = ch / chunks_b, gb = ch - ga * chunks_b;
+    const int64_t a0 = ga * na, b0 = gb * nb;
+    const int64_t na_here = min(na, A - a0), nb_here = min(nb, B - b0);
+    const int ncol = (int)(na_here * nb_here);
+    __syncthreads();
+    if (B == 1) {
+      const float* src = X + a0 * I;
+      for (int e = tid; e < CHC * Ip; e += blockDim.x) {
+        const int c = e / Ip, i = e - c * Ip;
+        Xs[c * Ip + i] = (c < ncol && i < I) ? src[(int64_t)c * I + i] : 0.f;
+      }
+    } else {
+      for (int e = tid; e < CHC * Ip; e += blockDim.x) {
+        const int b = (int)(e % nb), t = (int)(e / nb);
+        const int al = t % (int)na, i = t / (int)na;
+        float v = 0.f;
+        if (i < I && al < na_here && b < nb_here) v = X[((a0 + al) * I + i) * B + b0 + b];
+        if (i < Ip) Xs[(al * (int)nb + b) * Ip + i] = v;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      for (int c = grp; c < ncol; c += groups) {
+        const float4 x = *reinterpret_cast<const float4*>(Xs + c * Ip + 4 * ti);
+        const float4 y = *reinterpret_cast<const float4*>(Xs + c * Ip + 4 * tj);
+        const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xa[u], ya[v], acc[u][v]);
+      }
+      if (++since == GRAM_FOLD) {
+        since = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) { acc64[u][v] += (double)acc[u][v]; acc[u][v] = 0.f; }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc64[u][v] += (double)acc[u][v];
+  // sum over the groups in shared memory (FP64), then one atomic per entry per CTA
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(gs);  // [ntiles][16]
+  for (int e = tid; e < ntiles * 16; e += blockDim.x) red[e] = 0.0;
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) atomicAdd(&red[tile * 16 + u * 4 + v], acc64[u][v]);
+  }
+  __syncthreads();
+  for (int e = tid; e < ntiles * 16; e += blockDim.x) {
+    const int tl = e / 16, u = (e / 4) % 4, v = e % 4;
+    int a_ = 0, t = tl;
+    while (t >= T4 - a_) { t -= T4 - a_; ++a_; }
+    const int b_ = a_ + t;
+    const int i = 4 * a_ + u, j = 4 * b_ + v;
+    if (i >= I || j >= I) continue;
+    const double val = red[e];
+    if (val == 0.0) continue;
+    atomicAdd(&G[(int64_t)i * I + j], val);
+    if (a_ != b_) atomicAdd(&G[(int64_t)j * I + i], val);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // TTM: out[a][s][b] = sum_t M(s,t) X[a][t][b]
 // grid.x: tiles of the flattened column c = a * B + b, grid.y: tiles of s.
 // ---------------------------------------------------------------------------
@@ -479,6 +594,24 @@ cudaError_t launch_gram_f64(const T* X, double* G, int64_t A, int64_t I, int64_t
 }
 
 cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int64_t B, cudaStream_t s) {
+  if (I <= 64 && A * B >= 4 * CHC) {
+    // short index: the streaming kernel (the caller zeroed G)
+    const int Ip = (int)((I + 3) & ~3);
+    const int T4 = Ip / 4, ntiles = T4 * (T4 + 1) / 2;
+    const size_t sm = std::max(sizeof(float) * CHC * Ip, sizeof(double) * 16 * (size_t)ntiles);
+    int64_t nb = (B == 1) ? 1 : (B >= CHC ? CHC : B), na = (B == 1) ? CHC : (B >= CHC ? 1 : CHC / B);
+    const int64_t nchunks = ((A + na - 1) / na) * ((B == 1) ? 1 : (B + nb - 1) / nb);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>(nchunks, 4 * (int64_t)nsm);
+    const int64_t K = A * B;
+    ProfScope prof(K_GRAM_F32, s, (double)I * (double)(I + 1) * (double)K,
+                   4.0 * (double)K * (double)I + 8.0 * (double)I * (double)I);
+    gram_small_kernel<<<grid, 256, sm, s>>>(X, A, (int)I, B, G);
+    note_launch();
+    return cudaGetLastError();
+  }
   return launch_gram<float, float>(X, G, A, I, B, s);
 }
 
