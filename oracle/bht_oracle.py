@@ -179,6 +179,7 @@ class BHTState:
     cores: dict = field(default_factory=dict)   # leaf id -> U [n, r]; transfer id -> G [r_l, r_r, r]
     root: np.ndarray = None                     # G_0 [r_11, r_12, N_total] (batch last)
     n_items: int = 0
+    budget: str = "uniform"                     # "uniform" (Algorithms 1, 2) or "adaptive" (App. C)
 
     def rank(self, nid: int) -> int:
         return self.cores[nid].shape[-1]
@@ -260,21 +261,39 @@ def _to_paper_layout(Y: np.ndarray, tree: Tree) -> np.ndarray:
 # Algorithm 1: BHT-l2r
 # ---------------------------------------------------------------------------
 
-def bht_l2r(Y: np.ndarray, eps_rel: float, tree: Tree = None) -> BHTState:
+def _svds_above(tree: Tree, layer: int) -> int:
+    """Number of truncations (non-root nodes) on the layers above `layer` (ell - 1 .. 1)."""
+    return sum(len(tree.layers[l]) for l in range(1, layer))
+
+
+def _adaptive_eps_nw(eps_abs2: float, norm2: float, C: np.ndarray, svd_rem: int) -> float:
+    """App. C: the error spent so far eps_l^2 = ||Y||^2 - ||C_l||^2, the remaining budget
+    eps_rem = sqrt(eps_abs^2 - eps_l^2), spread over the svd_rem truncations still to come."""
+    eps_l2 = max(norm2 - float(np.sum(C * C)), 0.0)
+    eps_rem2 = max(eps_abs2 - eps_l2, 0.0)
+    return math.sqrt(eps_rem2 / svd_rem)
+
+
+def bht_l2r(Y: np.ndarray, eps_rel: float, tree: Tree = None, budget: str = "uniform") -> BHTState:
     """Error-truncated leaves-to-root batch HT decomposition (Algorithm 1).
 
-    Y: item-major batch [N, n_1, ..., n_d].
+    Y: item-major batch [N, n_1, ..., n_d]. budget "uniform": eps_nw = eps_abs / sqrt(2d - 2) at every
+    node (Algorithm 1); "adaptive": after each layer the error actually spent is measured and the
+    remaining budget is spread over the remaining truncations (App. C).
     """
     if tree is None:
         tree = Tree(Y.shape[1:])
     C = _to_paper_layout(Y, tree)
     d, p = tree.d, tree.p
-    state = BHTState(tree=tree, eps_rel=float(eps_rel))
-    eps_nw = eps_rel * np.linalg.norm(C) / math.sqrt(2 * d - 2)   # node-wise tolerance (R2)
+    state = BHTState(tree=tree, eps_rel=float(eps_rel), budget=budget)
+    norm2 = float(np.sum(C * C))
+    eps_nw = eps_rel * math.sqrt(norm2) / math.sqrt(2 * d - 2)   # node-wise tolerance (R2)
     axes = _initial_axes(tree)
     for layer in range(p, 0, -1):
         if layer < p:
             C, axes = _reshape_to_layer(tree, C, axes, layer)
+            if budget == "adaptive":
+                eps_nw = _adaptive_eps_nw(eps_rel * eps_rel * norm2, norm2, C, _svds_above(tree, layer + 1))
         # HOSVD of the layer: every node truncated from the same intermediate (R10)
         bases = {}
         for nd in tree.layer_nodes(layer):
@@ -326,10 +345,13 @@ def _pad_axis(A: np.ndarray, axis: int, extra: int) -> np.ndarray:
     return np.concatenate([A, np.zeros(shape, dtype=A.dtype)], axis=axis)
 
 
-def htrise_update(state: BHTState, Y: np.ndarray, eps_rel: float = None) -> UpdateInfo:
-    """Incremental update of the batch-HT state with a new batch (Algorithm 2). Mutates `state`."""
+def htrise_update(state: BHTState, Y: np.ndarray, eps_rel: float = None, budget: str = None) -> UpdateInfo:
+    """Incremental update of the batch-HT state with a new batch (Algorithm 2). Mutates `state`.
+    budget: as for bht_l2r (default: the state's)."""
     if eps_rel is None:
         eps_rel = state.eps_rel
+    if budget is None:
+        budget = state.budget
     tree = state.tree
     d, p = tree.d, tree.p
     Yp = _to_paper_layout(Y, tree)
@@ -351,6 +373,8 @@ def htrise_update(state: BHTState, Y: np.ndarray, eps_rel: float = None) -> Upda
     for layer in range(p, 0, -1):
         if layer < p:
             C, axes = _reshape_to_layer(tree, C, axes, layer)      # index set I^k of this layer
+            if budget == "adaptive":
+                eps_nw = _adaptive_eps_nw(eps_des * eps_des, normY ** 2, C, _svds_above(tree, layer + 1))
         # Steps 2-3 for every node of the layer, all from the same C
         new_bases = {}
         for nd in tree.layer_nodes(layer):

@@ -14,6 +14,7 @@ import scipy.linalg
 
 import bht_synth as S
 import oracle as O
+import oracle.bht_oracle as OB
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -377,3 +378,64 @@ def test_compression_ratio_from_ranks():
     c1, c2 = t.nodes[0].children
     elems += st.rank(c1) * st.rank(c2) * 12
     assert O.compression_ratio(st) == 12 * 16 ** 3 / elems
+
+
+# ---------------------------------------------------------------------------
+# App. C: adaptive error budget
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,N,eps", [((6, 7, 5), 4, 0.05), ((4, 5, 3, 6), 5, 0.1), ((3, 4, 5, 3, 4), 6, 0.08),
+                                        ((8, 8, 8, 8), 3, 0.03)])
+def test_adaptive_budget_keeps_the_bound(dims, N, eps):
+    rng = np.random.default_rng(sum(dims) + N)
+    Y = rng.normal(size=(N,) + dims)
+    Y = Y + 0.5 * np.cumsum(Y, axis=1)
+    st = O.bht_l2r(Y, eps, budget="adaptive")
+    assert np.linalg.norm(Y - O.reconstruct(st)) <= eps * np.linalg.norm(Y) * (1 + 1e-12)
+    for k in range(2):
+        Yk = rng.normal(size=(N,) + dims)
+        O.htrise_update(st, Yk, eps)
+        assert np.linalg.norm(Yk - O.reconstruct(st, st.n_items - N, N)) <= eps * np.linalg.norm(Yk) * (1 + 1e-12)
+
+
+def test_adaptive_budget_equals_uniform_with_one_layer():
+    # d = 2: every truncation is on the first layer, nothing is left to re-budget
+    rng = np.random.default_rng(21)
+    Y = rng.normal(size=(3, 9, 11))
+    a, u = O.bht_l2r(Y, 0.1, budget="adaptive"), O.bht_l2r(Y, 0.1)
+    assert a.ranks() == u.ranks()
+    np.testing.assert_allclose(O.reconstruct(a), O.reconstruct(u), atol=1e-12)
+
+
+def test_adaptive_budget_truncates_the_upper_layer_at_least_as_hard():
+    # d = 3: layer 2 is identical; layer 1 sees the same intermediate and a tolerance that is the
+    # unspent budget spread over its two truncations, never below eps_abs / sqrt(2d - 2)
+    rng = np.random.default_rng(22)
+    for trial in range(5):
+        Y = rng.normal(size=(4, 6, 7, 8)) + np.cumsum(rng.normal(size=(4, 6, 7, 8)), axis=2)
+        a, u = O.bht_l2r(Y, 0.2, budget="adaptive"), O.bht_l2r(Y, 0.2)
+        ra, ru = a.ranks(), u.ranks()
+        t = a.tree
+        for nid in t.layers[2]:
+            assert ra[nid] == ru[nid]
+        for nid in t.layers[1]:
+            assert ra[nid] <= ru[nid]
+
+
+def test_adaptive_budget_tolerance_formula():
+    # after layer p: eps_rem^2 = eps_abs^2 - (||Y||^2 - ||C_p||^2), eps_nw = eps_rem / sqrt(svd_rem)
+    rng = np.random.default_rng(23)
+    C = rng.normal(size=(5, 6))
+    norm2 = float(np.sum(C * C)) + 2.0                      # 2.0 of energy already removed
+    got = OB._adaptive_eps_nw(9.0, norm2, C, 4)
+    assert abs(got - np.sqrt((9.0 - 2.0) / 4)) < 1e-12
+    assert OB._adaptive_eps_nw(1.0, norm2, C, 4) == 0.0      # budget already spent: nothing more may be cut
+
+
+def test_remaining_truncation_counts_of_a_five_mode_tree():
+    # Fig. 2 style tree of 5 modes: layer 1 {1,2,3},{4,5}; layer 2 {1,2},{3},{4},{5}; layer 3 {1},{2}
+    t = O.dimension_tree((3, 4, 5, 6, 7))
+    assert [len(l) for l in t.layers] == [1, 2, 4, 2]
+    assert OB._svds_above(t, 4) == 8       # before layer 3: all 2d - 2 truncations remain
+    assert OB._svds_above(t, 3) == 6       # after layer 3: layers 2 and 1
+    assert OB._svds_above(t, 2) == 2       # after layer 2: layer 1
