@@ -77,6 +77,13 @@ typedef enum { BHT_F32 = 0, BHT_F64 = 1 } bht_dtype;
  *                   norms and the skip test stay in FP64. */
 typedef enum { BHT_PREC_FP64 = 0, BHT_PREC_MIXED = 1 } bht_precision;
 
+/* Node-wise error budget.
+ *   BHT_BUDGET_UNIFORM : eps_nw = eps_abs / sqrt(2d - 2) at every truncation (Algorithms 1, 2).
+ *   BHT_BUDGET_ADAPTIVE: after each layer the error actually spent, eps_l^2 = ||Y||^2 - ||C_l||^2, is
+ *                        measured and eps_nw = sqrt(eps_abs^2 - eps_l^2) / sqrt(truncations left)
+ *                        (App. C). The bound ||Y - Y~|| <= eps_abs holds for both. */
+typedef enum { BHT_BUDGET_UNIFORM = 0, BHT_BUDGET_ADAPTIVE = 1 } bht_budget;
+
 typedef struct bht_tree bht_tree;
 typedef struct bht_state bht_state;
 /* Rank / expansion predictor (no counterpart in the paper): a three-layer perceptron with bf16
@@ -86,7 +93,8 @@ typedef struct bht_mlp bht_mlp;
 /* Options of bht_l2r / htrise_update; NULL means all defaults (FP64, no predictor). */
 typedef struct {
   int32_t precision;      /* bht_precision */
-  int32_t reserved0;
+  int32_t budget;         /* bht_budget, or -1: bht_l2r uniform, htrise_update the state's (the budget
+                             given to bht_l2r) */
   /* htrise_update only. With a predictor, every node whose residual Gram matrix is formed gets its
    * 66 sketch features and a prediction; a node predicted not to expand skips its residual
    * eigensolve when the exact residual energy trace(R R^T) <= eps_nw^2 confirms that the truncation

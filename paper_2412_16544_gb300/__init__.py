@@ -34,7 +34,7 @@ class BHTError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("predictor", ctypes.c_void_p),
+    _fields_ = [("precision", ctypes.c_int32), ("budget", ctypes.c_int32), ("predictor", ctypes.c_void_p),
                 ("node_features", ctypes.c_void_p), ("node_labels", ctypes.c_void_p)]
 
 
@@ -161,11 +161,12 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def _opts(precision, predictor=None, node_features=None, node_labels=None):
-    if precision is None and predictor is None and node_features is None and node_labels is None:
+def _opts(precision, predictor=None, node_features=None, node_labels=None, budget=None):
+    if precision is None and predictor is None and node_features is None and node_labels is None and budget is None:
         return None
     code = {"fp64": BHT_PREC_FP64, "mixed": BHT_PREC_MIXED, None: BHT_PREC_FP64}.get(precision, precision)
-    o = _Opts(int(code), 0, predictor.value if predictor is not None else None,
+    bcode = {"uniform": 0, "adaptive": 1, None: -1}.get(budget, budget)  # -1: the state's own
+    o = _Opts(int(code), int(bcode), predictor.value if predictor is not None else None,
               node_features.ctypes.data if node_features is not None else None,
               node_labels.ctypes.data if node_labels is not None else None)
     return ctypes.byref(o)
@@ -205,17 +206,18 @@ def bht_tree_info(tree):
     return depth.value, nodes.value
 
 
-def bht_l2r(tree, Y, eps_rel: float, precision=None, stream=None) -> ctypes.c_void_p:
+def bht_l2r(tree, Y, eps_rel: float, precision=None, stream=None, budget=None) -> ctypes.c_void_p:
+    """budget: "uniform" (default) or "adaptive" (App. C); also the default of later htrise_update calls."""
     ptr, code, shape, keep = _buffer(Y)
     h = ctypes.c_void_p()
-    _check(_lib.bht_l2r(tree, ptr, code, int(shape[0]), float(eps_rel), _opts(precision), _stream(stream),
-                        ctypes.byref(h)), "bht_l2r")
+    _check(_lib.bht_l2r(tree, ptr, code, int(shape[0]), float(eps_rel), _opts(precision, budget=budget),
+                        _stream(stream), ctypes.byref(h)), "bht_l2r")
     del keep
     return h
 
 
 def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predictor=None, node_features=None,
-                  node_labels=None) -> UpdateInfo:
+                  node_labels=None, budget=None) -> UpdateInfo:
     """node_features (float32 [nodes][66]) and node_labels (int64 [nodes][2]): host numpy arrays the call
     fills for the nodes whose residual it forms (the predictor's training pairs)."""
     ptr, code, shape, keep = _buffer(Y)
@@ -224,7 +226,7 @@ def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predict
         if a is not None and (a.dtype != dt or not a.flags.c_contiguous):
             raise ValueError("node_features must be float32 and node_labels int64, C-contiguous")
     _check(_lib.htrise_update(state, ptr, code, int(shape[0]), float(eps_rel),
-                              _opts(precision, predictor, node_features, node_labels), _stream(stream),
+                              _opts(precision, predictor, node_features, node_labels, budget), _stream(stream),
                               ctypes.byref(info)), "htrise_update")
     del keep
     return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total,

@@ -300,6 +300,7 @@ size_t dtype_size(int dt) { return dt == BHT_F64 ? 8 : 4; }
 struct bht_state {
   bht_tree tree;
   int precision = BHT_PREC_FP64;
+  int budget = BHT_BUDGET_UNIFORM;  // default node-wise budget of htrise_update
   std::vector<int64_t> rank;    // per node id; rank[0] unused
   std::vector<double*> U;       // per node id: orthonormal matrix form [rows][rank], FP64, device
   std::vector<double*> Q;       // per node id: orthonormal complement of U in R^rows, [rows][rows - rank]
@@ -959,6 +960,37 @@ void mlp_forward(const bht_mlp* net, const float* X, int64_t B, MlpActs& A, cuda
      "mlp layer 3");
 }
 
+// Truncations (non-root nodes) on the layers 1 .. layer.
+int svds_through(const bht_tree& t, int layer) {
+  int n = 0;
+  for (int l = 1; l <= layer; ++l) n += (int)t.layers[l].size();
+  return n;
+}
+
+// Projection of a layer's nodes that also adds the energy it removes (on each node's complement) to
+// *removed (device double); see ttm_proj_resid.
+LTensor project_layer_removed(LTensor C, const std::vector<int>& ids, const std::vector<double*>& U,
+                              const std::vector<double*>& Q, const std::vector<int64_t>& rank, const bht_tree& t,
+                              const std::vector<int64_t>& rows, const Arith& ar, cudaStream_t s, double* removed) {
+  std::vector<std::pair<int, int64_t>> ops;
+  for (int id : ids) ops.push_back({C.axis_of(id), rank[id]});
+  for (int k : best_order(C.dims, ops)) {
+    const int id = ids[k];
+    LTensor nxt = ttm_proj_resid(C, C.axis_of(id), U[id], rank[id], Q[id], rows[id] - rank[id], false, ar, s, nullptr,
+                                 nullptr, removed);
+    C = std::move(nxt);
+  }
+  (void)t;
+  return C;
+}
+
+// App. C: the error spent after a layer, eps_l^2, from the FP64 norms (FP64 form) or the energy the
+// projections removed (mixed form); the tolerance of the next layer is the rest of the budget spread
+// over the truncations still to come.
+double adaptive_eps_nw2(double eps_abs2, double spent2, int svd_rem) {
+  return std::max(eps_abs2 - std::max(spent2, 0.0), 0.0) / std::max(svd_rem, 1);
+}
+
 Arith make_arith(int precision, double eps_rel, int* d_status) {
   Arith ar;
   ar.mixed = precision == BHT_PREC_MIXED;
@@ -982,6 +1014,8 @@ void copy_convert(const LTensor& C, void* out, int out_dtype, cudaStream_t s) {
 void validate_opts(const bht_opts* o) {
   if (o && o->precision != BHT_PREC_FP64 && o->precision != BHT_PREC_MIXED)
     fail(BHT_EINVAL, "opts.precision must be BHT_PREC_FP64 or BHT_PREC_MIXED");
+  if (o && (o->budget < -1 || o->budget > BHT_BUDGET_ADAPTIVE))
+    fail(BHT_EINVAL, "opts.budget must be BHT_BUDGET_UNIFORM, BHT_BUDGET_ADAPTIVE or -1");
 }
 
 // Root buffer with room for `cap` items of r11 x r12, old items zero-padded (eq. incremental_zero_padding1).
@@ -1109,6 +1143,7 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
   bht_state* st = new bht_state();
   st->tree = t;
   st->precision = opts ? opts->precision : BHT_PREC_FP64;
+  st->budget = (opts && opts->budget == BHT_BUDGET_ADAPTIVE) ? BHT_BUDGET_ADAPTIVE : BHT_BUDGET_UNIFORM;
   st->rank.assign(t.nodes.size(), 0);
   st->U.assign(t.nodes.size(), nullptr);
   st->Q.assign(t.nodes.size(), nullptr);
@@ -1122,8 +1157,11 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
     ck(cudaStreamSynchronize(s), "sync");
     if (!std::isfinite(normY2)) fail(BHT_ENUMERIC, "the batch holds non-finite values");
     // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1)
-    const double eps_nw2 = eps_rel * eps_rel * normY2 / (2.0 * t.d - 2.0);
+    double eps_nw2 = eps_rel * eps_rel * normY2 / (2.0 * t.d - 2.0);
     const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
+    const bool adaptive = st->budget == BHT_BUDGET_ADAPTIVE;
+    DBuf removed(sizeof(double), s);
+    ck(cudaMemsetAsync(removed.p, 0, sizeof(double), s), "memset");
 
     LTensor C = input_tensor(t, dY, dtype, N);
     for (int layer = t.p; layer >= 1; --layer) {
@@ -1158,7 +1196,29 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
         Us.push_back(st->U[id]);
         rs.push_back(st->rank[id]);
       }
-      C = project_layer(std::move(C), ids, Us, rs, ar, s);
+      if (adaptive && layer > 1 && ar.mixed) {
+        std::vector<int64_t> rows(t.nodes.size(), 0);
+        for (int id : ids) rows[id] = st->rows(id);
+        C = project_layer_removed(std::move(C), ids, st->U, st->Q, st->rank, t, rows, ar, s, removed.as<double>());
+      } else {
+        C = project_layer(std::move(C), ids, Us, rs, ar, s);
+      }
+      if (adaptive && layer > 1) {
+        // App. C: the rest of the budget over the truncations still to come
+        double spent2 = 0.0;
+        if (ar.mixed) {
+          ck(cudaMemcpyAsync(&spent2, removed.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H removed");
+          ck(cudaStreamSynchronize(s), "sync");
+        } else {
+          DBuf c2(sizeof(double), s);
+          sqnorm_of(C.ptr, C.dtype, C.numel(), c2.as<double>(), s);
+          double h = 0.0;
+          ck(cudaMemcpyAsync(&h, c2.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norm");
+          ck(cudaStreamSynchronize(s), "sync");
+          spent2 = normY2 - h;
+        }
+        eps_nw2 = adaptive_eps_nw2(eps_rel * eps_rel * normY2, spent2, svds_through(t, layer - 1));
+      }
     }
     // G_0 = reshape(C, [r11, r12, N]) stored item-major
     grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), N, s);
@@ -1219,7 +1279,10 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   Cbar = LTensor();
 
   // Steps 2-3 layer by layer; the new cores live in a shadow copy until commit
-  const double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
+  double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
+  const int budget = (opts && opts->budget >= 0) ? opts->budget : st->budget;
+  DBuf removed(sizeof(double), s);
+  ck(cudaMemsetAsync(removed.p, 0, sizeof(double), s), "memset");
   const bool want_feat = opts && (opts->predictor || opts->node_features);
   struct {
     int32_t nodes = 0, skipped = 0, fallback = 0, missed = 0;
@@ -1409,7 +1472,30 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         Us.push_back(U[id]);
         rs.push_back(rank[id]);
       }
-      C = project_layer(std::move(C), ids, Us, rs, ar, s);
+      const bool adaptive = budget == BHT_BUDGET_ADAPTIVE && layer > 1;
+      if (adaptive && ar.mixed) {
+        std::vector<int64_t> rows(t.nodes.size(), 0);
+        for (int k = 0; k < nn; ++k) rows[ids[k]] = alpha[k];
+        C = project_layer_removed(std::move(C), ids, U, Q, rank, t, rows, ar, s, removed.as<double>());
+      } else {
+        C = project_layer(std::move(C), ids, Us, rs, ar, s);
+      }
+      if (adaptive) {
+        // App. C on the update: the error spent by the projection onto the updated cores so far
+        double spent2 = 0.0;
+        if (ar.mixed) {
+          ck(cudaMemcpyAsync(&spent2, removed.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H removed");
+          ck(cudaStreamSynchronize(s), "sync");
+        } else {
+          DBuf c2(sizeof(double), s);
+          sqnorm_of(C.ptr, C.dtype, C.numel(), c2.as<double>(), s);
+          double hc = 0.0;
+          ck(cudaMemcpyAsync(&hc, c2.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norm");
+          ck(cudaStreamSynchronize(s), "sync");
+          spent2 = h[0] - hc;
+        }
+        eps_nw2 = adaptive_eps_nw2(eps_des * eps_des, spent2, svds_through(t, layer - 1));
+      }
     }
     // eq. incremental_root_concatenate with the root zero-padded in modes 1, 2
     const int64_t r11 = rank[t.nodes[0].child[0]], r12 = rank[t.nodes[0].child[1]];

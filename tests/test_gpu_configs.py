@@ -76,12 +76,12 @@ def to_dev(Y):
     return torch.from_numpy(np.ascontiguousarray(Y)).cuda()
 
 
-def check_stream(B, monkeypatch, batches, eps, precision, sample_items):
+def check_stream(B, monkeypatch, batches, eps, precision, sample_items, budget="uniform"):
     """BHT-l2r on the first batch, HT-RISE on the rest, GPU and oracle side by side."""
     rec = Recorder(monkeypatch)
     tree = B.bht_tree_create_balanced(batches[0].shape[1:])
-    st = B.bht_l2r(tree, to_dev(batches[0]), eps, precision=precision)
-    ost = O.bht_l2r(batches[0].astype(np.float64), eps)
+    st = B.bht_l2r(tree, to_dev(batches[0]), eps, precision=precision, budget=budget)
+    ost = O.bht_l2r(batches[0].astype(np.float64), eps, budget=budget)
     for Yk in batches[1:]:
         gi = B.htrise_update(st, to_dev(Yk), eps, precision=precision)
         oi = O.htrise_update(ost, Yk.astype(np.float64), eps)
@@ -182,3 +182,24 @@ def test_chebyshev_sensor_full_increments_properties(B):
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
     B.bht_state_destroy(st)
     B.bht_tree_destroy(tree)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["spectral", "multivar", "random5"])
+def test_adaptive_error_budget(B, monkeypatch, precision, case):
+    """App. C: the unspent budget moves up the tree; GPU and oracle take the same truncations."""
+    if case == "spectral":
+        Y = S.spectral_field(3, 0, 48, n=32)
+        batches = [Y[:16], Y[16:32], Y[32:]]
+        eps = 2e-2
+    elif case == "multivar":
+        Y = S.multivar_field(1, 0, 20, n=16)
+        batches = [Y[:8], Y[8:13], Y[13:]]
+        eps = 1e-2
+    else:
+        rng = np.random.default_rng(5)
+        Y = rng.normal(size=(18, 4, 5, 6, 3, 4))
+        Y = (Y + 0.7 * np.cumsum(Y, axis=2)).astype(np.float32)
+        batches = [Y[:6], Y[6:12], Y[12:]]
+        eps = 0.1
+    check_stream(B, monkeypatch, batches, eps, precision, sample_items=(0, len(Y) - 1), budget="adaptive")
