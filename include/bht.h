@@ -158,9 +158,17 @@ bht_status htrise_update(bht_state* state, const void* Y, int32_t dtype, int64_t
 bht_status ht_reconstruct(const bht_state* state, int64_t first, int64_t count,
                           void* out, int32_t dtype, void* stream);
 
+/* Root-to-leaves expansion of N latent items (FP64 [N][r_11][r_12], host or device, e.g. from
+ * ht_encode) into `out` ([N][n_1]..[n_d], element type `dtype`, host or device). With ht_encode this
+ * gives the relative test error ||X - decode(encode(X))|| / ||X|| of unseen items. N = 0 does
+ * nothing; N < 0 is BHT_EINVAL. Never modifies the state. Synchronises `stream`. */
+bht_status ht_decode(const bht_state* state, const double* latent, int64_t N, void* out, int32_t dtype,
+                     void* stream);
+
 /* Latent representation of N unseen items on the current cores (Step 1 of
  * Algorithm 2), written item-major [N][r_11][r_12] as FP64 into `out`
- * (device or host). Never modifies the state. */
+ * (device or host). N = 0 does nothing; N < 0 is BHT_EINVAL. Never modifies the
+ * state. Synchronises `stream`. */
 bht_status ht_encode(const bht_state* state, const void* Y, int32_t dtype, int64_t N,
                      double* out, void* stream);
 

@@ -413,12 +413,11 @@ def htrise_update(state: BHTState, Y: np.ndarray, eps_rel: float = None, budget:
 # Reconstruction root-to-leaves (eq. htucker_reconstruction, R11)
 # ---------------------------------------------------------------------------
 
-def reconstruct(state: BHTState, first: int = 0, count: int = None) -> np.ndarray:
-    """Decode items first..first+count-1 of the accumulation, item-major [count, n_1..n_d]."""
+def decode(state: BHTState, Z: np.ndarray) -> np.ndarray:
+    """Root-to-leaves expansion (eq. htucker_reconstruction) of latent items Z, item-major
+    [N, r_11, r_12], into [N, n_1..n_d]: every node's core contracted in, layer by layer."""
     tree = state.tree
-    if count is None:
-        count = state.n_items - first
-    C = state.root[:, :, first:first + count]
+    C = np.moveaxis(np.asarray(Z, dtype=np.float64), 0, -1)      # [r_11, r_12, N]
     tags = list(tree.nodes[0].children)          # axis -> node id still to expand
     for layer in range(1, tree.p + 1):
         for nd in tree.layer_nodes(layer):
@@ -433,6 +432,20 @@ def reconstruct(state: BHTState, first: int = 0, count: int = None) -> np.ndarra
                 tags[ax:ax + 1] = list(nd.children)
     assert tags == [("mode", m) for m in range(tree.d)]
     return np.moveaxis(C, -1, 0)
+
+
+def reconstruct(state: BHTState, first: int = 0, count: int = None) -> np.ndarray:
+    """Decode items first..first+count-1 of the accumulation, item-major [count, n_1..n_d]."""
+    if count is None:
+        count = state.n_items - first
+    return decode(state, np.moveaxis(state.root[:, :, first:first + count], -1, 0))
+
+
+def relative_test_error(state: BHTState, X: np.ndarray) -> float:
+    """||X - decode(project(X))|| / ||X|| for items X that need not be in the accumulation: the
+    error with which the current cores represent unseen data."""
+    X = np.asarray(X, dtype=np.float64)
+    return float(np.linalg.norm(X - decode(state, project(state, X))) / np.linalg.norm(X))
 
 
 def compression_ratio(state: BHTState, n_items_elements: int = None) -> float:

@@ -72,6 +72,7 @@ def _load():
         "bht_sym_eig": [vp, i64, vp, vp, i64, vp],
         "bht_mode_product_noalloc": [vp, i64, i64, vp, i64, vp, i64, vp, vp],
         "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
+        "ht_decode": [vp, vp, i64, vp, i32, vp],
         "bht_mlp_create": [i32, i32, vp, P(vp)],
         "bht_mlp_destroy": [vp],
         "bht_mlp_num_params": [vp, P(i64)],
@@ -100,7 +101,7 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
             "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
-            "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features"]
+            "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode"]
 KERNEL_CLASSES = 16
 
 
@@ -263,6 +264,9 @@ def ht_reconstruct(state, first: int, count: int, out=None, dtype="float32", str
 def ht_encode(state, Y, out=None, stream=None):
     ranks = bht_get_ranks(state)
     ptr, code, shape, keep = _buffer(Y)
+    dims = bht_get_dims(state)
+    if tuple(shape[1:]) != tuple(dims):
+        raise ValueError(f"items must be [N, {', '.join(map(str, dims))}], got {tuple(shape)}")
     if out is None:
         out = np.empty((shape[0], ranks[1], ranks[2]), dtype=np.float64)
     optr, ocode, _, okeep = _buffer(out)
@@ -270,6 +274,37 @@ def ht_encode(state, Y, out=None, stream=None):
         raise TypeError("ht_encode writes float64")
     _check(_lib.ht_encode(state, ptr, code, int(shape[0]), optr, _stream(stream)), "ht_encode")
     return out
+
+
+def ht_decode(state, Z, out=None, dtype="float32", stream=None):
+    """Decode latent items Z ([N][r11][r12] float64, host or device) into `out` (device when None)."""
+    ptr, code, shape, keep = _buffer(Z)
+    if code != BHT_F64:
+        raise TypeError("latent items are float64")
+    ranks = bht_get_ranks(state)
+    if len(shape) != 3 or tuple(shape[1:]) != (ranks[1], ranks[2]):
+        raise ValueError(f"latent items must be [N, {ranks[1]}, {ranks[2]}], got {tuple(shape)}")
+    dims = bht_get_dims(state)
+    if out is None:
+        torch = _torch()
+        tdt = torch.float32 if dtype in ("float32", BHT_F32) else torch.float64
+        out = torch.empty((shape[0], *dims), dtype=tdt, device="cuda")
+    optr, ocode, oshape, okeep = _buffer(out)
+    if tuple(oshape) != (shape[0], *dims):
+        raise ValueError(f"out must be [{shape[0]}, {', '.join(map(str, dims))}], got {tuple(oshape)}")
+    _check(_lib.ht_decode(state, ptr, int(shape[0]), optr, ocode, _stream(stream)), "ht_decode")
+    del keep, okeep
+    return out
+
+
+def relative_test_error(state, X, stream=None) -> float:
+    """||X - decode(encode(X))|| / ||X|| for unseen items X (the relative test error), on the GPU."""
+    torch = _torch()
+    Z = ht_encode(state, X, stream=stream)
+    Xh = ht_decode(state, Z, dtype="float64", stream=stream)
+    Xd = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Xd = Xd.to(torch.float64)
+    return float(torch.linalg.vector_norm(Xh - Xd) / torch.linalg.vector_norm(Xd))
 
 
 def bht_get_core(state, node: int) -> np.ndarray:

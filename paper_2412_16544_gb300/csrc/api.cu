@@ -1037,6 +1037,63 @@ void grow_root(bht_state* st, int64_t r11_old, int64_t r12_old, int64_t r11, int
 
 }  // namespace
 
+namespace {
+// Root-to-leaves expansion (eq. htucker_reconstruction) of N latent items Z (device, FP64,
+// [N][r11][r12]) into out ([N][n_1]..[n_d], element type dtype, host or device).
+void decode_latent(const bht_state* st, const double* Z, int64_t count, void* out, int32_t dtype, cudaStream_t s) {
+  const bht_tree& t = st->tree;
+  const Arith ar = make_arith(st->precision, 1.0, st->d_status);
+  LTensor C;
+  C.dtype = BHT_F64;
+  C.N = count;
+  C.dims = {st->r11(), st->r12()};
+  C.node = {t.nodes[0].child[0], t.nodes[0].child[1]};
+  C.ptr = Z;
+  for (int layer = 1; layer <= t.p; ++layer) {
+    // expand every node of this layer: axis r -> rows
+    std::vector<std::pair<int, int64_t>> ops;
+    std::vector<int> ids;
+    for (int id : t.layers[layer]) {
+      ids.push_back(id);
+      ops.push_back({C.axis_of(id), st->rows(id)});
+    }
+    for (int k : best_order(C.dims, ops)) {
+      const int id = ids[k];
+      const int ax = C.axis_of(id);
+      const int64_t r = st->rank[id], a = st->rows(id);
+      LTensor nxt = ttm_any(C, ax, st->U[id], r, 1, a, false, ar, s);
+      C = std::move(nxt);
+    }
+    // split transfer axes into their successors' axes (C-order)
+    std::vector<int64_t> dims;
+    std::vector<int> node;
+    for (size_t i = 0; i < C.node.size(); ++i) {
+      const TNode& nd = t.nodes[C.node[i]];
+      if (nd.layer == layer && !nd.leaf()) {
+        dims.push_back(st->rank[nd.child[0]]);
+        dims.push_back(st->rank[nd.child[1]]);
+        node.push_back(nd.child[0]);
+        node.push_back(nd.child[1]);
+      } else {
+        dims.push_back(C.dims[i]);
+        node.push_back(C.node[i]);
+      }
+    }
+    C.dims = dims;
+    C.node = node;
+  }
+  const int64_t n = C.numel();
+  if (is_device_ptr(out)) {
+    copy_convert(C, out, dtype, s);
+  } else {
+    DBuf tmp(dtype_size(dtype) * n, s);
+    copy_convert(C, tmp.p, dtype, s);
+    ck(cudaMemcpyAsync(out, tmp.p, dtype_size(dtype) * n, cudaMemcpyDeviceToHost, s), "D2H");
+  }
+  ck(cudaStreamSynchronize(s), "sync");
+}
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1532,72 +1589,35 @@ bht_status ht_reconstruct(const bht_state* st, int64_t first, int64_t count, voi
   if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
   if (first < 0 || count < 0 || first + count > st->n_items) fail(BHT_EINVAL, "item range outside the accumulation");
   if (count == 0) return BHT_OK;
+  decode_latent(st, st->root + first * st->r11() * st->r12(), count, out, dtype, static_cast<cudaStream_t>(stream));
+  BHT_API_END
+}
+
+bht_status ht_decode(const bht_state* st, const double* latent, int64_t N, void* out, int32_t dtype, void* stream) {
+  BHT_API_BEGIN
+  if (!st || (N > 0 && (!latent || !out))) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 0) fail(BHT_EINVAL, "N must be >= 0");
+  if (N == 0) return BHT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bht_tree& t = st->tree;
-  const Arith ar = make_arith(st->precision, 1.0, st->d_status);
-  LTensor C;
-  C.dtype = BHT_F64;
-  C.N = count;
-  C.dims = {st->r11(), st->r12()};
-  C.node = {t.nodes[0].child[0], t.nodes[0].child[1]};
-  C.ptr = st->root + first * st->r11() * st->r12();
-  for (int layer = 1; layer <= t.p; ++layer) {
-    // expand every node of this layer: axis r -> rows (eq. htucker_reconstruction)
-    std::vector<std::pair<int, int64_t>> ops;
-    std::vector<int> ids;
-    for (int id : t.layers[layer]) {
-      ids.push_back(id);
-      ops.push_back({C.axis_of(id), st->rows(id)});
-    }
-    for (int k : best_order(C.dims, ops)) {
-      const int id = ids[k];
-      const int ax = C.axis_of(id);
-      const int64_t r = st->rank[id], a = st->rows(id);
-      LTensor nxt = ttm_any(C, ax, st->U[id], r, 1, a, false, ar, s);
-      C = std::move(nxt);
-    }
-    // split transfer axes into their successors' axes (C-order)
-    std::vector<int64_t> dims;
-    std::vector<int> node;
-    for (size_t i = 0; i < C.node.size(); ++i) {
-      const TNode& nd = t.nodes[C.node[i]];
-      if (nd.layer == layer && !nd.leaf()) {
-        dims.push_back(st->rank[nd.child[0]]);
-        dims.push_back(st->rank[nd.child[1]]);
-        node.push_back(nd.child[0]);
-        node.push_back(nd.child[1]);
-      } else {
-        dims.push_back(C.dims[i]);
-        node.push_back(C.node[i]);
-      }
-    }
-    C.dims = dims;
-    C.node = node;
-  }
-  const int64_t n = C.numel();
-  if (is_device_ptr(out)) {
-    copy_convert(C, out, dtype, s);
-  } else {
-    DBuf tmp(dtype_size(dtype) * n, s);
-    copy_convert(C, tmp.p, dtype, s);
-    ck(cudaMemcpyAsync(out, tmp.p, dtype_size(dtype) * n, cudaMemcpyDeviceToHost, s), "D2H");
-    ck(cudaStreamSynchronize(s), "sync");
-  }
-  ck(cudaStreamSynchronize(s), "sync");
+  DBuf staging;
+  const double* dZ = static_cast<const double*>(stage_input(latent, BHT_F64, N * st->r11() * st->r12(), staging, s));
+  decode_latent(st, dZ, N, out, dtype, s);
   BHT_API_END
 }
 
 bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t N, double* out, void* stream) {
   BHT_API_BEGIN
-  if (!st || !Y || !out) fail(BHT_EINVAL, "null argument");
+  if (!st || (N > 0 && (!Y || !out))) fail(BHT_EINVAL, "null argument");
   if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
-  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (N < 0) fail(BHT_EINVAL, "N must be >= 0");
+  if (N == 0) return BHT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int64_t item = 1;
   for (auto v : st->tree.dims) item *= v;
   DBuf staging;
   const void* dY = stage_input(Y, dtype, N * item, staging, s);
-  const Arith ar = make_arith(st->precision, st->precision == BHT_PREC_MIXED ? 1.0 : 1.0, st->d_status);
+  const Arith ar = make_arith(st->precision, 1.0, st->d_status);
   LTensor C = project_all(st, dY, dtype, N, ar, s);
   if (is_device_ptr(out)) {
     copy_convert(C, out, BHT_F64, s);

@@ -439,3 +439,76 @@ def test_remaining_truncation_counts_of_a_five_mode_tree():
     assert OB._svds_above(t, 4) == 8       # before layer 3: all 2d - 2 truncations remain
     assert OB._svds_above(t, 3) == 6       # after layer 3: layers 2 and 1
     assert OB._svds_above(t, 2) == 2       # after layer 2: layer 1
+
+
+# ---------------------------------------------------------------------------
+# Decoding of latent items and the relative test error (eq. htucker_reconstruction with the
+# orthonormal frames of Sec. 3; Step 1 of Algorithm 2 as the encoder)
+# ---------------------------------------------------------------------------
+
+def _small_state(seed, dims=(2, 3, 2, 3), eps=0.3, N=6):
+    rng = np.random.default_rng(seed)
+    Y = rng.normal(size=(N,) + dims) + np.cumsum(rng.normal(size=(N,) + dims), axis=1)
+    return O.bht_l2r(Y, eps), Y
+
+
+def test_decode_of_a_unit_latent_by_explicit_loops():
+    # tree of (2,3,2,3): layer 1 {1,2},{3,4}; layer 2 the leaves. decode(e_ij) is the outer product of the
+    # two layer-1 frames' columns i and j, each frame (U_a (x) U_b) B written out index by index
+    st, _ = _small_state(31)
+    t = st.tree
+    l1 = t.layers[1]
+    cores = st.cores
+    frames = []
+    for nid in l1:
+        a, b = t.nodes[nid].children
+        Ua, Ub, Bt = cores[a], cores[b], cores[nid]
+        na, nb = Ua.shape[0], Ub.shape[0]
+        F = np.zeros((na, nb, Bt.shape[2]))
+        for x in range(na):
+            for y in range(nb):
+                for k in range(Bt.shape[2]):
+                    F[x, y, k] = sum(Ua[x, p] * Ub[y, q] * Bt[p, q, k]
+                                     for p in range(Ua.shape[1]) for q in range(Ub.shape[1]))
+        frames.append(F)
+    r11, r12 = frames[0].shape[2], frames[1].shape[2]
+    for i in range(r11):
+        for j in range(r12):
+            Z = np.zeros((1, r11, r12))
+            Z[0, i, j] = 1.0
+            want = np.einsum("ab,cd->abcd", frames[0][:, :, i], frames[1][:, :, j])
+            assert np.abs(O.decode(st, Z)[0] - want).max() < 1e-13
+
+
+def test_decode_is_an_isometry_and_the_adjoint_of_projection():
+    st, _ = _small_state(32, dims=(3, 4, 5, 2, 3), eps=0.2, N=9)
+    rng = np.random.default_rng(33)
+    r = st.ranks()
+    Z = rng.normal(size=(7, r[1], r[2]))
+    X = rng.normal(size=(7,) + st.tree.dims)
+    D = O.decode(st, Z)
+    for n in range(7):      # orthonormal frames: every item keeps its norm
+        assert abs(np.linalg.norm(D[n]) - np.linalg.norm(Z[n])) < 1e-12 * np.linalg.norm(Z[n])
+    assert abs(np.sum(D * X) - np.sum(Z * O.project(st, X))) < 1e-11 * np.linalg.norm(Z) * np.linalg.norm(X)
+
+
+def test_relative_test_error_closed_forms():
+    # items that are sums of three separable terms plus 5 % noise: the frames keep a small subspace
+    rng = np.random.default_rng(34)
+    dims = (4, 5, 4, 5)
+    Y = sum(np.einsum("n,a,b,c,d->nabcd", *[rng.normal(size=m) for m in (12,) + dims]) for _ in range(3))
+    Y = Y + 0.05 * np.linalg.norm(Y) / np.sqrt(Y.size) * rng.normal(size=Y.shape)
+    st = O.bht_l2r(Y, 0.25)
+    r = st.ranks()
+    k, n = r[1] * r[2], int(np.prod(st.tree.dims))
+    assert k < n // 4
+    # items drawn from the represented subspace are represented exactly
+    assert O.relative_test_error(st, O.decode(st, rng.normal(size=(5, r[1], r[2])))) < 1e-13
+    # isotropic Gaussian items keep k/n of their energy on average: RTE^2 -> 1 - k/n (chi-square with
+    # k of N n degrees of freedom; 4000 items put the relative spread of the estimate near 1e-3)
+    rte = O.relative_test_error(st, rng.normal(size=(4000,) + st.tree.dims))
+    assert abs(rte ** 2 - (1 - k / n)) < 0.02 * (1 - k / n)
+    # the accumulated batch itself: the projection onto the frames is the best in their span, so it is
+    # no worse than the stored approximation, which meets the bound of Corollary bht_leaves_to_root
+    assert O.relative_test_error(st, Y) <= 0.25 * (1 + 1e-12)
+    assert abs(O.relative_test_error(st, Y) - rel(O.reconstruct(st), Y)) < 1e-12
