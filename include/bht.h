@@ -143,6 +143,20 @@ bht_status bht_tree_info(const bht_tree* tree, int32_t* depth, int32_t* num_node
 bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N,
                    double eps_rel, const bht_opts* opts, void* stream, bht_state** out);
 
+/* Plain hierarchical Tucker baseline (the leaves-to-root algorithm of Sec. 2.3.1, one-shot): the N
+ * items are one (d+1)-mode tensor with the batch as the LAST leaf of the balanced tree over
+ * (n_1, .., n_d, N) (Fig. htucker_as_node), truncated with eps_nw = eps_rel ||Y|| / sqrt(2(d+1) - 3)
+ * (Theorem ht_nodewise_error).
+ *   dims   : the d item mode sizes, each in [1, 4096]; 2 <= d <= 15.
+ *   Y      : [N][n_1]..[n_d] item-major, element type `dtype`, device or host; 1 <= N <= 4096.
+ *   opts   : precision as for bht_l2r; the budget must be uniform (BHT_EINVAL otherwise).
+ *   out    : a state of one tensor: bht_get_dims reports (n_1, .., n_d, N), bht_get_ranks[0] = 1, the
+ *            root is the r_11 x r_12 matrix of the last truncation, and ht_reconstruct(state, 0, 1)
+ *            writes the tensor with the batch last, [n_1]..[n_d][N]. htrise_update and ht_encode
+ *            return BHT_EINVAL on it. */
+bht_status ht_l2r(int32_t d, const int64_t* dims, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                  const bht_opts* opts, void* stream, bht_state** out);
+
 /* HT-RISE (Algorithm 2): update `state` with a new batch of N items.
  *   Projects Y onto the current cores; if the projection error is <= eps_rel ||Y||
  *   only the root grows, otherwise residuals are truncated node by node, the
@@ -164,6 +178,38 @@ bht_status ht_reconstruct(const bht_state* state, int64_t first, int64_t count,
  * nothing; N < 0 is BHT_EINVAL. Never modifies the state. Synchronises `stream`. */
 bht_status ht_decode(const bht_state* state, const double* latent, int64_t N, void* out, int32_t dtype,
                      void* stream);
+
+/* Relative test error of N items X (eq. generalization_performance): each item is encoded (Step 1
+ * of Algorithm 2) and decoded (eq. htucker_reconstruction) on the current cores and the per-item
+ * relative errors ||X_i - X~_i|| / ||X_i|| are averaged into *rte (host). item_err (host, [N]) may be
+ * NULL, else receives the per-item errors; an all-zero item that decodes to zero counts 0.
+ * X: [N][n_1]..[n_d], element type `dtype`, host or device; N >= 1. BHT_EINVAL on a plain HT state.
+ * Works in chunks of at most 2^27 decoded elements. Synchronises `stream`. */
+bht_status ht_relative_test_error(const bht_state* state, const void* X, int32_t dtype, int64_t N, double* rte,
+                                  double* item_err, void* stream);
+
+/* Normalisation of snapshots before compression, in place on device memory: Y holds `groups`
+ * consecutive groups of `group_size` elements (one group per item, or per item and physical
+ * quantity) and every group is normalised on its own, y <- (y - shift) / scale, with
+ *   BHT_NORM_MAXABS : shift 0, scale max |y|;
+ *   BHT_NORM_UNITVEC: shift 0, scale ||y||_2;
+ *   BHT_NORM_ZSCORE : shift mean(y), scale the population standard deviation of y;
+ *   BHT_NORM_NONE   : Y unchanged, params (0, 1).
+ * A scale that is zero or not finite is replaced by 1. params ([groups][2] FP64 (shift, scale),
+ * host or device) receives the parameters for bht_denormalize. Synchronises `stream`. */
+typedef enum { BHT_NORM_NONE = 0, BHT_NORM_MAXABS = 1, BHT_NORM_UNITVEC = 2, BHT_NORM_ZSCORE = 3 } bht_norm;
+bht_status bht_normalize(void* Y, int32_t dtype, int64_t groups, int64_t group_size, int32_t kind, double* params,
+                         void* stream);
+/* Inverse of bht_normalize: y <- y * scale + shift per group (params host or device). */
+bht_status bht_denormalize(void* Y, int32_t dtype, int64_t groups, int64_t group_size, const double* params,
+                           void* stream);
+
+/* Reordering of the item axes (the axis-ordering study of App. D): out[n] is item n of Y with its
+ * axes permuted, out axis k = input axis perm[k], so out has the item shape (dims[perm[0]], ..,
+ * dims[perm[d-1]]). Y and out: distinct device buffers of N items; 1 <= d <= 16. Synchronises
+ * `stream`. */
+bht_status bht_permute_items(const void* Y, int32_t dtype, int64_t N, int32_t d, const int64_t* dims,
+                             const int32_t* perm, void* out, void* stream);
 
 /* Latent representation of N unseen items on the current cores (Step 1 of
  * Algorithm 2), written item-major [N][r_11][r_12] as FP64 into `out`

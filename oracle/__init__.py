@@ -11,6 +11,7 @@ the paper's algorithms step by step (see ``bht_oracle``).
 from .bht_oracle import (  # noqa: F401
     Tree, Node, dimension_tree, truncation_rank, truncated_left_svd,
     BHTState, UpdateInfo, bht_l2r, htrise_update, project, reconstruct, decode, relative_test_error,
+    ht_l2r, ht_items, reduction_ratio, normalize,
     compression_ratio, layer_shape,
 )
 from . import mlp_oracle  # noqa: F401

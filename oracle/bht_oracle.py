@@ -313,6 +313,56 @@ def bht_l2r(Y: np.ndarray, eps_rel: float, tree: Tree = None, budget: str = "uni
 
 
 # ---------------------------------------------------------------------------
+# Plain HT baseline: leaves-to-root HT (Sec. 2.3.1) with the batch as a leaf (Fig. htucker_as_node)
+# ---------------------------------------------------------------------------
+
+def ht_l2r(Y: np.ndarray, eps_rel: float) -> BHTState:
+    """One-shot leaves-to-root HT decomposition of the N items as a single tensor (n_1, .., n_d, N): the
+    batch is the last leaf of the balanced tree over d + 1 modes. Layers p .. 2 are truncated node by
+    node from the same intermediate as in Algorithm 1; layer 1 is one error-truncated SVD of the matrix
+    C_1 (eq. ht_last_svd) whose left and right singular vectors become the two layer-1 cores and whose
+    singular values the root. Node-wise tolerance eps_rel ||Y|| / sqrt(2 (d + 1) - 3) (Theorem
+    ht_nodewise_error). The state holds one item (root [r_11, r_12, 1], diagonal)."""
+    T = np.moveaxis(np.asarray(Y, dtype=np.float64), 0, -1)
+    tree = Tree(T.shape)
+    C = T[..., None]             # a trailing axis of one item, so the layer helpers above apply
+    state = BHTState(tree=tree, eps_rel=float(eps_rel))
+    norm2 = float(np.sum(C * C))
+    eps_nw = eps_rel * math.sqrt(norm2) / math.sqrt(2 * tree.d - 3)
+    axes = _initial_axes(tree)
+
+    def store(nd, U):
+        if nd.is_leaf:
+            state.cores[nd.id] = U
+        else:
+            a, b = nd.children
+            state.cores[nd.id] = U.reshape(state.rank(a), state.rank(b), U.shape[1])
+
+    for layer in range(tree.p, 1, -1):
+        if layer < tree.p:
+            C, axes = _reshape_to_layer(tree, C, axes, layer)
+        bases = {nd.id: truncated_left_svd(unfold(C, axes.index(nd.id)), eps_nw, rmin=1)[0]
+                 for nd in tree.layer_nodes(layer)}
+        for nd in tree.layer_nodes(layer):
+            store(nd, bases[nd.id])
+            C = mode_product_t(C, axes.index(nd.id), bases[nd.id])
+    C, axes = _reshape_to_layer(tree, C, axes, 1)
+    U, s, Vt = np.linalg.svd(C[:, :, 0], full_matrices=False)
+    r = truncation_rank(s * s, eps_nw * eps_nw, 1)
+    left, right = tree.layer_nodes(1)
+    store(left, U[:, :r].copy())
+    store(right, Vt[:r].T.copy())
+    state.root = np.diag(s[:r])[:, :, None]
+    state.n_items = 1
+    return state
+
+
+def ht_items(state: BHTState) -> np.ndarray:
+    """The tensor of a plain HT state back in item-major order [N, n_1, .., n_d]."""
+    return np.moveaxis(reconstruct(state)[0], -1, 0)
+
+
+# ---------------------------------------------------------------------------
 # Step 1 of Algorithm 2: projection onto the existing cores
 # ---------------------------------------------------------------------------
 
@@ -441,11 +491,44 @@ def reconstruct(state: BHTState, first: int = 0, count: int = None) -> np.ndarra
     return decode(state, np.moveaxis(state.root[:, :, first:first + count], -1, 0))
 
 
-def relative_test_error(state: BHTState, X: np.ndarray) -> float:
-    """||X - decode(project(X))|| / ||X|| for items X that need not be in the accumulation: the
-    error with which the current cores represent unseen data."""
+def relative_test_error(state: BHTState, X: np.ndarray, per_item: bool = False):
+    """eq. generalization_performance: the mean over the items X_i (which need not be in the
+    accumulation) of ||X_i - decode(project(X_i))|| / ||X_i||; an all-zero item counts 0."""
     X = np.asarray(X, dtype=np.float64)
-    return float(np.linalg.norm(X - decode(state, project(state, X))) / np.linalg.norm(X))
+    E = X - decode(state, project(state, X))
+    errs = np.array([np.linalg.norm(E[i]) / np.linalg.norm(X[i]) if np.any(X[i]) else 0.0
+                     for i in range(X.shape[0])])
+    return (float(errs.mean()), errs) if per_item else float(errs.mean())
+
+
+def reduction_ratio(state: BHTState) -> float:
+    """eq. reduction_ratio: elements of one item over elements of its latent representation (r_11 r_12)."""
+    r = state.ranks()
+    return int(np.prod(state.tree.dims)) / (r[1] * r[2])
+
+
+def normalize(Y: np.ndarray, kind: str, groups: int = None):
+    """Normalisation of the scientific-data experiments (Sec. 5.2), each group of consecutive elements on
+    its own (default one group per item): maxabs Y / max|Y|, unitvec Y / ||Y||, zscore (Y - mean) / std
+    with the population standard deviation; a zero or non-finite scale is replaced by 1. Returns the
+    normalised float64 array and the (shift, scale) rows."""
+    Y = np.asarray(Y, dtype=np.float64)
+    groups = Y.shape[0] if groups is None else groups
+    G = Y.reshape(groups, -1)
+    shift = np.zeros(groups)
+    if kind == "maxabs":
+        scale = np.abs(G).max(axis=1)
+    elif kind == "unitvec":
+        scale = np.sqrt((G * G).sum(axis=1))
+    elif kind == "zscore":
+        shift = G.mean(axis=1)
+        scale = np.sqrt(((G - shift[:, None]) ** 2).mean(axis=1))
+    elif kind == "none":
+        scale = np.ones(groups)
+    else:
+        raise ValueError(kind)
+    scale = np.where((scale > 0) & np.isfinite(scale), scale, 1.0)
+    return ((G - shift[:, None]) / scale[:, None]).reshape(Y.shape), np.column_stack([shift, scale])
 
 
 def compression_ratio(state: BHTState, n_items_elements: int = None) -> float:

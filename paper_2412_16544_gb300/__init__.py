@@ -73,6 +73,11 @@ def _load():
         "bht_mode_product_noalloc": [vp, i64, i64, vp, i64, vp, i64, vp, vp],
         "bht_profile_read": [P(dbl), P(i64), P(dbl), P(dbl), i32, i32],
         "ht_decode": [vp, vp, i64, vp, i32, vp],
+        "ht_l2r": [i32, P(i64), vp, i32, i64, dbl, P(_Opts), vp, P(vp)],
+        "ht_relative_test_error": [vp, vp, i32, i64, P(dbl), P(dbl), vp],
+        "bht_normalize": [vp, i32, i64, i64, i32, vp, vp],
+        "bht_denormalize": [vp, i32, i64, i64, vp, vp],
+        "bht_permute_items": [vp, i32, i64, i32, P(i64), P(ctypes.c_int32), vp, vp],
         "bht_mlp_create": [i32, i32, vp, P(vp)],
         "bht_mlp_destroy": [vp],
         "bht_mlp_num_params": [vp, P(i64)],
@@ -101,7 +106,8 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
             "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
-            "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode"]
+            "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode", "ht_l2r",
+            "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items"]
 KERNEL_CLASSES = 16
 
 
@@ -217,6 +223,17 @@ def bht_l2r(tree, Y, eps_rel: float, precision=None, stream=None, budget=None) -
     return h
 
 
+def ht_l2r(Y, eps_rel: float, precision=None, stream=None) -> ctypes.c_void_p:
+    """Plain HT baseline: the batch Y [N, n_1..n_d] as one tensor with the batch as the last leaf."""
+    ptr, code, shape, keep = _buffer(Y)
+    dims = (ctypes.c_int64 * (len(shape) - 1))(*shape[1:])
+    h = ctypes.c_void_p()
+    _check(_lib.ht_l2r(len(shape) - 1, dims, ptr, code, int(shape[0]), float(eps_rel), _opts(precision),
+                       _stream(stream), ctypes.byref(h)), "ht_l2r")
+    del keep
+    return h
+
+
 def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predictor=None, node_features=None,
                   node_labels=None, budget=None) -> UpdateInfo:
     """node_features (float32 [nodes][66]) and node_labels (int64 [nodes][2]): host numpy arrays the call
@@ -297,14 +314,67 @@ def ht_decode(state, Z, out=None, dtype="float32", stream=None):
     return out
 
 
-def relative_test_error(state, X, stream=None) -> float:
-    """||X - decode(encode(X))|| / ||X|| for unseen items X (the relative test error), on the GPU."""
+def relative_test_error(state, X, per_item: bool = False, stream=None):
+    """Mean over the items of X of ||X_i - decode(encode(X_i))|| / ||X_i|| (eq. generalization_performance);
+    with per_item=True also the per-item errors."""
+    ptr, code, shape, keep = _buffer(X)
+    dims = bht_get_dims(state)
+    if tuple(shape[1:]) != tuple(dims):
+        raise ValueError(f"items must be [N, {', '.join(map(str, dims))}], got {tuple(shape)}")
+    rte = ctypes.c_double()
+    errs = np.zeros(shape[0], dtype=np.float64)
+    _check(_lib.ht_relative_test_error(state, ptr, code, int(shape[0]), ctypes.byref(rte),
+                                       errs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)),
+           "ht_relative_test_error")
+    del keep
+    return (rte.value, errs) if per_item else rte.value
+
+
+NORMALIZATIONS = {"none": 0, "maxabs": 1, "unitvec": 2, "zscore": 3}
+
+
+def bht_normalize(Y, kind: str, groups: int = None, stream=None) -> np.ndarray:
+    """Normalise the device tensor Y in place, group by group (default: one group per item); returns the
+    (shift, scale) parameters [groups, 2]."""
+    ptr, code, shape, keep = _buffer(Y)
+    total = int(np.prod(shape)) if len(shape) else 0
+    groups = int(shape[0]) if groups is None else int(groups)
+    if groups <= 0 or total % groups:
+        raise ValueError("groups must divide the element count")
+    params = np.zeros((groups, 2), dtype=np.float64)
+    _check(_lib.bht_normalize(ptr, code, groups, total // groups, NORMALIZATIONS[kind],
+                              ctypes.c_void_p(params.ctypes.data), _stream(stream)), "bht_normalize")
+    del keep
+    return params
+
+
+def bht_denormalize(Y, params, stream=None) -> None:
+    ptr, code, shape, keep = _buffer(Y)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    groups = params.shape[0]
+    total = int(np.prod(shape))
+    if groups <= 0 or total % groups:
+        raise ValueError("params rows must divide the element count")
+    _check(_lib.bht_denormalize(ptr, code, groups, total // groups, ctypes.c_void_p(params.ctypes.data),
+                                _stream(stream)), "bht_denormalize")
+    del keep
+
+
+def bht_permute_items(Y, perm, stream=None):
+    """Items of the device tensor Y [N, n_1..n_d] with their axes reordered: out axis k = item axis perm[k]."""
     torch = _torch()
-    Z = ht_encode(state, X, stream=stream)
-    Xh = ht_decode(state, Z, dtype="float64", stream=stream)
-    Xd = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    Xd = Xd.to(torch.float64)
-    return float(torch.linalg.vector_norm(Xh - Xd) / torch.linalg.vector_norm(Xd))
+    ptr, code, shape, keep = _buffer(Y)
+    d = len(shape) - 1
+    perm = [int(p) for p in perm]
+    if len(perm) != d:
+        raise ValueError("perm needs one entry per item axis")
+    out = torch.empty((shape[0], *[shape[1 + p] for p in perm]), dtype=Y.dtype, device=Y.device)
+    optr, _, _, okeep = _buffer(out)
+    dims = (ctypes.c_int64 * d)(*shape[1:])
+    pm = (ctypes.c_int32 * d)(*perm)
+    _check(_lib.bht_permute_items(ptr, code, int(shape[0]), d, dims, pm, optr, _stream(stream)), "bht_permute_items")
+    del keep, okeep
+    return out
 
 
 def bht_get_core(state, node: int) -> np.ndarray:

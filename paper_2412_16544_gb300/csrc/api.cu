@@ -131,7 +131,7 @@ const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
-                                             "house_f64",      "mlp",            "other"};
+                                             "house_f64",      "mlp",            "prep",            "other"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -308,6 +308,7 @@ struct bht_state {
   int64_t root_cap = 0;
   int64_t n_items = 0;
   int* d_status = nullptr;      // device status word of bounded waits
+  bool plain = false;           // plain HT of one tensor (n_1..n_d, N): the batch is a leaf, not the root's
 
   int64_t rows(int id) const {  // alpha of eq. compute_residual; n for a leaf
     const TNode& nd = tree.nodes[id];
@@ -1182,23 +1183,21 @@ bht_status bht_tree_info(const bht_tree* tree, int32_t* depth, int32_t* num_node
   return BHT_OK;
 }
 
-bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N, double eps_rel,
-                   const bht_opts* opts, void* stream, bht_state** out) {
-  BHT_API_BEGIN
-  if (!tree || !Y || !out) fail(BHT_EINVAL, "null argument");
-  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
-  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
-  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
-  validate_opts(opts);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bht_tree& t = *tree;
-  int64_t item = 1;
-  for (auto v : t.dims) item *= v;
+namespace {
+// Leaves-to-root decomposition (Algorithm 1; for `plain`, the leaves-to-root HT algorithm of Sec. 2.3.1
+// with the batch as the last leaf of the tree t over (n_1, .., n_d, N)). Y is item-major [N][n_1..n_d]
+// in both cases, so for `plain` the batch is the outermost axis of the single tensor until the first
+// reshape moves it behind the others.
+bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, double eps_rel, const bht_opts* opts,
+                     cudaStream_t s, bool plain) {
+  int64_t total = plain ? 1 : N;
+  for (auto v : t.dims) total *= v;
   DBuf staging;
-  const void* dY = stage_input(Y, dtype, N * item, staging, s);
+  const void* dY = stage_input(Y, dtype, total, staging, s);
 
   bht_state* st = new bht_state();
   st->tree = t;
+  st->plain = plain;
   st->precision = opts ? opts->precision : BHT_PREC_FP64;
   st->budget = (opts && opts->budget == BHT_BUDGET_ADAPTIVE) ? BHT_BUDGET_ADAPTIVE : BHT_BUDGET_UNIFORM;
   st->rank.assign(t.nodes.size(), 0);
@@ -1208,20 +1207,46 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
     ck(cudaMalloc(&st->d_status, sizeof(int)), "cudaMalloc status");
     ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
     DBuf acc(sizeof(double) * 2, s);
-    sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
+    sqnorm_of(dY, dtype, total, acc.as<double>(), s);
     double normY2 = 0.0;
     ck(cudaMemcpyAsync(&normY2, acc.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norm");
     ck(cudaStreamSynchronize(s), "sync");
     if (!std::isfinite(normY2)) fail(BHT_ENUMERIC, "the batch holds non-finite values");
-    // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1)
-    double eps_nw2 = eps_rel * eps_rel * normY2 / (2.0 * t.d - 2.0);
+    // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1). The plain HT tree has d + 1
+    // modes and one SVD fewer: its layer-1 nodes split one matrix, whose left and right truncations at
+    // the same rank remove the same energy, hence sqrt(2 (d + 1) - 3) (Theorem ht_nodewise_error).
+    double eps_nw2 = eps_rel * eps_rel * normY2 / (plain ? 2.0 * t.d - 3.0 : 2.0 * t.d - 2.0);
     const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
     const bool adaptive = st->budget == BHT_BUDGET_ADAPTIVE;
     DBuf removed(sizeof(double), s);
     ck(cudaMemsetAsync(removed.p, 0, sizeof(double), s), "memset");
 
     LTensor C = input_tensor(t, dY, dtype, N);
+    if (plain) {  // one tensor [N][n_1..n_d]: the batch leaf carries the outermost axis
+      C.N = 1;
+      C.dims.assign(1, N);
+      C.node.assign(1, t.leaf_of_mode[t.d - 1]);
+      for (int m = 0; m + 1 < t.d; ++m) {
+        C.dims.push_back(t.dims[m]);
+        C.node.push_back(t.leaf_of_mode[m]);
+      }
+    }
     for (int layer = t.p; layer >= 1; --layer) {
+      if (layer < t.p && plain && C.node[0] == t.leaf_of_mode[t.d - 1]) {
+        // move the batch axis behind the others, the tree's order: [b][rest] -> [rest][b]
+        LTensor T;
+        T.dtype = C.dtype;
+        T.N = 1;
+        T.dims.assign(C.dims.begin() + 1, C.dims.end());
+        T.dims.push_back(C.dims[0]);
+        T.node.assign(C.node.begin() + 1, C.node.end());
+        T.node.push_back(C.node[0]);
+        T.own = DBuf(dtype_size(C.dtype) * (size_t)C.numel(), s);
+        T.ptr = T.own.p;
+        ck(launch_transpose2d(C.ptr, T.own.p, C.dims[0], C.numel() / C.dims[0], (int)dtype_size(C.dtype), s),
+           "transpose");
+        C = std::move(T);
+      }
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
       // HOSVD of the layer: every node from the same intermediate, the nodes side by side
@@ -1277,16 +1302,50 @@ bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N
         eps_nw2 = adaptive_eps_nw2(eps_rel * eps_rel * normY2, spent2, svds_through(t, layer - 1));
       }
     }
-    // G_0 = reshape(C, [r11, r12, N]) stored item-major
-    grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), N, s);
+    // G_0 = reshape(C, [r11, r12, N]) stored item-major (plain: the one root matrix)
+    const int64_t items = plain ? 1 : N;
+    grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), items, s);
     copy_convert(C, st->root, BHT_F64, s);
-    st->n_items = N;
+    st->n_items = items;
     ck(cudaStreamSynchronize(s), "sync");
-    *out = st;
+    return st;
   } catch (...) {
     bht_state_destroy(st);
     throw;
   }
+}
+}  // namespace
+
+
+bht_status bht_l2r(const bht_tree* tree, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                   const bht_opts* opts, void* stream, bht_state** out) {
+  BHT_API_BEGIN
+  if (!tree || !Y || !out) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  *out = l2r_build(*tree, Y, dtype, N, eps_rel, opts, static_cast<cudaStream_t>(stream), false);
+  BHT_API_END
+}
+
+bht_status ht_l2r(int32_t d, const int64_t* dims, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                  const bht_opts* opts, void* stream, bht_state** out) {
+  BHT_API_BEGIN
+  if (!dims || !Y || !out) fail(BHT_EINVAL, "null argument");
+  if (d < 2 || d > 15) fail(BHT_EINVAL, "d must be in [2, 15]");
+  for (int i = 0; i < d; ++i)
+    if (dims[i] < 1 || dims[i] > 4096) fail(BHT_EINVAL, "every mode size must be in [1, 4096]");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1 || N > 4096) fail(BHT_EINVAL, "the batch is a mode of the tree: N must be in [1, 4096]");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  if (opts && opts->budget == BHT_BUDGET_ADAPTIVE) fail(BHT_EINVAL, "the plain HT baseline takes the uniform budget");
+  std::vector<int64_t> full(dims, dims + d);
+  full.push_back(N);
+  bht_tree t;
+  build_tree(t, d + 1, full.data());
+  *out = l2r_build(t, Y, dtype, N, eps_rel, opts, static_cast<cudaStream_t>(stream), true);
   BHT_API_END
 }
 
@@ -1298,6 +1357,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
   if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
   validate_opts(opts);
+  if (st->plain) fail(BHT_EINVAL, "HT-RISE appends items along the root; this state holds a plain HT tensor");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bht_tree& t = st->tree;
   int64_t item = 1;
@@ -1606,11 +1666,117 @@ bht_status ht_decode(const bht_state* st, const double* latent, int64_t N, void*
   BHT_API_END
 }
 
+bht_status ht_relative_test_error(const bht_state* st, const void* X, int32_t dtype, int64_t N, double* rte,
+                                  double* item_err, void* stream) {
+  BHT_API_BEGIN
+  if (!st || !X || !rte) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (st->plain) fail(BHT_EINVAL, "a plain HT state has no item axis to encode along");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t item = 1;
+  for (auto v : st->tree.dims) item *= v;
+  DBuf staging;
+  const char* dX = static_cast<const char*>(stage_input(X, dtype, N * item, staging, s));
+  const Arith ar = make_arith(st->precision, 1.0, st->d_status);
+  DBuf acc(sizeof(double) * 2 * N, s);
+  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 2 * N, s), "memset");
+  double* err2 = acc.as<double>();
+  double* nrm2 = err2 + N;
+  // items in chunks of at most 2^27 decoded FP64 elements (1 GiB)
+  const int64_t per = std::max<int64_t>(1, ((int64_t)1 << 27) / item);
+  for (int64_t first = 0; first < N; first += per) {
+    const int64_t n = std::min(per, N - first);
+    const void* xc = dX + dtype_size(dtype) * (size_t)(first * item);
+    LTensor C = project_all(st, xc, dtype, n, ar, s);           // encode (Step 1 of Algorithm 2)
+    DBuf Z(sizeof(double) * (size_t)C.numel(), s);
+    copy_convert(C, Z.p, BHT_F64, s);
+    DBuf Xh(sizeof(double) * (size_t)(n * item), s);
+    decode_latent(st, Z.as<double>(), n, Xh.p, BHT_F64, s);   // decode (eq. htucker_reconstruction)
+    ck(launch_item_errors(xc, dtype, Xh.as<double>(), n, item, err2 + first, nrm2 + first, s), "item errors");
+  }
+  std::vector<double> h(2 * N);
+  ck(cudaMemcpyAsync(h.data(), acc.p, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, s), "D2H errors");
+  ck(cudaStreamSynchronize(s), "sync");
+  // eq. generalization_performance: the mean over items of ||X_i - X~_i|| / ||X_i|| (a zero item that
+  // decodes to zero has error 0)
+  double sum = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    const double e = h[i] > 0.0 ? std::sqrt(h[i] / h[N + i]) : 0.0;
+    if (item_err) item_err[i] = e;
+    sum += e;
+  }
+  *rte = sum / (double)N;
+  BHT_API_END
+}
+
+bht_status bht_normalize(void* Y, int32_t dtype, int64_t groups, int64_t group_size, int32_t kind, double* params,
+                         void* stream) {
+  BHT_API_BEGIN
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (kind < BHT_NORM_NONE || kind > BHT_NORM_ZSCORE) fail(BHT_EINVAL, "unknown normalisation");
+  if (groups < 0 || group_size < 0) fail(BHT_EINVAL, "negative size");
+  if (groups == 0 || group_size == 0) return BHT_OK;
+  if (!Y || !params) fail(BHT_EINVAL, "null argument");
+  if (!is_device_ptr(Y)) fail(BHT_EINVAL, "Y must be device memory (normalised in place)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dev = is_device_ptr(params);
+  DBuf tmp;
+  double* dp = params;
+  if (!dev) {
+    tmp = DBuf(sizeof(double) * 2 * groups, s);
+    dp = tmp.as<double>();
+  }
+  ck(launch_normalize(Y, dtype, groups, group_size, kind, dp, s), "normalise");
+  if (!dev) ck(cudaMemcpyAsync(params, dp, sizeof(double) * 2 * groups, cudaMemcpyDeviceToHost, s), "D2H params");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_denormalize(void* Y, int32_t dtype, int64_t groups, int64_t group_size, const double* params,
+                           void* stream) {
+  BHT_API_BEGIN
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (groups < 0 || group_size < 0) fail(BHT_EINVAL, "negative size");
+  if (groups == 0 || group_size == 0) return BHT_OK;
+  if (!Y || !params) fail(BHT_EINVAL, "null argument");
+  if (!is_device_ptr(Y)) fail(BHT_EINVAL, "Y must be device memory (restored in place)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf staging;
+  const double* dp = static_cast<const double*>(stage_input(params, BHT_F64, 2 * groups, staging, s));
+  ck(launch_denormalize(Y, dtype, groups, group_size, dp, s), "denormalise");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
+bht_status bht_permute_items(const void* Y, int32_t dtype, int64_t N, int32_t d, const int64_t* dims,
+                             const int32_t* perm, void* out, void* stream) {
+  BHT_API_BEGIN
+  if (!Y || !dims || !perm || !out) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (d < 1 || d > 16) fail(BHT_EINVAL, "d must be in [1, 16]");
+  if (N < 0) fail(BHT_EINVAL, "N must be >= 0");
+  std::vector<int> seen(d, 0), pm(d);
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1) fail(BHT_EINVAL, "every mode size must be >= 1");
+    if (perm[k] < 0 || perm[k] >= d || seen[perm[k]]++) fail(BHT_EINVAL, "perm is not a permutation of 0 .. d-1");
+    pm[k] = perm[k];
+  }
+  if (!is_device_ptr(Y) || !is_device_ptr(out)) fail(BHT_EINVAL, "Y and out must be device memory");
+  if (Y == out) fail(BHT_EINVAL, "the permutation is out of place");
+  if (N == 0) return BHT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ck(launch_permute_items(Y, dtype, N, d, dims, pm.data(), out, s), "permute");
+  ck(cudaStreamSynchronize(s), "sync");
+  BHT_API_END
+}
+
 bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t N, double* out, void* stream) {
   BHT_API_BEGIN
   if (!st || (N > 0 && (!Y || !out))) fail(BHT_EINVAL, "null argument");
   if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
   if (N < 0) fail(BHT_EINVAL, "N must be >= 0");
+  if (st->plain) fail(BHT_EINVAL, "a plain HT state has no item axis to encode along");
   if (N == 0) return BHT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int64_t item = 1;

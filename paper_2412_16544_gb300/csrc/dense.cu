@@ -744,6 +744,40 @@ cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// out[c][r] = in[r][c] for a row-major [rows][cols] matrix: 32 x 32 tiles through shared memory so
+// that both the reads and the writes are coalesced (the padding column avoids bank conflicts).
+template <typename T>
+__global__ void transpose2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t rows, int64_t cols) {
+  __shared__ T tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = r0 + j, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t c = c0 + j, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][j];
+  }
+}
+
+cudaError_t launch_transpose2d(const void* in, void* out, int64_t rows, int64_t cols, int elem_bytes,
+                               cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int64_t gx = (cols + 31) / 32, gy = (rows + 31) / 32;
+  if (gy > 65535 || gx > 2147483647LL || (elem_bytes != 4 && elem_bytes != 8)) return cudaErrorInvalidValue;
+  ProfScope prof(K_COPY, s);
+  const dim3 grid((unsigned)gx, (unsigned)gy), block(32, 8);
+  if (elem_bytes == 4)
+    transpose2d_kernel<float><<<grid, block, 0, s>>>(static_cast<const float*>(in), static_cast<float*>(out), rows,
+                                                     cols);
+  else
+    transpose2d_kernel<double><<<grid, block, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out),
+                                                      rows, cols);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_cols_invsqrt(double* W, int64_t rows, int64_t cols, const double* lam, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   ProfScope prof(K_COPY, s);

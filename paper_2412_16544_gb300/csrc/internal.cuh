@@ -30,8 +30,9 @@ enum KernelClass {
   K_TTM_F32 = 11,
   K_HOUSE = 12,
   K_MLP = 13,
-  K_OTHER = 14,
-  K_NUM_CLASSES = 15
+  K_PREP = 14,
+  K_OTHER = 15,
+  K_NUM_CLASSES = 16
 };
 const char* kernel_class_name(int cls);
 
@@ -149,6 +150,23 @@ cudaError_t launch_cast(const Tin* in, Tout* out, int64_t n, cudaStream_t s);
 
 // W (rows x cols, row-major) <- W * diag(1/sqrt(max(lam, tiny)))
 cudaError_t launch_scale_cols_invsqrt(double* W, int64_t rows, int64_t cols, const double* lam, cudaStream_t s);
+// Data preparation (prep.cu). Per group g of `size` consecutive elements: params[2g] = shift,
+// params[2g + 1] = scale (device), kind 1 max-abs, 2 unit vector, 3 z-score; then y <- (y - shift) / scale.
+cudaError_t launch_normalize(void* Y, int dtype, int64_t groups, int64_t size, int kind, double* params,
+                             cudaStream_t s);
+// y <- y * scale + shift per group.
+cudaError_t launch_denormalize(void* Y, int dtype, int64_t groups, int64_t size, const double* params,
+                               cudaStream_t s);
+// out item n = permutation of item n of Y: out[n][i_{perm[0]}]..[i_{perm[d-1]}] = Y[n][i_0]..[i_{d-1}].
+cudaError_t launch_permute_items(const void* Y, int dtype, int64_t N, int d, const int64_t* dims, const int* perm,
+                                 void* out, cudaStream_t s);
+// err2[n] += ||X_n - Xh_n||^2, nrm2[n] += ||X_n||^2 over items of `item` elements (Xh FP64).
+cudaError_t launch_item_errors(const void* X, int dtype, const double* Xh, int64_t N, int64_t item, double* err2,
+                               double* nrm2, cudaStream_t s);
+
+// out = in^T for a row-major [rows][cols] matrix of 4- or 8-byte elements (rows <= 2,097,120).
+cudaError_t launch_transpose2d(const void* in, void* out, int64_t rows, int64_t cols, int elem_bytes,
+                               cudaStream_t s);
 
 // X[e] <- uniform in [-1, 1) from a counter-based hash of (seed, e); deterministic
 cudaError_t launch_fill_uniform(double* X, int64_t n, uint64_t seed, cudaStream_t s);

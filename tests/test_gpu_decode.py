@@ -107,28 +107,35 @@ def test_reconstruct_is_decode_of_the_root(B, precision):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_relative_test_error_matches_oracle(B, precision):
     # the spectral stream at 32^3: three increments accumulated, then items of later snapshots that the
-    # cores never saw
+    # cores never saw; the RTE is the mean of the per-item relative errors (eq. generalization_performance)
     Y = S.spectral_field(7, 0, 24, n=32)
     eps = 1e-2
     tree, st = stream_state(B, Y, 8, eps, precision)
     ost = oracle_copy(B, st, Y.shape[1:])
     X = S.spectral_field(7, 40, 6, n=32)
-    got = B.relative_test_error(st, to_dev(X))
-    want = O.relative_test_error(ost, X)
+    got, gerr = B.relative_test_error(st, to_dev(X), per_item=True)
+    want, werr = O.relative_test_error(ost, X, per_item=True)
+    assert np.abs(gerr - werr).max() <= TOL[precision] * 10 + 1e-14
     assert abs(got - want) <= TOL[precision] * 10 + 1e-14
     assert got > 0.0
+    got_h = B.relative_test_error(st, X)                       # host items: the same numbers
+    assert abs(got_h - got) <= 1e-15 + TOL[precision] * 1e-3
     # encoded latents agree element by element with the oracle's projection on the same cores
     Zg = B.ht_encode(st, to_dev(X))
     Zo = O.project(ost, X)
     assert rel(Zg, Zo) <= TOL[precision]
-    # the last stored increment: the projection is the best in the frames' span, so its error is at
-    # most the stored approximation's, which meets the per-increment bound
+    # the last stored increment: the projection is the best in the frames' span, so its aggregate error
+    # is at most the stored approximation's, which meets the per-increment bound
     last = Y[16:24]
-    assert B.relative_test_error(st, to_dev(last)) <= eps * (1 + 1e-4)
-    # items of the represented subspace come back unchanged
+    _, e = B.relative_test_error(st, to_dev(last), per_item=True)
+    nrm = np.linalg.norm(last.reshape(8, -1).astype(np.float64), axis=1)
+    assert np.sqrt(np.sum((e * nrm) ** 2)) <= eps * np.linalg.norm(nrm) * (1 + 1e-4)
+    # items of the represented subspace come back unchanged; an all-zero item counts 0
     r = B.bht_get_ranks(st)
     Xs = O.decode(ost, np.random.default_rng(8).normal(size=(3, r[1], r[2])))
     assert B.relative_test_error(st, to_dev(Xs)) <= TOL[precision] * 10
+    Xz = np.concatenate([X[:2], np.zeros_like(X[:1])])
+    assert abs(B.relative_test_error(st, to_dev(Xz)) - np.mean(gerr[:2]) * 2 / 3) <= TOL[precision] * 10
     B.bht_state_destroy(st)
     B.bht_tree_destroy(tree)
 

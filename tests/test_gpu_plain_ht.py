@@ -1,0 +1,104 @@
+"""Plain HT baseline (batch as the last leaf, leaves-to-root of Sec. 2.3.1) on the GPU against the oracle.
+
+Parity as for BHT-l2r: ranks equal away from ties of the tail rule, reconstructions within 1e-10 of
+||Y|| (FP64 path) when ranks agree, the error bound ||Y - Y~|| <= eps ||Y||, and the root's singular
+values equal to the oracle's diagonal root (the GPU truncates the two layer-1 nodes from the Gram
+matrices of C_1 and C_1^T, so its root is that diagonal up to rotations inside equal singular values).
+"""
+import numpy as np
+import pytest
+
+import bht_synth as S
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_16544_gb300 as B
+    return B
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.linalg.norm(b))
+
+
+def gpu_items(B, st):
+    """[N, n_1..n_d] from the GPU's plain HT state (reconstructed with the batch last)."""
+    out = B.ht_reconstruct(st, 0, 1, dtype="float64").cpu().numpy()[0]
+    return np.moveaxis(out, -1, 0)
+
+
+@pytest.mark.parametrize("dims,N,eps", [
+    ((7, 9), 5, 0.05),
+    ((5, 6, 7), 3, 0.1),
+    ((16, 16, 16), 8, 1e-3),
+    ((13, 67, 11), 4, 1e-2),
+    ((4, 5, 3, 6), 6, 0.05),
+    ((3, 4, 5, 3, 4), 9, 0.02),
+])
+def test_plain_ht_matches_oracle(B, dims, N, eps):
+    rng = np.random.default_rng(sum(dims) + N)
+    Y = np.cumsum(rng.normal(size=(N,) + dims), axis=1) + 0.1 * rng.normal(size=(N,) + dims)
+    st = B.ht_l2r(torch.from_numpy(Y).cuda(), eps, precision="fp64")
+    ost = O.ht_l2r(Y, eps)
+    assert B.bht_get_dims(st) == list(dims) + [N]
+    ranks = B.bht_get_ranks(st)
+    assert ranks[0] == 1
+    Yg = gpu_items(B, st)
+    assert np.linalg.norm(Y - Yg) <= eps * np.linalg.norm(Y) * (1 + 1e-9)
+    if ranks[1:] == ost.ranks()[1:]:
+        assert rel(Yg, O.ht_items(ost)) <= 1e-10 * np.linalg.norm(Y) / np.linalg.norm(O.ht_items(ost)) + 1e-10
+        root = B.bht_get_root(st, 0, 1)[0]
+        sv = np.linalg.svd(root, compute_uv=False)
+        assert np.allclose(sv, np.diag(ost.root[:, :, 0]), rtol=1e-9, atol=1e-12 * np.linalg.norm(Y))
+    else:
+        # ranks may differ only at a tie of the tail rule; the bound still holds (checked above)
+        assert sum(abs(a - b) for a, b in zip(ranks[1:], ost.ranks()[1:])) <= 2
+    B.bht_state_destroy(st)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plain_ht_spectral_increment_full_size(B, precision):
+    """The spectral field's first increment (32 snapshots of 64^3) as one 4-mode tensor: against the
+    oracle's ranks and reconstruction, and against BHT-l2r of the same batch (compression ratio)."""
+    eps = 1e-2
+    Y = S.spectral_field(0, 0, 32, n=64)
+    Yd = torch.from_numpy(Y).cuda()
+    st = B.ht_l2r(Yd, eps, precision=precision)
+    Yg = gpu_items(B, st)
+    nY = np.linalg.norm(Y.astype(np.float64))
+    assert np.linalg.norm(Y - Yg) <= eps * nY * (1 + (1e-9 if precision == "fp64" else 1e-4))
+    ost = O.ht_l2r(Y, eps)
+    ranks = B.bht_get_ranks(st)
+    diff = [abs(a - b) for a, b in zip(ranks[1:], ost.ranks()[1:])]
+    assert max(diff) <= (0 if precision == "fp64" else 2)
+    if precision == "fp64":
+        assert rel(Yg, O.ht_items(ost)) <= 1e-9
+    numel = Y.size
+    cr_ht = numel / B.bht_num_elements(st)
+    cr_ht_oracle = numel / ost.num_elements()
+    assert abs(cr_ht - cr_ht_oracle) <= 0.05 * cr_ht_oracle
+    tree = B.bht_tree_create_balanced(Y.shape[1:])
+    sb = B.bht_l2r(tree, Yd, eps, precision=precision)
+    cr_bht = numel / B.bht_num_elements(sb)
+    print(f"CR HT {cr_ht:.1f} BHT {cr_bht:.1f}")
+    B.bht_state_destroy(sb)
+    B.bht_tree_destroy(tree)
+    B.bht_state_destroy(st)
+
+
+def test_plain_ht_rejects_incremental_calls(B):
+    Y = torch.from_numpy(S.spectral_field(1, 0, 4, n=16)).cuda()
+    st = B.ht_l2r(Y, 1e-2)
+    with pytest.raises(B.BHTError):
+        B.htrise_update(st, Y, 1e-2)
+    with pytest.raises(B.BHTError):
+        B.ht_encode(st, torch.zeros((1, 16, 16, 16, 4), device="cuda"))
+    with pytest.raises(B.BHTError):
+        B.ht_l2r(Y[:0], 1e-2)
+    B.bht_state_destroy(st)

@@ -508,7 +508,97 @@ def test_relative_test_error_closed_forms():
     # k of N n degrees of freedom; 4000 items put the relative spread of the estimate near 1e-3)
     rte = O.relative_test_error(st, rng.normal(size=(4000,) + st.tree.dims))
     assert abs(rte ** 2 - (1 - k / n)) < 0.02 * (1 - k / n)
-    # the accumulated batch itself: the projection onto the frames is the best in their span, so it is
-    # no worse than the stored approximation, which meets the bound of Corollary bht_leaves_to_root
-    assert O.relative_test_error(st, Y) <= 0.25 * (1 + 1e-12)
-    assert abs(O.relative_test_error(st, Y) - rel(O.reconstruct(st), Y)) < 1e-12
+    # the accumulated batch itself: BHT-l2r's root is the projection of the batch, so each item's error is
+    # that of its stored approximation; the average of eq. generalization_performance, item by item
+    rec = O.reconstruct(st)
+    want = np.mean([np.linalg.norm(rec[i] - Y[i]) / np.linalg.norm(Y[i]) for i in range(Y.shape[0])])
+    got, errs = O.relative_test_error(st, Y, per_item=True)
+    assert abs(got - want) < 1e-12
+    # the aggregate error meets the bound of Corollary bht_leaves_to_root; individual items may not
+    assert np.sqrt(np.sum((errs * np.linalg.norm(Y.reshape(12, -1), axis=1)) ** 2)) <= 0.25 * np.linalg.norm(Y) * (1 + 1e-12)
+    # an all-zero item counts 0 and leaves the others' average unchanged
+    Z = np.concatenate([Y[:3], np.zeros_like(Y[:1])])
+    assert abs(O.relative_test_error(st, Z) - np.mean(errs[:3]) * 3 / 4) < 1e-12
+
+
+def test_reduction_ratio_and_normalisations():
+    st, _ = _small_state(36, dims=(4, 5, 6), eps=0.2, N=5)
+    r = st.ranks()
+    assert O.reduction_ratio(st) == 120 / (r[1] * r[2])
+    rng = np.random.default_rng(37)
+    Y = rng.normal(size=(6, 2, 5, 7)) * rng.uniform(0.1, 10, size=(6, 2, 1, 1)) + 3.0
+    for kind in ("maxabs", "unitvec", "zscore", "none"):
+        Yn, P = O.normalize(Y, kind, groups=12)                 # per item and physical quantity
+        G = Yn.reshape(12, -1)
+        if kind == "maxabs":
+            assert np.allclose(np.abs(G).max(axis=1), 1.0, atol=1e-15)
+        elif kind == "unitvec":
+            assert np.allclose(np.linalg.norm(G, axis=1), 1.0, atol=1e-14)
+        elif kind == "zscore":
+            assert np.allclose(G.mean(axis=1), 0.0, atol=1e-14) and np.allclose(G.std(axis=1), 1.0, atol=1e-14)
+        else:
+            assert np.array_equal(Yn, Y)
+        assert np.allclose((G * P[:, 1:2] + P[:, 0:1]).reshape(Y.shape), Y, rtol=0, atol=1e-13)
+    Yc = np.ones((2, 3, 4))
+    Yn, P = O.normalize(Yc, "zscore")                            # constant item: scale falls back to 1
+    assert np.array_equal(P[:, 1], [1.0, 1.0]) and np.array_equal(Yn, np.zeros_like(Yc))
+
+
+# ---------------------------------------------------------------------------
+# Plain HT baseline: the batch as the last leaf (Fig. htucker_as_node), leaves-to-root of Sec. 2.3.1
+# ---------------------------------------------------------------------------
+
+def test_plain_ht_two_mode_items_are_the_truncated_svd_of_the_matricisation():
+    # items of 3 x 4: tree over (3, 4, N) = {1,2},{N}; {1},{2}. Items drawn from a 5-dimensional space
+    # plus 1e-4 noise keep both leaves at full rank, so the layer-1 SVD acts on (n_1 n_2) x N through an
+    # orthogonal change of basis: the result is the Eckart-Young truncation of that matrix (LAPACK)
+    rng = np.random.default_rng(41)
+    N = 50
+    A = rng.normal(size=(12, 5)) @ rng.normal(size=(5, N))
+    A = A + 1e-4 * rng.normal(size=A.shape)
+    Y = A.T.reshape(N, 3, 4)
+    st = O.ht_l2r(Y, 1e-2)
+    r = st.ranks()
+    t = st.tree
+    assert [r[nid] for nid in t.layers[2]] == [3, 4]
+    assert r[t.layers[1][0]] == r[t.layers[1][1]] == 5
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    best = (U[:, :5] * s[:5]) @ Vt[:5]
+    assert rel(O.ht_items(st).reshape(N, 12).T, best) < 1e-12
+    assert np.allclose(np.diag(st.root[:, :, 0]), s[:5], rtol=1e-12, atol=0)
+
+
+def test_plain_ht_recovers_known_ranks():
+    # a tensor built index by index from a chosen HT over (4, 5, 6, N=7): {1,2},{3,N}; leaf ranks 2,3,2,3
+    rng = np.random.default_rng(42)
+    U1, U2, U3, U4 = rand_orth(rng, 4, 2), rand_orth(rng, 5, 3), rand_orth(rng, 6, 2), rand_orth(rng, 7, 3)
+    B12 = rand_orth(rng, 6, 2).reshape(2, 3, 2)
+    B34 = rand_orth(rng, 6, 2).reshape(2, 3, 2)
+    S0 = np.diag([3.0, 0.5])
+    T = np.einsum("ai,bj,ijk,kl,cm,dn,mnl->abcd", U1, U2, B12, S0, U3, U4, B34)
+    Y = np.moveaxis(T, -1, 0)
+    st = O.ht_l2r(Y, 1e-10)
+    t = st.tree
+    r = st.ranks()
+    assert [r[nid] for nid in t.layers[1]] == [2, 2]
+    assert [r[t.leaf_of_mode[m]] for m in range(4)] == [2, 3, 2, 3]
+    assert rel(O.ht_items(st), Y) < 1e-12
+    assert np.allclose(np.diag(st.root[:, :, 0]), [3.0, 0.5], rtol=1e-12)
+
+
+@pytest.mark.parametrize("eps", [0.3, 0.1, 0.03])
+def test_plain_ht_error_bound_and_tolerance(monkeypatch, eps):
+    rng = np.random.default_rng(43)
+    Y = np.cumsum(np.cumsum(rng.normal(size=(9, 5, 6, 7, 4)), axis=2), axis=3)
+    seen = []
+    real = OB.truncated_left_svd
+    monkeypatch.setattr(OB, "truncated_left_svd", lambda M, e, rmin=1: (seen.append(e), real(M, e, rmin))[1])
+    st = O.ht_l2r(Y, eps)
+    # d = 4 item modes plus the batch: 2 (d + 1) - 3 = 7 truncations share the budget
+    assert all(abs(e - eps * np.linalg.norm(Y) / np.sqrt(7)) < 1e-12 * np.linalg.norm(Y) for e in seen)
+    assert len(seen) == 2 * 5 - 2 - 2          # every non-root node but the two of the last SVD
+    assert np.linalg.norm(Y - O.ht_items(st)) <= eps * np.linalg.norm(Y) * (1 + 1e-12)
+    # nested orthonormal frames (orthonormal leaves and reshaped transfer cores)
+    for nd in st.tree.non_root():
+        Bm = st.basis(nd.id)
+        assert np.abs(Bm.T @ Bm - np.eye(Bm.shape[1])).max() < 1e-12
