@@ -1249,6 +1249,9 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
       }
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
+      for (int id : ids)
+        if (C.dims[C.axis_of(id)] > 4096)
+          fail(BHT_ECAPACITY, "a node's unfolding has more than 4096 rows (the eigensolver's limit)");
       // HOSVD of the layer: every node from the same intermediate, the nodes side by side
       run_nodes((int)ids.size(), s, [&](int k, cudaStream_t sk) {
         const int id = ids[k];
@@ -1423,6 +1426,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         alpha[k] = C.dims[ax];
         rold[k] = rank[ids[k]];
         qc[k] = alpha[k] - rold[k];  // <= 0: U spans R^alpha and the residual vanishes
+        if (qc[k] > 4096) fail(BHT_ECAPACITY, "a node's residual space exceeds 4096 dimensions (the eigensolver's limit)");
         stat[k] = DBuf(sizeof(int), s);
         ck(cudaMemsetAsync(stat[k].p, 0, sizeof(int), s), "memset status");
         if (qc[k] <= 0) continue;

@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
                                                               double* __restrict__ pbuf, Barrier* bar,
                                                               int* status) {
   extern __shared__ double sm[];
+  unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
   double* v = sm;       // n
   double* w = sm + n;   // n
   __shared__ double red[33];
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
     }
     __syncthreads();
     if (tk == 0.0) {  // column already reduced: no reflection, nothing to update
-      if (!grid_barrier(bar, status)) return;
+      if (!grid_barrier_count(bar, epoch, status)) return;
       continue;
     }
     // p = tau A22 v, one warp per row
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
       dot = warp_sum(dot);
       if (lane == 0) pbuf[i] = tk * dot;
     }
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier_count(bar, epoch, status)) return;
     // w = p - (tau/2)(p.v) v
     double pv = 0.0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double* __restrict
       const double vi = v[i], wi = w[i];
       for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
     }
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier_count(bar, epoch, status)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (n >= 2) {
@@ -136,8 +137,10 @@ __device__ double householder(const double* x, int m, double* v, double* red, do
   double t = 0.0, beta = alpha, scale = 0.0;
   if (xn2 > 0.0) {
     beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-    t = (beta - alpha) / beta;
-    scale = 1.0 / (alpha - beta);
+    // t = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one reciprocal of their product
+    const double am = alpha - beta, inv = 1.0 / (beta * am);
+    t = -am * am * inv;
+    scale = beta * inv;
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) v[j] = (j == 0) ? 1.0 : (t != 0.0 ? x[j] * scale : 0.0);
   *beta_out = beta;
@@ -149,7 +152,7 @@ __device__ double householder(const double* x, int m, double* v, double* red, do
 // Householder tridiagonalisation with the matrix resident in shared memory.
 // Row gi belongs to CTA gi % gridDim.x (slot gi / gridDim.x) for the whole
 // reduction, so the rank-2 updates and matrix-vector products never leave the
-// SM. One grid barrier per column: after it every CTA holds p_t = tau A22 v_t
+// SM. One grid barrier (a growing counter) per column: after it every CTA holds p_t = tau A22 v_t
 // and row t+1 as it was before update t (published by its owner), and itself
 // forms w_t, the updated column t+1 and the next reflector v_{t+1}; then one
 // pass over its rows applies update t and accumulates p_{t+1} at once.
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
   __shared__ double red[33];
   const int nb = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
   for (int l = 0; l < rpb; ++l) {
     const int gi = b + l * nb;
     if (gi >= n) break;
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
     if (gi == 1)
       for (int c = 1 + lane; c < n; c += 32) pub[n + c] = r[c];
   }
-  if (!grid_barrier(bar, status)) return;
+  if (!grid_barrier_count(bar, epoch, status)) return;
 
   for (int t = 0; t + 2 < n; ++t) {
     const int m = n - t - 1;  // length of v_t; index q <-> column t + 1 + q
@@ -205,19 +209,22 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
     double* vn = vb[(t + 1) & 1];
     const double* p = pbuf + (size_t)(t & 1) * n;
     const double* R = pub + (size_t)((t + 1) & 1) * n;  // row t + 1 before update t
-    // w_t = p - (tau/2)(p.v) v
+    // w_t = p - (tau/2)(p.v) v; row t + 1 is fetched in the same pass (both come from L2 after the
+    // barrier, so their latencies overlap)
     double pv = 0.0;
     for (int q = threadIdx.x; q < m; q += blockDim.x) {
       const double pq = p[q];
       w[q] = pq;
+      if (q >= 1) x[q - 1] = R[t + 1 + q];
       pv = fma(pq, v[q], pv);
     }
     const double Kc = 0.5 * tc * block_sum(pv, red);
     for (int q = threadIdx.x; q < m; q += blockDim.x) w[q] -= Kc * v[q];
     __syncthreads();
-    // column t + 1 after update t: x[c - t - 2] for columns c >= t + 2
+    // column t + 1 after update t: x[c - t - 2] for columns c >= t + 2 (each thread the entries it
+    // fetched above)
     const int m1 = m - 1;
-    for (int q = 1 + threadIdx.x; q < m; q += blockDim.x) x[q - 1] = R[t + 1 + q] - (w[q] + w[0] * v[q]);
+    for (int q = 1 + threadIdx.x; q < m; q += blockDim.x) x[q - 1] -= w[q] + w[0] * v[q];
     __syncthreads();
     const double dnext = R[t + 1] - 2.0 * w[0];
     double tn = 0.0;
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
       if (gi == n - 1 && m1 < 2 && lane == 0) d[n - 1] = r[n - 1];
     }
     tc = tn;
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier_count(bar, epoch, status)) return;
   }
   if (b == 0 && threadIdx.x == 0) {
     e[n - 1] = 0.0;

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   double* vloc = rows + (size_t)rpb * k;  // rpb: v_j on the own rows
   __shared__ double red[33];
   const int nb = gridDim.x, b = blockIdx.x;
+  unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
   for (int l = 0; l < rpb; ++l) {
     const int i = b + l * nb;
     for (int q = threadIdx.x; q < k; q += blockDim.x) rows[(size_t)l * k + q] = (i < c) ? Z[(size_t)i * k + q] : 0.0;
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
     }
     s = block_sum(s, red);
     if (threadIdx.x == 0) part[par * nb + b] = s;
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier_count(bar, epoch, status)) return;
     // B: the reflector, identical in every CTA (same partials, same order)
     double t = 0.0;
     for (int q = threadIdx.x; q < nb; q += blockDim.x) t += part[par * nb + q];
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
         if (d != 0.0) atomicAdd(&dsum[par * k + q], d);
       }
     }
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier_count(bar, epoch, status)) return;
     // C: Z(:, q) -= tau v (v^T Z(:, q)) on the own rows
     if (tj != 0.0) {
       for (int e = threadIdx.x; e < rpb * (k - j - 1); e += blockDim.x) {

@@ -7,7 +7,7 @@ namespace bht {
 
 struct Barrier {
   unsigned int count;
-  unsigned int gen;
+  unsigned int spare;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -16,40 +16,34 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch with a 1 s limit: arrival is a
-// release add on the counter, the last CTA resets it and publishes the next
-// generation with a release store, the others poll the generation with
-// acquire loads. Returns false when the wait gave up (the status word then
-// holds BHT_ETIMEOUT = 6) or another CTA reported a failure. With one CTA it
-// is __syncthreads.
-__device__ __forceinline__ bool grid_barrier(Barrier* bar, int* status) {
+// Grid barrier of a cooperative launch on a counter that only grows (zero at launch): the k-th call
+// of every CTA adds one with a release reduction, which returns nothing, and waits until the counter
+// reaches k * gridDim.x. `epoch` counts the calls (the same in every thread of the CTA). The wait is
+// limited to 1 s: returns false when it gave up (the status word then holds BHT_ETIMEOUT = 6) or
+// another CTA reported a failure. With one CTA it is __syncthreads.
+__device__ __forceinline__ bool grid_barrier_count(Barrier* bar, unsigned int& epoch, int* status) {
   __shared__ int ok;
   __syncthreads();
   if (gridDim.x == 1) return true;
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned int g, arrived;
-    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(g) : "l"(&bar->gen) : "memory");
-    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&bar->count) : "memory");
-    if (arrived == gridDim.x - 1) {
-      asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
-      asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(&bar->gen), "r"(g + 1) : "memory");
-    } else {
-      const uint64_t t0 = global_ns();
-      unsigned int cur;
-      for (uint32_t spin = 0;; ++spin) {
-        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
-        if (cur != g) break;
-        if ((spin & 63) == 63) {
-          if (*(volatile int*)status != 0) {
-            ok = 0;
-            break;
-          }
-          if (global_ns() - t0 > 1000000000ull) {
-            atomicExch(status, 6);
-            ok = 0;
-            break;
-          }
+    const unsigned int target = epoch * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+    const uint64_t t0 = global_ns();
+    unsigned int cur;
+    for (uint32_t spin = 0;; ++spin) {
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if ((spin & 63) == 63) {
+        if (*(volatile int*)status != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > 1000000000ull) {
+          atomicExch(status, 6);
+          ok = 0;
+          break;
         }
       }
     }
@@ -72,8 +66,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   if (l == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
-    double t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
-    t = warp_sum(t);
+    // second level over the warps' partial sums only: log2 of the warp count rounded up, not 5 steps
+    const int nwarps = (int)(blockDim.x >> 5);
+    double t = (l < nwarps) ? red[l] : 0.0;
+    int span = 1;
+    while (span < nwarps) span <<= 1;
+    for (int o = span >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (l == 0) red[32] = t;
   }
   __syncthreads();

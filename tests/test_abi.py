@@ -83,3 +83,13 @@ def test_eps_and_size_checks_before_any_device_work(bht):
     assert L.bht_l2r(t, buf, 0, 0, 0.1, None, None, ctypes.byref(out)) == 1       # N = 0
     assert L.bht_l2r(t, buf, 7, 1, 0.1, None, None, ctypes.byref(out)) == 1       # dtype
     bht.bht_tree_destroy(t)
+
+
+def test_sweep_tensorisations_keep_the_snapshot_size():
+    import numpy as np
+    from paper_2412_16544_gb300 import sweeps as W
+    for g in (4, 16, 64):
+        for name, shape in W.reshapes(g).items():
+            assert int(np.prod(shape)) == g ** 3 and len(shape) <= 16, name
+    for name, perm in W.AXIS_ORDERS.items():
+        assert sorted(perm) == list(range(6)), name
