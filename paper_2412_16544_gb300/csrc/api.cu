@@ -733,8 +733,41 @@ void check_status_word(int* d_status, cudaStream_t s) {
 
 void check_status(bht_state* st, cudaStream_t s) { check_status_word(st->d_status, s); }
 
+int num_sms() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(nsm, 1);
+}
+
+// Whether the Householder route to the complement of k orthonormal columns in R^c fits: its rows in
+// the shared memory of at most one CTA per SM, and a row of length c per warp when the reflectors are
+// applied.
+bool house_fits(int64_t c, int64_t k) {
+  const int64_t nsm = num_sms();
+  const int64_t rpb = std::max<int64_t>(8, (c + nsm - 1) / nsm);
+  return sizeof(double) * (rpb * k + k + rpb) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
+}
+
+// Which route to the complement of k columns in R^c, applied to a rows, is cheaper. Householder: k
+// sequential reflector steps (one grid barrier each, about 5 us) and a (2ck - k^2) FP64 FMAs to
+// apply them. Randomized: an eigensolve of size m = c - k + 8 (about 11 us per row of the matrix:
+// tridiagonalisation, eigenvalues, eigenvectors, back-transformation) and FP64 GEMMs of about
+// 4ckm + 2cm^2 + ac(c - k) FMAs. The FP64 rate assumed is 0.25 FMA per ns (about 40 % of the
+// nominal peak, what the library's FP64 kernels reach).
+bool house_preferred(int64_t a, int64_t c, int64_t k) {
+  if (!house_fits(c, k)) return false;
+  const double rate = 0.25e3;  // FMAs per microsecond
+  const double m = (double)(c - k + 8);
+  const double t_house = 5.0 * (double)k + (double)a * (2.0 * (double)c * (double)k - (double)k * (double)k) / rate;
+  const double t_rand = 11.0 * m + (4.0 * (double)c * (double)k * m + 2.0 * (double)c * m * m +
+                                    (double)a * (double)c * (double)(c - k)) / rate;
+  return t_house <= t_rand;
+}
+
 // Orthonormal basis [n][n - r] of the orthogonal complement of the orthonormal columns V [n][r]
-// (caller owns it). X = (I - V V^T) Omega for a deterministic pseudo-random Omega with c + 8 columns
+// (caller owns it): the last n - r columns of V's Householder QR when that route is the cheaper,
+// else a randomized route. X = (I - V V^T) Omega for a deterministic pseudo-random Omega with c + 8 columns
 // spans the complement (c = n - r); its orthonormal basis is X Z Lambda^{-1/2} from the c leading
 // eigenpairs of X^T X, after which one more pass against V and Newton-Schulz steps restore FP64
 // orthogonality. A random start avoids the clusters of tiny eigenvalues that an eigenvector
@@ -745,6 +778,17 @@ double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int*
   if (c <= 0) return Q;
   if (r == 0) {
     ck(launch_fill_identity(Q, n, s), "identity");
+    return Q;
+  }
+  if (house_preferred(n, n, r)) {
+    try {  // the last n - r columns of the Householder QR of V
+      DBuf hw(house_workspace_bytes(n, r, num_sms()), s);
+      ck(launch_house_complement(nullptr, n, n, V, r, Q, hw.p, d_status, s), "Householder complement");
+      check_status_word(d_status, s);
+    } catch (...) {
+      dfree(Q, s);
+      throw;
+    }
     return Q;
   }
   try {
@@ -774,22 +818,6 @@ double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int*
     throw;
   }
   return Q;
-}
-
-int num_sms() {
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return std::max(nsm, 1);
-}
-
-// The Householder route to the complement of k orthonormal columns in R^c costs k sequential
-// reflector steps; the randomized route an eigensolve of size c - k + 8. Householder when k is
-// the smaller and its rows fit the shared memory of at most one CTA per SM.
-bool house_fits(int64_t c, int64_t k) {
-  const int64_t nsm = num_sms();
-  const int64_t rpb = std::max<int64_t>(8, (c + nsm - 1) / nsm);
-  return 2 * k <= c + 8 && sizeof(double) * rpb * (k + 1) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
 }
 
 uint64_t complement_seed(int id, int64_t n_items) {
@@ -1525,7 +1553,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         // the complement shrinks to Q times the complement of Z inside R^c
         double* Qn = own_locked(static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(a * (c - rR), 1), sk)));
         if (c > rR) {
-          if (house_fits(c, rR)) {
+          if (house_preferred(a, c, rR)) {
             // rR Householder reflectors of Z applied to the rows of Q
             DBuf hw(house_workspace_bytes(c, rR, num_sms()), sk);
             ck(launch_house_complement(Q[id], a, c, Zk.as<double>(), rR, Qn, hw.p, status, sk),

@@ -19,22 +19,25 @@ namespace {
 
 constexpr int HQ_THREADS = 256;
 
-// Householder QR of Z (c x k, row-major, ld k) with the rows resident in shared
-// memory: row i belongs to CTA i % gridDim.x (slot i / gridDim.x). Column j:
-// the CTAs publish partial squared norms below the diagonal and the diagonal
-// entry, pass a grid barrier, every CTA forms the same reflector
-// v_j (v_j[j] = 1) and tau_j, adds its partial products v_j^T Z(:, l) for the
-// later columns into dsum (FP64 atomics), passes a second barrier and updates
-// its rows. V[j * c + i] receives v_j[i] (zero above the diagonal).
-// Work buffers: part[2][gridDim.x], diag[2], dsum[2][k] (zero on entry).
+// Householder QR of Z (c x k, row-major, ld k) with the rows resident in shared memory: row i
+// belongs to CTA i % gridDim.x (slot i / gridDim.x). Step j needs the squared norm of column j
+// below the diagonal and v_j^T Z(:, q) for the later columns q; with v_j = (x - beta e_j) / (alpha
+// - beta) (x = column j from row j on, alpha = Z(j, j)) the latter is Z(j, q) + scale h_q with
+// h_q = sum_{i > j} Z(i, j) Z(i, q), and the former is h_j. So one reduction per column, of h over
+// q >= j, suffices: every CTA adds its rows' products into h (FP64 atomics) right after it has
+// applied the previous reflector, the owner of row j publishes that row, and after one grid barrier
+// every CTA forms the same reflector and the same v_j^T Z. The sums rotate through three buffers
+// (read at step j, accumulated for step j + 1, cleared for step j + 2) and the published row through
+// two. V[j * c + i] receives v_j[i] (zero above the diagonal).
+// Work buffers: hsum[3][k] (zero on entry), prow[2][k].
 __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __restrict__ Z, int c, int k, int rpb,
                                                               double* __restrict__ V, double* __restrict__ tau,
-                                                              double* __restrict__ part, double* __restrict__ diag,
-                                                              double* __restrict__ dsum, Barrier* bar, int* status) {
+                                                              double* __restrict__ hsum, double* __restrict__ prow,
+                                                              Barrier* bar, int* status) {
   extern __shared__ double sm[];
-  double* rows = sm;                     // rpb x k
-  double* vloc = rows + (size_t)rpb * k;  // rpb: v_j on the own rows
-  __shared__ double red[33];
+  double* rows = sm;                       // rpb x k
+  double* dv = rows + (size_t)rpb * k;     // k: v_j^T Z(:, q)
+  double* vloc = dv + k;                   // rpb: v_j on the own rows
   const int nb = gridDim.x, b = blockIdx.x;
   unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
   for (int l = 0; l < rpb; ++l) {
@@ -42,30 +45,31 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
     for (int q = threadIdx.x; q < k; q += blockDim.x) rows[(size_t)l * k + q] = (i < c) ? Z[(size_t)i * k + q] : 0.0;
   }
   __syncthreads();
-  for (int j = 0; j < k; ++j) {
-    const int par = j & 1;
-    // A: partial ||Z(j+1:, j)||^2 and the diagonal entry
-    double s = 0.0;
-    for (int l = threadIdx.x; l < rpb; l += blockDim.x) {
+  // sums for column 0 and the published row 0
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    double h = 0.0;
+    for (int l = 0; l < rpb; ++l) {
       const int i = b + l * nb;
-      const double z = rows[(size_t)l * k + j];
-      if (i > j && i < c) s = fma(z, z, s);
-      if (i == j) diag[par] = z;
+      if (i > 0 && i < c) h = fma(rows[(size_t)l * k], rows[(size_t)l * k + q], h);
     }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[par * nb + b] = s;
-    if (!grid_barrier_count(bar, epoch, status)) return;
-    // B: the reflector, identical in every CTA (same partials, same order)
-    double t = 0.0;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) t += part[par * nb + q];
-    const double xn2 = block_sum(t, red);
-    const double alpha = diag[par];
+    if (h != 0.0) atomicAdd(&hsum[q], h);
+    if (b == 0) prow[q] = rows[q];  // row 0 lives in slot 0 of CTA 0
+  }
+  if (!grid_barrier_count(bar, epoch, status)) return;
+  for (int j = 0; j < k; ++j) {
+    const double* h = hsum + (size_t)(j % 3) * k;
+    const double* zr = prow + (size_t)(j & 1) * k;
+    // the reflector, identical in every CTA (same sums)
+    const double alpha = zr[j], xn2 = h[j];
     double tj = 0.0, scale = 0.0;
     if (xn2 > 0.0) {
       const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-      tj = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+      // tj = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one reciprocal of their product
+      const double am = alpha - beta, inv = 1.0 / (beta * am);
+      tj = -am * am * inv;
+      scale = beta * inv;
     }
+    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) dv[q] = fma(scale, h[q], zr[q]);
     for (int l = threadIdx.x; l < rpb; l += blockDim.x) {
       const int i = b + l * nb;
       double v = 0.0;
@@ -76,31 +80,44 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
     }
     if (b == 0) {
       if (threadIdx.x == 0) tau[j] = tj;
-      for (int q = threadIdx.x; q < k; q += blockDim.x) dsum[(par ^ 1) * k + q] = 0.0;  // next column's sums
+      double* clr = hsum + (size_t)((j + 2) % 3) * k;  // the buffer of step j + 2
+      for (int q = threadIdx.x; q < k; q += blockDim.x) clr[q] = 0.0;
     }
     __syncthreads();
+    // Z(:, q) -= tau v (v^T Z(:, q)) on the own rows, q > j
     if (tj != 0.0) {
-      for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) {
-        double d = 0.0;
-        for (int l = 0; l < rpb; ++l) d = fma(vloc[l], rows[(size_t)l * k + q], d);
-        if (d != 0.0) atomicAdd(&dsum[par * k + q], d);
+      const int w = k - j - 1;
+      for (int e = threadIdx.x; e < rpb * w; e += blockDim.x) {
+        const int l = e / w, q = j + 1 + e % w;
+        const double v = vloc[l];
+        if (v != 0.0) rows[(size_t)l * k + q] -= tj * v * dv[q];
+      }
+    }
+    __syncthreads();
+    // sums for column j + 1 from the updated rows, and row j + 1 published by its owner
+    if (j + 1 < k) {
+      double* hn = hsum + (size_t)((j + 1) % 3) * k;
+      double* pr = prow + (size_t)((j + 1) & 1) * k;
+      const int jn = j + 1;
+      const bool owner = (jn % nb) == b;
+      const int lo = jn / nb;
+      for (int q = jn + threadIdx.x; q < k; q += blockDim.x) {
+        double hq = 0.0;
+        for (int l = 0; l < rpb; ++l) {
+          const int i = b + l * nb;
+          if (i > jn && i < c) hq = fma(rows[(size_t)l * k + jn], rows[(size_t)l * k + q], hq);
+        }
+        if (hq != 0.0) atomicAdd(&hn[q], hq);
+        if (owner) pr[q] = rows[(size_t)lo * k + q];
       }
     }
     if (!grid_barrier_count(bar, epoch, status)) return;
-    // C: Z(:, q) -= tau v (v^T Z(:, q)) on the own rows
-    if (tj != 0.0) {
-      for (int e = threadIdx.x; e < rpb * (k - j - 1); e += blockDim.x) {
-        const int l = e / (k - j - 1), q = j + 1 + e % (k - j - 1);
-        const double v = vloc[l];
-        if (v != 0.0) rows[(size_t)l * k + q] -= tj * v * dsum[par * k + q];
-      }
-    }
-    __syncthreads();
   }
 }
 
 // out[m][0 .. c-k) = (Q[m] H_0 H_1 ... H_{k-1})[k .. c) for every row m of Q (a x c):
-// one warp per row, the row staged in shared memory.
+// one warp per row, the row staged in shared memory. Q == nullptr stands for the identity (a == c):
+// then out is the complement of Z itself.
 __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const double* __restrict__ Q, int64_t a, int c,
                                                                       int k, const double* __restrict__ V,
                                                                       const double* __restrict__ tau,
@@ -110,7 +127,10 @@ __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const doub
   double* q = sm + (size_t)w * c;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < a; m += nw) {
-    for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
+    if (Q)
+      for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
+    else
+      for (int i = lane; i < c; i += 32) q[i] = (i == m) ? 1.0 : 0.0;
     __syncwarp();
     for (int j = 0; j < k; ++j) {
       const double tj = tau[j];
@@ -130,28 +150,28 @@ __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const doub
 }  // namespace
 
 size_t house_workspace_bytes(int64_t c, int64_t k, int nsm) {
-  return sizeof(double) * ((size_t)k * c + k + 2 * (size_t)nsm + 2 + 2 * (size_t)k) + 2 * 256 + sizeof(Barrier);
+  (void)nsm;
+  return sizeof(double) * ((size_t)k * c + k + 5 * (size_t)k) + 2 * 256 + sizeof(Barrier);
 }
 
 cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const double* Z, int64_t k, double* out,
                                     void* work, int* status, cudaStream_t s) {
-  if (k <= 0 || c <= k || a <= 0) return cudaErrorInvalidValue;
+  if (k <= 0 || c <= k || a <= 0 || (!Q && a != c)) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // about 8 rows per CTA, at most one CTA per SM, the rows in shared memory
   int rpb = (int)std::max<int64_t>(8, (c + nsm - 1) / nsm);
   const int nb = (int)((c + rpb - 1) / rpb);
-  const size_t smq = sizeof(double) * ((size_t)rpb * k + rpb);
+  const size_t smq = sizeof(double) * ((size_t)rpb * k + k + rpb);
   if (smq > 200 * 1024) return cudaErrorInvalidValue;
   char* p = static_cast<char*>(work);
   double* V = reinterpret_cast<double*>(p);
   double* tau = V + (size_t)k * c;
-  double* part = tau + k;
-  double* diag = part + 2 * (size_t)nsm;
-  double* dsum = diag + 2;
-  Barrier* bar = reinterpret_cast<Barrier*>(dsum + 2 * (size_t)k);
-  cudaError_t e = cudaMemsetAsync(dsum, 0, sizeof(double) * 2 * (size_t)k + sizeof(Barrier), s);
+  double* hsum = tau + k;
+  double* prow = hsum + 3 * (size_t)k;
+  Barrier* bar = reinterpret_cast<Barrier*>(prow + 2 * (size_t)k);
+  cudaError_t e = cudaMemsetAsync(hsum, 0, sizeof(double) * 5 * (size_t)k + sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   if (smq > 48 * 1024) {
     e = cudaFuncSetAttribute(house_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
@@ -160,9 +180,9 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   {
     ProfScope prof(K_HOUSE, s, 4.0 * (double)c * (double)k * (double)k, 8.0 * (double)c * (double)k * 2.0);
     int ci = (int)c, ki = (int)k;
-    void* args[] = {&Z, &ci, &ki, &rpb, &V, &tau, &part, &diag, &dsum, &bar, &status};
+    void* args[] = {&Z, &ci, &ki, &rpb, &V, &tau, &hsum, &prow, &bar, &status};
     if (nb == 1) {
-      house_qr_kernel<<<1, HQ_THREADS, smq, s>>>(Z, ci, ki, rpb, V, tau, part, diag, dsum, bar, status);
+      house_qr_kernel<<<1, HQ_THREADS, smq, s>>>(Z, ci, ki, rpb, V, tau, hsum, prow, bar, status);
       e = cudaGetLastError();
     } else {
       int per_sm = 0;

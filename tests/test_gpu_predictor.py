@@ -120,10 +120,12 @@ def test_predictor_gain_on_method_generated_streams(B):
     assert np.mean(hist[-40:]) < hist[0]
     res = P.evaluate(net, range(100, 104), inc, items, grid)
     print(res)
-    # the judge: the same ranks, and reconstructions that differ from the plain run's no more than two
-    # plain runs differ from each other (the mixed path's reductions use FP64 atomics)
+    # the judge: the same ranks, and reconstructions that differ from the plain run's only at the mixed
+    # path's rounding level: its reductions combine FP32 partial sums with FP64 atomics whose order
+    # follows the launch order, which the predictor's extra kernels change (two plain runs may or may
+    # not differ); 1e-5 is the mixed path's tolerance elsewhere (split TF32 / FP32 mode products)
     assert res["ranks_equal"]
-    assert res["max_diff_vs_plain"] <= 10 * res["max_diff_plain_repeat"] + 1e-9
+    assert res["max_diff_vs_plain"] <= max(10 * res["max_diff_plain_repeat"], 1e-5)
     assert res["violation_rate_after_fallback"] == 0.0
     assert res["max_rel_err"] <= 1.0 + 1e-4                     # ||Y - Y~|| <= eps ||Y|| per increment
     assert res["skipped"] > 0                                   # residual eigensolves avoided
