@@ -344,8 +344,10 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
     red_hi[threadIdx.x >> 5] = gu;
   }
   __syncthreads();
-  gl = fmin(fmin(red_lo[0], red_lo[1]), fmin(red_lo[2], red_lo[3]));
-  gu = fmax(fmax(red_hi[0], red_hi[1]), fmax(red_hi[2], red_hi[3]));
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {  // 1, 2 or 4 warps
+    gl = fmin(gl, red_lo[w]);
+    gu = fmax(gu, red_hi[w]);
+  }
   const double tnorm = fmax(fmax(fabs(gl), fabs(gu)), DBL_MIN);
   int ex = 0;
   frexp(tnorm, &ex);
@@ -391,20 +393,26 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
 // with the stationary (top-down) and progressive (bottom-up) LDL^T
 // factorisations of T - lambda I, the twist index k minimising
 // |gamma_k| = |D+_k + D-_k - (d_k - lambda)| gives the eigenvector from
-// z_k = 1 and two one-sided recurrences. One thread per eigenvalue; inside a
+// z_k = 1 and two one-sided recurrences. One lane per eigenvalue; inside a
 // cluster (a chain of eigenvalues closer than ctol) the shifts are spread by
 // 10 eps ||T|| per member so the members differ, and cluster_orth_kernel
 // then orthogonalises each cluster.
 // Z[i * r + j] receives component i of eigenvector j of T.
-// Scratch per eigenvalue index: 4 n doubles.
+// Scratch: 4 n r doubles.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double cluster_tol(const double* lam, int n) {
   return 1e-9 * (fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN);
 }
 
-__global__ void invit_kernel(const double* dg, const double* eg, int n, const double* __restrict__ lam, int r,
-                             double* __restrict__ Z, double* __restrict__ scratch) {
+__global__ void __launch_bounds__(64) invit_kernel(const double* dg, const double* eg, int n,
+                                                   const double* __restrict__ lam, int r, double* __restrict__ Z,
+                                                   double* __restrict__ scratch) {
+  // 32 eigenvalues per CTA, lane = eigenvalue; warp 0 runs the forward factorisation and the
+  // recurrence below the twist, warp 1 the backward factorisation and the recurrence above it (the
+  // two halves of each step are independent chains of FP64 divisions and products)
   extern __shared__ double tsm[];
+  __shared__ double bestv[2][32], part[2][32];
+  __shared__ int bestk[2][32];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     tsm[i] = dg[i];
     tsm[n + i] = eg[i];
@@ -412,62 +420,106 @@ __global__ void invit_kernel(const double* dg, const double* eg, int n, const do
   __syncthreads();
   const double* d = tsm;
   const double* e = tsm + n;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= r) return;
+  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const bool act = j < r;
   const double tnorm = fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN;
   const double ctol = cluster_tol(lam, n);
   const double tiny = 1e-3 * DBL_EPSILON * tnorm + DBL_MIN;
-  int lead = j;
-  while (lead > 0 && fabs(lam[lead - 1] - lam[lead]) <= ctol) --lead;
-  double* Dp = scratch + (int64_t)j * 4 * n;
-  double* Lp = Dp + n;
-  double* Dm = Lp + n;
-  double* Um = Dm + n;
-  const double s = lam[j] + (double)(j - lead) * 10.0 * DBL_EPSILON * tnorm;
-  Dp[0] = d[0] - s;
-  for (int i = 0; i + 1 < n; ++i) {
-    if (fabs(Dp[i]) < tiny) Dp[i] = tiny;
-    Lp[i] = e[i] / Dp[i];
-    Dp[i + 1] = (d[i + 1] - s) - Lp[i] * e[i];
-  }
-  Dm[n - 1] = d[n - 1] - s;
-  for (int i = n - 1; i >= 1; --i) {
-    if (fabs(Dm[i]) < tiny) Dm[i] = tiny;
-    Um[i] = e[i - 1] / Dm[i];
-    Dm[i - 1] = (d[i - 1] - s) - Um[i] * e[i - 1];
-  }
-  int k = 0;
-  double best = INFINITY;
-  for (int i = 0; i < n; ++i) {
-    const double g = fabs(Dp[i] + Dm[i] - (d[i] - s));
-    if (g < best) {
-      best = g;
-      k = i;
+  // scratch [4][n][r]: D+, L+, D-, U- with the eigenvalue index innermost (coalesced per step)
+  const int64_t R = r;
+  double* Dp = scratch + j;
+  double* Lp = scratch + (int64_t)n * R + j;
+  double* Dm = scratch + 2 * (int64_t)n * R + j;
+  double* Um = scratch + 3 * (int64_t)n * R + j;
+  double s = 0.0;
+  if (act) {
+    int lead = j;
+    while (lead > 0 && fabs(lam[lead - 1] - lam[lead]) <= ctol) --lead;
+    s = lam[j] + (double)(j - lead) * 10.0 * DBL_EPSILON * tnorm;
+    if (half == 0) {
+      double dp = d[0] - s;
+      for (int i = 0; i + 1 < n; ++i) {
+        if (fabs(dp) < tiny) dp = tiny;
+        const double l = e[i] / dp;
+        Dp[(int64_t)i * R] = dp;
+        Lp[(int64_t)i * R] = l;
+        dp = (d[i + 1] - s) - l * e[i];
+      }
+      Dp[(int64_t)(n - 1) * R] = dp;
+    } else {
+      double dm = d[n - 1] - s;
+      for (int i = n - 1; i >= 1; --i) {
+        if (fabs(dm) < tiny) dm = tiny;
+        const double u = e[i - 1] / dm;
+        Dm[(int64_t)i * R] = dm;
+        Um[(int64_t)i * R] = u;
+        dm = (d[i - 1] - s) - u * e[i - 1];
+      }
+      Dm[0] = dm;
     }
   }
+  __syncthreads();
+  // twist index: the first i of least |D+_i + D-_i - (d_i - s)|, each warp over half of the range
+  const int mid = n / 2;
+  {
+    int k = 0;
+    double best = INFINITY;
+    if (act) {
+      const int lo = half == 0 ? 0 : mid, hi = half == 0 ? mid : n;
+      for (int i = lo; i < hi; ++i) {
+        const double g = fabs(Dp[(int64_t)i * R] + Dm[(int64_t)i * R] - (d[i] - s));
+        if (g < best) {
+          best = g;
+          k = i;
+        }
+      }
+    }
+    bestv[half][lane] = best;
+    bestk[half][lane] = k;
+  }
+  __syncthreads();
+  const int k = (bestv[1][lane] < bestv[0][lane]) ? bestk[1][lane] : bestk[0][lane];
   // z in the output column: z_k = 1, then the two one-sided recurrences
   double* zc = Z + j;
-  zc[(int64_t)k * r] = 1.0;
   double mx = 1.0;
-  for (int i = k - 1; i >= 0; --i) {
-    const double z = -Lp[i] * zc[(int64_t)(i + 1) * r];
-    zc[(int64_t)i * r] = z;
-    mx = fmax(mx, fabs(z));
+  if (act) {
+    if (half == 0) {
+      zc[(int64_t)k * R] = 1.0;
+      double z = 1.0;
+      for (int i = k - 1; i >= 0; --i) {
+        z = -Lp[(int64_t)i * R] * z;
+        zc[(int64_t)i * R] = z;
+        mx = fmax(mx, fabs(z));
+      }
+    } else {
+      double z = 1.0;
+      for (int i = k + 1; i < n; ++i) {
+        z = -Um[(int64_t)i * R] * z;
+        zc[(int64_t)i * R] = z;
+        mx = fmax(mx, fabs(z));
+      }
+    }
   }
-  for (int i = k + 1; i < n; ++i) {
-    const double z = -Um[i] * zc[(int64_t)(i - 1) * r];
-    zc[(int64_t)i * r] = z;
-    mx = fmax(mx, fabs(z));
-  }
+  part[half][lane] = mx;
+  __syncthreads();
+  mx = fmax(part[0][lane], part[1][lane]);
   if (!isfinite(mx)) mx = 1.0;
   const double inv_mx = 1.0 / mx;
+  __syncthreads();
   double nrm = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double z = zc[(int64_t)i * r] * inv_mx;
-    nrm = fma(z, z, nrm);
-  }
+  const int lo = half == 0 ? 0 : mid, hi = half == 0 ? mid : n;
+  if (act)
+    for (int i = lo; i < hi; ++i) {
+      const double z = zc[(int64_t)i * R] * inv_mx;
+      nrm = fma(z, z, nrm);
+    }
+  part[half][lane] = nrm;
+  __syncthreads();
+  nrm = part[0][lane] + part[1][lane];
   const double sc = nrm > 0.0 ? inv_mx / sqrt(nrm) : 0.0;
-  for (int i = 0; i < n; ++i) zc[(int64_t)i * r] *= sc;
+  if (act)
+    for (int i = lo; i < hi; ++i) zc[(int64_t)i * R] *= sc;
 }
 
 // One CTA per potential cluster leader j < r (an index that starts a chain of
@@ -649,12 +701,20 @@ cudaError_t launch_bisect_l(int64_t n, const double* d, const double* e, double*
     cudaError_t e2 = cudaFuncSetAttribute(bisect_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e2 != cudaSuccess) return e2;
   }
-  const int64_t per_block = 128 / L;  // eigenvalues per 128-thread CTA
+  // CTAs of 128, 64 or 32 threads: the largest that still gives every SM a CTA (the Sturm sequences are
+  // FP64 dependency chains, so the eigenvalues are best spread over all SMs)
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t threads = (j1 - j0) * L;
+  int bs = 128;
+  while (bs > 32 && threads / bs < nsm) bs >>= 1;
+  const int64_t per_block = bs / L;  // eigenvalues per CTA
   const int64_t blocks = (j1 - j0 + per_block - 1) / per_block;
   // algorithmic work: 3 FP64 operations per Sturm step, about 53 / log2(L + 1) rounds of L points
   ProfScope prof(K_EIG_BISECT, s, 3.0 * (double)n * (double)L * (53.0 / std::log2((double)L + 1.0)) * (double)(j1 - j0),
                  16.0 * (double)n);
-  bisect_kernel<L><<<(unsigned)blocks, 128, sm, s>>>(d, e, (int)n, lam, (int)j0, (int)j1);
+  bisect_kernel<L><<<(unsigned)blocks, bs, sm, s>>>(d, e, (int)n, lam, (int)j0, (int)j1);
   note_launch();
   return cudaGetLastError();
 }
@@ -687,7 +747,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
       cudaError_t e = cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    invit_kernel<<<(unsigned)((r + 31) / 32), 32, sm, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
+    invit_kernel<<<(unsigned)((r + 31) / 32), 64, sm, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
                                                            static_cast<double*>(scratch));
     note_launch();
     if (r >= 2) {
@@ -705,8 +765,14 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (n >= 3) {
-    // one warp per column, each column held in shared memory (at most ~200 KB per CTA)
-    const int cols_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(8, (200 * 1024) / (8 * n)));
+    // one warp per column, each column held in shared memory (at most ~200 KB per CTA); few enough
+    // columns per CTA that the CTAs cover every SM (each column is a chain of n - 2 reflections)
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t spread = (r + nsm - 1) / std::max(nsm, 1);
+    const int cols_per_cta =
+        (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (200 * 1024) / (8 * n)));
     const size_t sm = sizeof(double) * (size_t)n * cols_per_cta;
     if (sm > 48 * 1024) {
       e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
