@@ -127,6 +127,27 @@ namespace bht {
 void note_launch(int n) { g_launches += n; }
 void set_last_error(const char* msg) { g_err = msg; }
 
+cudaError_t allow_max_smem(const void* func) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d.first == func && d.second == dev) return cudaSuccess;
+  int cap = 0;
+  e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  // the cap covers the dynamic part only: the opt-in maximum less the kernel's static shared memory
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.push_back({func, dev});
+  return e;
+}
+
 const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
   double* w = rows + (size_t)(rpb + 2) * n;  // n
   double* x = rows + (size_t)(rpb + 3) * n;  // n
   __shared__ double red[33];
+  __shared__ double scal[4];  // K_t, tau_{t+1}, 1 / (alpha - beta) of the step
   const int nb = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
@@ -218,32 +219,65 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
       if (q >= 1) x[q - 1] = R[t + 1 + q];
       pv = fma(pq, v[q], pv);
     }
-    const double Kc = 0.5 * tc * block_sum(pv, red);
+    // The second levels of the two reductions and every scalar of the step run on thread 0, which
+    // publishes them in shared memory: a scalar FP64 chain executed by every warp would hold each SM
+    // sub-partition's FP64 pipe for 64 cycles per instruction and per warp, and the rows' updates need it.
+    pv = warp_sum(pv);
+    if (lane == 0) red[warp] = pv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int k2 = 0; k2 < nw; ++k2) sum += red[k2];
+      scal[0] = 0.5 * tc * sum;
+    }
+    __syncthreads();
+    const double Kc = scal[0];
     for (int q = threadIdx.x; q < m; q += blockDim.x) w[q] -= Kc * v[q];
     __syncthreads();
     // column t + 1 after update t: x[c - t - 2] for columns c >= t + 2 (each thread the entries it
-    // fetched above)
+    // fetched above), with the squared norm below its first entry
     const int m1 = m - 1;
-    for (int q = 1 + threadIdx.x; q < m; q += blockDim.x) x[q - 1] -= w[q] + w[0] * v[q];
-    __syncthreads();
-    const double dnext = R[t + 1] - 2.0 * w[0];
-    double tn = 0.0;
-    if (m1 >= 2) {
-      tn = householder(x, m1, vn, red, &beta);
-    } else {
-      beta = x[0];
-      if (threadIdx.x == 0) vn[0] = 1.0;
-      __syncthreads();
+    double xs = 0.0;
+    for (int q = 1 + threadIdx.x; q < m; q += blockDim.x) {
+      const double xq = x[q - 1] - (w[q] + w[0] * v[q]);
+      x[q - 1] = xq;
+      if (q >= 2) xs = fma(xq, xq, xs);
     }
-    if (b == 0) {
-      if (m1 >= 2)
-        for (int j = threadIdx.x; j < m1; j += blockDim.x) Vh[(size_t)(t + 1) * n + j] = vn[j];
-      if (threadIdx.x == 0) {
-        d[t + 1] = dnext;
-        e[t + 1] = beta;
-        tau[t + 1] = tn;
+    xs = warp_sum(xs);
+    if (lane == 0) red[warp] = xs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // the reflector of column t + 1 (v[0] = 1), as in householder()
+      double xn2 = 0.0;
+      for (int k2 = 0; k2 < nw; ++k2) xn2 += red[k2];
+      const double alpha = x[0];
+      double tt = 0.0, bt = alpha, sc = 0.0;
+      if (m1 >= 2 && xn2 > 0.0) {
+        bt = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        const double am = alpha - bt, inv = 1.0 / (bt * am);
+        tt = -am * am * inv;
+        sc = bt * inv;
+      }
+      scal[1] = tt;
+      scal[2] = sc;
+      if (b == 0) {
+        d[t + 1] = R[t + 1] - 2.0 * w[0];
+        e[t + 1] = bt;
+        tau[t + 1] = tt;
       }
     }
+    __syncthreads();
+    const double tn = scal[1], vscale = scal[2];
+    if (m1 >= 2) {
+      for (int j = threadIdx.x; j < m1; j += blockDim.x) {
+        const double vj = (j == 0) ? 1.0 : (tn != 0.0 ? x[j] * vscale : 0.0);
+        vn[j] = vj;
+        if (b == 0) Vh[(size_t)(t + 1) * n + j] = vj;
+      }
+    } else if (threadIdx.x == 0) {
+      vn[0] = 1.0;
+    }
+    __syncthreads();
     // update t on the own rows gi >= t + 2, with p_{t+1} from the updated entries
     double* pn = pbuf + (size_t)((t + 1) & 1) * n;
     double* Rn = pub + (size_t)(t & 1) * n;  // row t + 2 after update t
@@ -635,7 +669,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
   if (e != cudaSuccess) return e;
   const size_t sm = 2 * sizeof(double) * (size_t)n;
   if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_max_smem(reinterpret_cast<const void*>(tridiag_kernel));
     if (e != cudaSuccess) return e;
   }
   const double flops = 4.0 / 3.0 * (double)n * (double)n * (double)n;
@@ -651,7 +685,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
     const size_t smr = sizeof(double) * (size_t)(rpb + 4) * (size_t)n;
     if (smr <= 200 * 1024) {
       if (smr > 48 * 1024) {
-        e = cudaFuncSetAttribute(tridiag_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        e = allow_max_smem(reinterpret_cast<const void*>(tridiag_rows_kernel));
         if (e != cudaSuccess) return e;
       }
       ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
@@ -698,7 +732,7 @@ cudaError_t launch_bisect_l(int64_t n, const double* d, const double* e, double*
                             cudaStream_t s) {
   const size_t sm = 2 * sizeof(double) * (size_t)n;
   if (sm > 48 * 1024) {
-    cudaError_t e2 = cudaFuncSetAttribute(bisect_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e2 = allow_max_smem(reinterpret_cast<const void*>(bisect_kernel<L>));
     if (e2 != cudaSuccess) return e2;
   }
   // CTAs of 128, 64 or 32 threads: the largest that still gives every SM a CTA (the Sturm sequences are
@@ -744,7 +778,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     ProfScope prof(K_EIG_INVIT, s);
     const size_t sm = 2 * sizeof(double) * (size_t)n;
     if (sm > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(invit_kernel));
       if (e != cudaSuccess) return e;
     }
     invit_kernel<<<(unsigned)((r + 31) / 32), 64, sm, s>>>(L.d, L.e, (int)n, lam, (int)r, U,
@@ -754,8 +788,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
       // every index may lead a cluster; a cluster never exceeds r members
       const size_t smc = sizeof(double) * (size_t)r;
       if (smc > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(cluster_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smc);
+        cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(cluster_orth_kernel));
         if (e != cudaSuccess) return e;
       }
       cluster_orth_kernel<<<(unsigned)r, EIG_THREADS, smc, s>>>(lam, (int)n, (int)r, U);
@@ -775,7 +808,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
         (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (200 * 1024) / (8 * n)));
     const size_t sm = sizeof(double) * (size_t)n * cols_per_cta;
     if (sm > 48 * 1024) {
-      e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      e = allow_max_smem(reinterpret_cast<const void*>(backtransform_kernel));
       if (e != cudaSuccess) return e;
     }
     ProfScope prof(K_EIG_BACK, s, 2.0 * (double)n * (double)n * (double)r,

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   double* rows = sm;                       // rpb x k
   double* dv = rows + (size_t)rpb * k;     // k: v_j^T Z(:, q)
   double* vloc = dv + k;                   // rpb: v_j on the own rows
+  __shared__ double scal[2];               // tau_j and 1 / (alpha - beta) of the step
   const int nb = gridDim.x, b = blockIdx.x;
   unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
   for (int l = 0; l < rpb; ++l) {
@@ -59,16 +60,23 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   for (int j = 0; j < k; ++j) {
     const double* h = hsum + (size_t)(j % 3) * k;
     const double* zr = prow + (size_t)(j & 1) * k;
-    // the reflector, identical in every CTA (same sums)
-    const double alpha = zr[j], xn2 = h[j];
-    double tj = 0.0, scale = 0.0;
-    if (xn2 > 0.0) {
-      const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-      // tj = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one reciprocal of their product
-      const double am = alpha - beta, inv = 1.0 / (beta * am);
-      tj = -am * am * inv;
-      scale = beta * inv;
+    // the reflector, identical in every CTA (same sums); its scalar FP64 chain runs on thread 0 only
+    // (run by every warp it would hold each SM sub-partition's FP64 pipe 64 cycles per instruction)
+    if (threadIdx.x == 0) {
+      const double alpha = zr[j], xn2 = h[j];
+      double t0 = 0.0, s0 = 0.0;
+      if (xn2 > 0.0) {
+        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        // tj = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one reciprocal of their product
+        const double am = alpha - beta, inv = 1.0 / (beta * am);
+        t0 = -am * am * inv;
+        s0 = beta * inv;
+      }
+      scal[0] = t0;
+      scal[1] = s0;
     }
+    __syncthreads();
+    const double tj = scal[0], scale = scal[1];
     for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) dv[q] = fma(scale, h[q], zr[q]);
     for (int l = threadIdx.x; l < rpb; l += blockDim.x) {
       const int i = b + l * nb;
@@ -174,7 +182,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   cudaError_t e = cudaMemsetAsync(hsum, 0, sizeof(double) * 5 * (size_t)k + sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   if (smq > 48 * 1024) {
-    e = cudaFuncSetAttribute(house_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+    e = allow_max_smem(reinterpret_cast<const void*>(house_qr_kernel));
     if (e != cudaSuccess) return e;
   }
   {
@@ -197,7 +205,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   const size_t sma = sizeof(double) * (size_t)c * (HQ_THREADS / 32);
   if (sma > 200 * 1024) return cudaErrorInvalidValue;
   if (sma > 48 * 1024) {
-    e = cudaFuncSetAttribute(apply_reflectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
+    e = allow_max_smem(reinterpret_cast<const void*>(apply_reflectors_kernel));
     if (e != cudaSuccess) return e;
   }
   ProfScope prof(K_HOUSE, s, 4.0 * (double)a * (double)c * (double)k, 8.0 * (double)a * (double)c * 2.0);

@@ -36,6 +36,12 @@ enum KernelClass {
 };
 const char* kernel_class_name(int cls);
 
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum, once per kernel and
+// device, under a lock. The cap belongs to the function and is shared by every host thread; a value
+// set per launch by one thread could be lowered by another between its occupancy query and its
+// launch, so it is only ever raised. Call before launching with more than 48 KB.
+cudaError_t allow_max_smem(const void* func);
+
 // Records a CUDA event pair around one launch on `s` when the class is enabled.
 // `flops` and `bytes` are the algorithmic work of the launch (what the math
 // requires, not what the kernel happens to do), summed per class.

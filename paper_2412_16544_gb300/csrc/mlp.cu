@@ -360,7 +360,7 @@ cudaError_t launch_sketch_features(const double* G, int64_t c, int k, double tol
   sketch_right_kernel<<<grid1((int64_t)k * k), MT, 0, s>>>(T, c, Om, k, S);
   // k x k sketch Gram; when c < k its eigenvalues beyond the c-th are zero
   const size_t sm = sizeof(float) * ((size_t)k * k + k);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(jacobi_features_kernel));
   if (e != cudaSuccess) return e;
   jacobi_features_kernel<<<1, 256, sm, s>>>(S, k, tol, norm2, c, feat);
   note_launch();

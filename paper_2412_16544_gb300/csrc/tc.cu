@@ -470,7 +470,7 @@ cudaError_t launch_ttm_tc_resid(const float* X, int64_t rows, int64_t K, const f
   if (!make_map_2d(&mw, W, (uint64_t)K_pad, (uint64_t)S_pad * nb, KC, (uint32_t)S_tile)) return cudaErrorInvalidValue;
   const size_t smem = 1024 + (size_t)nslot * slot_bytes + (size_t)(3 * nslot + 4) * 8;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(ttm_tc_kernel));
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);

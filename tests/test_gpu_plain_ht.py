@@ -102,3 +102,13 @@ def test_plain_ht_rejects_incremental_calls(B):
     with pytest.raises(B.BHTError):
         B.ht_l2r(Y[:0], 1e-2)
     B.bht_state_destroy(st)
+
+
+def test_concurrent_nodes_of_different_sizes_repeatedly(B):
+    """The nodes of a layer run side by side on host threads; the plain HT tree of (64, 64, 64, 32) has
+    leaves of two sizes and layer-1 nodes of two sizes, so kernels with different shared-memory needs are
+    launched at once. Shared per-kernel launch attributes must not make any of them fail."""
+    Y = torch.from_numpy(S.spectral_field(0, 0, 32, n=64)).cuda()
+    for it in range(60):
+        st = B.ht_l2r(Y, 1e-2, precision="fp64" if it % 2 else "mixed")
+        B.bht_state_destroy(st)
