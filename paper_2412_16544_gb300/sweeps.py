@@ -7,6 +7,7 @@
 * ``axis_order``  item axes permuted on the GPU before the stream (App. D.3).
 * ``normalize``   the multi-variable stream with each physical quantity of each snapshot normalised on
                   its own (none, max-abs, unit vector, z-score; Sec. 5.2): time, CR, RR, RTE.
+* ``budget``      the uniform node-wise tolerance against the adaptive budget of App. C.
 
 The snapshots are the advected spectral fields of ``bht_synth`` (stand-ins for the simulation data the
 paper uses). Times are CUDA-event times of the library calls with the batch already in device memory.
@@ -199,7 +200,41 @@ def normalize(grid=48, items=64, inc=16, test=8, eps=1e-2, precision="mixed", se
     return rows
 
 
-STUDIES = {"bht_vs_ht": bht_vs_ht, "reshape": reshape, "axis_order": axis_order, "normalize": normalize}
+def budget(grid=64, items=128, inc=32, test=16, eps_list=(1e-2, 1e-1), precision="mixed", seed=0):
+    """Uniform node-wise tolerance (Algorithms 1, 2) against the adaptive budget of App. C on the same
+    stream: CR, RR, RTE, time and the error actually spent per increment."""
+    import torch
+    rows = []
+    base = spectral_batch(seed, 0, items, grid)
+    held = spectral_batch(seed, 10_000, test, grid)
+    for eps in eps_list:
+        for mode in ("uniform", "adaptive"):
+            tree = B.bht_tree_create_balanced(base.shape[1:])
+            incs = [base[k:k + inc].contiguous() for k in range(0, items, inc)]
+
+            def one_run():
+                st, total = _timed(lambda: B.bht_l2r(tree, incs[0], eps, precision=precision, budget=mode))
+                for Yk in incs[1:]:
+                    _, ms = _timed(lambda: B.htrise_update(st, Yk, eps, precision=precision))
+                    total += ms
+                return st, total
+
+            st, ms = _median_of(one_run, 3)
+            errs = []
+            for k, Yk in enumerate(incs):
+                rec = B.ht_reconstruct(st, k * inc, Yk.shape[0], dtype="float32")
+                errs.append(float(torch.linalg.vector_norm(rec - Yk) / torch.linalg.vector_norm(Yk)))
+            rows.append({"study": "budget", "budget": mode, "eps": eps, "items": items, "increment": inc,
+                         "precision": precision, "ms": ms, "cr": base.numel() / B.bht_num_elements(st),
+                         "rr": reduction_ratio(st), "rte": B.relative_test_error(st, held),
+                         "max_err_over_eps": max(errs) / eps, "ranks": B.bht_get_ranks(st)})
+            B.bht_state_destroy(st)
+            B.bht_tree_destroy(tree)
+    return rows
+
+
+STUDIES = {"bht_vs_ht": bht_vs_ht, "reshape": reshape, "axis_order": axis_order, "normalize": normalize,
+           "budget": budget}
 
 
 def main():
@@ -215,6 +250,7 @@ def main():
         "reshape": dict(grid=16, items=16, inc=8, test=4),
         "axis_order": dict(items=16, inc=8, test=4),
         "normalize": dict(grid=16, items=16, inc=8, test=4),
+        "budget": dict(grid=16, items=16, inc=8, test=4, eps_list=(1e-1,)),
     }
     t0 = time.time()
     for name in names:

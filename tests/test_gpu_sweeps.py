@@ -28,8 +28,15 @@ def test_bht_vs_ht_small(W):
 
 def test_reshape_axis_order_normalize_small(W):
     rows = W.reshape(grid=16, items=16, inc=8, test=4) + W.axis_order(items=16, inc=8, test=4) + \
-        W.normalize(grid=16, items=16, inc=8, test=4)
-    assert len(rows) == 2 + 4 + 4
+        W.normalize(grid=16, items=16, inc=8, test=4) + W.budget(grid=16, items=16, inc=8, test=4, eps_list=(1e-1,))
+    assert len(rows) == 2 + 4 + 4 + 2
     for r in rows:
         assert "failed" not in r, r
         assert r["cr"] > 0 and r["rr"] >= 1.0 and math.isfinite(r["rte"]) and 0 <= r["rte"] < 1
+
+
+def test_adaptive_budget_keeps_the_per_increment_bound(W):
+    rows = W.budget(grid=32, items=32, inc=16, test=4, eps_list=(1e-1,))
+    uni, ada = rows
+    assert uni["budget"] == "uniform" and ada["budget"] == "adaptive"
+    assert ada["max_err_over_eps"] <= 1.0 + 1e-4 and uni["max_err_over_eps"] <= 1.0 + 1e-4
