@@ -719,6 +719,32 @@ double orth_error(const double* X, int64_t rows, int64_t r, cudaStream_t s) {
   return std::sqrt(h[1] / h[0]);
 }
 
+// Estimate of ||V^T X||_2 for V (rows x r0) and X (rows x k) with orthonormal columns: two power steps
+// on (V^T X)^T (V^T X) from a pseudo-random start, each four matrix-vector products (the ratio of the
+// last two iterates' norms).
+double cross_error(const double* V, int64_t r0, const double* X, int64_t k, int64_t rows, cudaStream_t s) {
+  if (r0 <= 0 || k <= 0) return 0.0;
+  DBuf v(sizeof(double) * (k + r0), s), y(sizeof(double) * rows, s), acc(sizeof(double) * 2, s);
+  double* x = v.as<double>();
+  double* z = x + k;
+  ck(launch_fill_uniform(x, k, 0x63726f7373ull, s), "probe");
+  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 2, s), "memset");
+  for (int it = 0; it < 2; ++it) {
+    if (it == 1) sqnorm_of(x, BHT_F64, k, acc.as<double>(), s);
+    ck(launch_gemm_f64(rows, 1, k, 1.0, X, k, 1, x, 1, 1, 0.0, y.as<double>(), 1, 1, s), "X x");
+    ck(launch_gemm_f64(r0, 1, rows, 1.0, V, 1, r0, y.as<double>(), 1, 1, 0.0, z, 1, 1, s), "V^T y");
+    if (it == 1) break;
+    ck(launch_gemm_f64(rows, 1, r0, 1.0, V, r0, 1, z, 1, 1, 0.0, y.as<double>(), 1, 1, s), "V z");
+    ck(launch_gemm_f64(k, 1, rows, 1.0, X, 1, k, y.as<double>(), 1, 1, 0.0, x, 1, 1, s), "X^T y");
+  }
+  sqnorm_of(z, BHT_F64, r0, acc.as<double>() + 1, s);
+  double h[2];
+  ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H probe");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (!(h[0] > 0.0)) return h[1] > 0.0 ? 1.0 : 0.0;
+  return std::sqrt(h[1] / h[0]);
+}
+
 // Newton-Schulz steps until the estimated orthonormality error is below 1e-12 (none when the
 // columns already are orthonormal to that level; at most max_iters).
 void orthonormalise(double* X, int64_t rows, int64_t r, cudaStream_t s, int max_iters) {
@@ -1588,8 +1614,10 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
           }
         }
         DBuf W(sizeof(double) * r0 * rR + 8, sk);
-        // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic)
-        for (int pass = 0; pass < 2 && r0 > 0; ++pass) {
+        // two Gram-Schmidt passes against U_old (U_R is orthogonal to U_old in exact arithmetic, and Q keeps
+        // it so to rounding level: the passes run only when a probe finds ||U_old^T U_R|| above 1e-13)
+        const bool need_gs = r0 > 0 && cross_error(U[id], r0, UR.as<double>(), rR, a, sk) > 1e-13;
+        for (int pass = 0; pass < 2 && need_gs; ++pass) {
           ck(launch_gemm_f64(r0, rR, a, 1.0, U[id], 1, r0, UR.as<double>(), rR, 1, 0.0, W.as<double>(), rR, 1, sk),
              "U^T U_R");
           ck(launch_gemm_f64(a, rR, r0, -1.0, U[id], r0, 1, W.as<double>(), rR, 1, 1.0, UR.as<double>(), rR, 1, sk),
