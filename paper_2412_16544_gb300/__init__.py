@@ -25,6 +25,7 @@ BHT_F32, BHT_F64 = 0, 1
 BHT_PREC_FP64, BHT_PREC_MIXED = 0, 1
 STATUS_NAMES = {0: "BHT_OK", 1: "BHT_EINVAL", 2: "BHT_ENOMEM", 3: "BHT_ECAPACITY", 4: "BHT_ECUDA",
                 5: "BHT_ENUMERIC", 6: "BHT_ETIMEOUT", 7: "BHT_EUNSUPPORTED"}
+(BHT_EINVAL, BHT_ENOMEM, BHT_ECAPACITY, BHT_ECUDA, BHT_ENUMERIC, BHT_ETIMEOUT, BHT_EUNSUPPORTED) = range(1, 8)
 
 
 class BHTError(RuntimeError):
@@ -386,11 +387,17 @@ def bht_get_core(state, node: int) -> np.ndarray:
     return buf
 
 
-def bht_get_root(state, first: int, count: int) -> np.ndarray:
+def bht_get_root(state, first: int, count: int, out=None):
+    """Root slices [count, r11, r12] as float64 in host memory: a new numpy array, or `out` (a numpy array
+    or a CPU torch tensor, e.g. pinned, of that shape)."""
     ranks = bht_get_ranks(state)
-    out = np.empty((count, ranks[1], ranks[2]), dtype=np.float64)
-    _check(_lib.bht_get_root(state, int(first), int(count), ctypes.c_void_p(out.ctypes.data), out.size),
-           "bht_get_root")
+    if out is None:
+        out = np.empty((count, ranks[1], ranks[2]), dtype=np.float64)
+    ptr, code, shape, keep = _buffer(out)
+    if code != BHT_F64 or tuple(shape) != (count, ranks[1], ranks[2]):
+        raise ValueError(f"out must be float64 [{count}, {ranks[1]}, {ranks[2]}]")
+    _check(_lib.bht_get_root(state, int(first), int(count), ptr, int(np.prod(shape))), "bht_get_root")
+    del keep
     return out
 
 

@@ -793,7 +793,7 @@ int num_sms() {
 bool house_fits(int64_t c, int64_t k) {
   const int64_t nsm = num_sms();
   const int64_t rpb = std::max<int64_t>(8, (c + nsm - 1) / nsm);
-  return sizeof(double) * (rpb * k + k + rpb) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
+  return sizeof(double) * (rpb * k + 2 * k + rpb) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
 }
 
 // Which route to the complement of k columns in R^c, applied to a rows, is cheaper. Householder: k

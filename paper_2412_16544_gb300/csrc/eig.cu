@@ -668,7 +668,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
   cudaError_t e = cudaMemsetAsync(L.bar, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   const size_t sm = 2 * sizeof(double) * (size_t)n;
-  if (sm > 48 * 1024) {
+  if (sm > 0) {  // dynamic + static must fit the cap
     e = allow_max_smem(reinterpret_cast<const void*>(tridiag_kernel));
     if (e != cudaSuccess) return e;
   }
@@ -684,7 +684,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
     const int nbk = (int)((n + rpb - 1) / rpb);
     const size_t smr = sizeof(double) * (size_t)(rpb + 4) * (size_t)n;
     if (smr <= 200 * 1024) {
-      if (smr > 48 * 1024) {
+      if (smr > 0) {  // dynamic + static must fit the cap
         e = allow_max_smem(reinterpret_cast<const void*>(tridiag_rows_kernel));
         if (e != cudaSuccess) return e;
       }
@@ -731,7 +731,7 @@ template <int L>
 cudaError_t launch_bisect_l(int64_t n, const double* d, const double* e, double* lam, int64_t j0, int64_t j1,
                             cudaStream_t s) {
   const size_t sm = 2 * sizeof(double) * (size_t)n;
-  if (sm > 48 * 1024) {
+  if (sm > 0) {  // dynamic + static must fit the cap
     cudaError_t e2 = allow_max_smem(reinterpret_cast<const void*>(bisect_kernel<L>));
     if (e2 != cudaSuccess) return e2;
   }
@@ -777,7 +777,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
   {
     ProfScope prof(K_EIG_INVIT, s);
     const size_t sm = 2 * sizeof(double) * (size_t)n;
-    if (sm > 48 * 1024) {
+    if (sm > 0) {  // dynamic + static must fit the cap
       cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(invit_kernel));
       if (e != cudaSuccess) return e;
     }
@@ -787,7 +787,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     if (r >= 2) {
       // every index may lead a cluster; a cluster never exceeds r members
       const size_t smc = sizeof(double) * (size_t)r;
-      if (smc > 48 * 1024) {
+      if (smc > 0) {  // dynamic + static must fit the cap
         cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(cluster_orth_kernel));
         if (e != cudaSuccess) return e;
       }
@@ -807,7 +807,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     const int cols_per_cta =
         (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (200 * 1024) / (8 * n)));
     const size_t sm = sizeof(double) * (size_t)n * cols_per_cta;
-    if (sm > 48 * 1024) {
+    if (sm > 0) {  // dynamic + static must fit the cap
       e = allow_max_smem(reinterpret_cast<const void*>(backtransform_kernel));
       if (e != cudaSuccess) return e;
     }

@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   extern __shared__ double sm[];
   double* rows = sm;                       // rpb x k
   double* dv = rows + (size_t)rpb * k;     // k: v_j^T Z(:, q)
-  double* vloc = dv + k;                   // rpb: v_j on the own rows
+  double* zq = dv + k;                     // k: the published pivot row
+  double* vloc = zq + k;                   // rpb: v_j on the own rows
   __shared__ double scal[2];               // tau_j and 1 / (alpha - beta) of the step
   const int nb = gridDim.x, b = blockIdx.x;
   unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
@@ -60,6 +61,11 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   for (int j = 0; j < k; ++j) {
     const double* h = hsum + (size_t)(j % 3) * k;
     const double* zr = prow + (size_t)(j & 1) * k;
+    // this step's sums and pivot row for the later columns, fetched while thread 0 forms the reflector
+    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) {
+      dv[q] = h[q];
+      zq[q] = zr[q];
+    }
     // the reflector, identical in every CTA (same sums); its scalar FP64 chain runs on thread 0 only
     // (run by every warp it would hold each SM sub-partition's FP64 pipe 64 cycles per instruction)
     if (threadIdx.x == 0) {
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
     }
     __syncthreads();
     const double tj = scal[0], scale = scal[1];
-    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) dv[q] = fma(scale, h[q], zr[q]);
+    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) dv[q] = fma(scale, dv[q], zq[q]);  // own entries
     for (int l = threadIdx.x; l < rpb; l += blockDim.x) {
       const int i = b + l * nb;
       double v = 0.0;
@@ -92,13 +98,13 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
       for (int q = threadIdx.x; q < k; q += blockDim.x) clr[q] = 0.0;
     }
     __syncthreads();
-    // Z(:, q) -= tau v (v^T Z(:, q)) on the own rows, q > j
+    // Z(:, q) -= (tau v_i) (v^T Z(:, q)) on the own rows, q > j: one FMA per entry
     if (tj != 0.0) {
-      const int w = k - j - 1;
-      for (int e = threadIdx.x; e < rpb * w; e += blockDim.x) {
-        const int l = e / w, q = j + 1 + e % w;
-        const double v = vloc[l];
-        if (v != 0.0) rows[(size_t)l * k + q] -= tj * v * dv[q];
+      for (int l = 0; l < rpb; ++l) {
+        const double tv = tj * vloc[l];
+        if (tv == 0.0) continue;
+        double* row = rows + (size_t)l * k;
+        for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) row[q] = fma(-tv, dv[q], row[q]);
       }
     }
     __syncthreads();
@@ -171,7 +177,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   // about 8 rows per CTA, at most one CTA per SM, the rows in shared memory
   int rpb = (int)std::max<int64_t>(8, (c + nsm - 1) / nsm);
   const int nb = (int)((c + rpb - 1) / rpb);
-  const size_t smq = sizeof(double) * ((size_t)rpb * k + k + rpb);
+  const size_t smq = sizeof(double) * ((size_t)rpb * k + 2 * (size_t)k + rpb);
   if (smq > 200 * 1024) return cudaErrorInvalidValue;
   char* p = static_cast<char*>(work);
   double* V = reinterpret_cast<double*>(p);
@@ -181,7 +187,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   Barrier* bar = reinterpret_cast<Barrier*>(prow + 2 * (size_t)k);
   cudaError_t e = cudaMemsetAsync(hsum, 0, sizeof(double) * 5 * (size_t)k + sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
-  if (smq > 48 * 1024) {
+  if (smq > 0) {  // dynamic + static must fit the cap
     e = allow_max_smem(reinterpret_cast<const void*>(house_qr_kernel));
     if (e != cudaSuccess) return e;
   }
@@ -204,7 +210,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   }
   const size_t sma = sizeof(double) * (size_t)c * (HQ_THREADS / 32);
   if (sma > 200 * 1024) return cudaErrorInvalidValue;
-  if (sma > 48 * 1024) {
+  if (sma > 0) {  // dynamic + static must fit the cap
     e = allow_max_smem(reinterpret_cast<const void*>(apply_reflectors_kernel));
     if (e != cudaSuccess) return e;
   }

@@ -39,7 +39,8 @@ const char* kernel_class_name(int cls);
 // Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum, once per kernel and
 // device, under a lock. The cap belongs to the function and is shared by every host thread; a value
 // set per launch by one thread could be lowered by another between its occupancy query and its
-// launch, so it is only ever raised. Call before launching with more than 48 KB.
+// launch, so it is only ever raised. Call before every launch with dynamic shared memory (dynamic
+// plus static must fit the cap, and the default cap is 48 KB).
 cudaError_t allow_max_smem(const void* func);
 
 // Records a CUDA event pair around one launch on `s` when the class is enabled.
