@@ -375,6 +375,15 @@ struct LTensor {
     for (auto v : dims) n *= v;
     return n;
   }
+  LTensor view_copy() const {  // a non-owning view of the same data
+    LTensor v;
+    v.ptr = ptr;
+    v.dtype = dtype;
+    v.N = N;
+    v.dims = dims;
+    v.node = node;
+    return v;
+  }
   int axis_of(int id) const {
     for (size_t i = 0; i < node.size(); ++i)
       if (node[i] == id) return (int)i;
@@ -487,8 +496,11 @@ void gram_any(const LTensor& C, int axis, double* G, const Arith& ar, cudaStream
 // M(s, t) = U[s * ms + t * mt] (projection: U [T][S], ms = 1, mt = S; expansion: U [S][T], ms = T, mt = 1).
 // rotate: only for the innermost axis, the new axis moves to the front (right after the items).
 // norm_in (nullable, device double): ||C||^2 added in FP64 when the tensor-core kernel runs.
+// k_valid >= 0: the axis is zero padded beyond its first k_valid entries (the basis has k_valid rows);
+// only the tensor-core kernel takes such an axis.
 LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t mt, int64_t S, bool rotate,
-                const Arith& ar, cudaStream_t s, double* norm_in = nullptr, bool* used_norm = nullptr) {
+                const Arith& ar, cudaStream_t s, double* norm_in = nullptr, bool* used_norm = nullptr,
+                int64_t k_valid = -1) {
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
@@ -527,13 +539,16 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
     DBuf W(ttm_tc_weights_bytes(T, S), s);
     // W[s][t] = M(s, t): projection reads U transposed (ldu = S), expansion reads U as is (ldu = T)
     const bool transpose = (ms == 1);
-    ck(launch_prep_tc_weights(U, T, S, transpose ? S : T, transpose, W.as<float>(), nb, s), "tc weights");
+    ck(launch_prep_tc_weights2(U, S, transpose ? S : (k_valid >= 0 ? k_valid : T), nullptr, 0, 1, T, transpose,
+                               W.as<float>(), nb, s, k_valid),
+       "tc weights");
     ck(launch_ttm_tc(static_cast<const float*>(C.ptr), A, T, W.as<float>(), S, nb, out.own.as<float>(), R2, norm_in,
                      nullptr, ar.d_status, s),
        "tensor-core mode product");
     if (used_norm) *used_norm = norm_in != nullptr;
     return out;
   }
+  if (k_valid >= 0) fail(BHT_EINVAL, "internal: padded axis outside the tensor-core kernel");
   // the basis enters the FP32 SIMT kernel as an FP32 copy [S][T]
   DBuf M32(sizeof(float) * (size_t)std::max<int64_t>(S * T, 1), s);
   ck(launch_cast_matrix(U, ms, mt, S, T, M32.as<float>(), s), "basis to FP32");
@@ -556,8 +571,9 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
 // in ||Y||^2 - ||C||^2.
 LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, const double* Q, int64_t c,
                        bool rotate, const Arith& ar, cudaStream_t s, double* norm_in, bool* used_norm,
-                       double* resid) {
-  if (!ar.mixed || !resid || c <= 0) return ttm_any(C, axis, U, 1, r, r, rotate, ar, s, norm_in, used_norm);
+                       double* resid, int64_t k_valid = -1) {
+  if (!ar.mixed || !resid || c <= 0)
+    return ttm_any(C, axis, U, 1, r, r, rotate, ar, s, norm_in, used_norm, k_valid);
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
@@ -579,13 +595,14 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
   const bool aligned = (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0;
   if (B == 1 && C.dtype == BHT_F32 && aligned && ttm_tc_supported(T, r + c, nb)) {
     DBuf W(ttm_tc_weights_bytes(T, r + c), s);
-    ck(launch_prep_tc_weights2(U, r, r, Q, c, c, T, true, W.as<float>(), nb, s), "tc weights");
+    ck(launch_prep_tc_weights2(U, r, r, Q, c, c, T, true, W.as<float>(), nb, s, k_valid), "tc weights");
     ck(launch_ttm_tc_resid(static_cast<const float*>(C.ptr), A, T, W.as<float>(), r + c, r, nb, out.own.as<float>(), R2,
                            norm_in, nullptr, resid, ar.d_status, s),
        "tensor-core mode product");
     if (used_norm) *used_norm = norm_in != nullptr;
     return out;
   }
+  if (k_valid >= 0) fail(BHT_EINVAL, "internal: padded axis outside the tensor-core kernel");
   // FP32 SIMT on [U | Q] cast to fp32 [r + c][T]
   DBuf M32(sizeof(float) * (size_t)std::max<int64_t>((r + c) * T, 1), s);
   ck(launch_cast_matrix(U, 1, r, r, T, M32.as<float>(), s), "basis to FP32");
@@ -601,9 +618,85 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
   return out;
 }
 
+// The axis `ax` of an fp32 tensor moved innermost and zero padded to a multiple of four entries (rows
+// the tensor-core kernel's TMA reads in 16-byte steps). The last axis of the result carries the node of
+// `ax` with the padded size; *k_valid receives its true size.
+LTensor move_axis_innermost(const LTensor& C, int ax, int64_t* k_valid, cudaStream_t s) {
+  int64_t A, T, B;
+  C.view(ax, A, T, B);
+  const int64_t Tp = (T + 3) / 4 * 4;
+  LTensor out;
+  out.dtype = BHT_F32;
+  out.N = C.N;
+  for (size_t i = 0; i < C.dims.size(); ++i)
+    if ((int)i != ax) {
+      out.dims.push_back(C.dims[i]);
+      out.node.push_back(C.node[i]);
+    }
+  out.dims.push_back(Tp);
+  out.node.push_back(C.node[ax]);
+  out.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(A * B * Tp, 1), s);
+  out.ptr = out.own.p;
+  ck(launch_transpose_pad(static_cast<const float*>(C.ptr), out.own.as<float>(), A, T, B, Tp, s), "axis innermost");
+  *k_valid = T;
+  return out;
+}
+
+// Reorder the axes of C to `order` (node ids), moving data only when the order differs.
+void restore_axis_order(LTensor& C, const std::vector<int>& order, cudaStream_t s) {
+  const int d = (int)order.size();
+  std::vector<int> perm(d);
+  bool same = true;
+  for (int k = 0; k < d; ++k) {
+    perm[k] = C.axis_of(order[k]);
+    same = same && perm[k] == k;
+  }
+  if (same) return;
+  LTensor out;
+  out.dtype = C.dtype;
+  out.N = C.N;
+  out.node = order;
+  for (int k = 0; k < d; ++k) out.dims.push_back(C.dims[perm[k]]);
+  out.own = DBuf(dtype_size(C.dtype) * (size_t)std::max<int64_t>(C.numel(), 1), s);
+  out.ptr = out.own.p;
+  ck(launch_permute_items(C.ptr, C.dtype, C.N, d, C.dims.data(), perm.data(), out.own.p, s), "axis order");
+  C = std::move(out);
+}
+
+// Mixed form of a layer's projections on the tensor cores: each listed axis, from the innermost
+// outward, is contracted as the innermost axis (moved there, zero padded, when it is not a
+// multiple-of-four innermost axis) with the new axis rotated to the front; when every axis of the
+// layer is listed the rotations alone restore the order, otherwise one permutation does. With Qs
+// and resid, each axis is projected onto [U | Q] and the complement energy is added to *resid.
+LTensor project_layer_tc(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
+                         const std::vector<int64_t>& rs, const std::vector<const double*>* Qs,
+                         const std::vector<int64_t>* qcs, double* resid, const Arith& ar, cudaStream_t s) {
+  const std::vector<int> order0 = C.node;
+  std::vector<int> ks(ids.size());
+  for (size_t k = 0; k < ks.size(); ++k) ks[k] = (int)k;
+  std::sort(ks.begin(), ks.end(), [&](int a, int b) { return C.axis_of(ids[a]) > C.axis_of(ids[b]); });
+  for (int k : ks) {
+    int ax = C.axis_of(ids[k]);
+    int64_t A, T, B, kv = -1;
+    C.view(ax, A, T, B);
+    if (B != 1 || T % 4 != 0 || (reinterpret_cast<uintptr_t>(C.ptr) & 15) != 0) {
+      C = move_axis_innermost(C, ax, &kv, s);
+      ax = (int)C.dims.size() - 1;
+    }
+    LTensor nxt = (resid && Qs) ? ttm_proj_resid(C, ax, Us[k], rs[k], (*Qs)[k], (*qcs)[k], true, ar, s, nullptr, nullptr,
+                                                 resid, kv)
+                                : ttm_any(C, ax, Us[k], 1, rs[k], rs[k], true, ar, s, nullptr, nullptr, kv);
+    C = std::move(nxt);
+  }
+  restore_axis_order(C, order0, s);
+  return C;
+}
+
 // Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j], cheapest order first.
 LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
                       const std::vector<int64_t>& rs, const Arith& ar, cudaStream_t s) {
+  if (ar.mixed && !ar.tight && C.dtype == BHT_F32 && !ids.empty())
+    return project_layer_tc(std::move(C), ids, Us, rs, nullptr, nullptr, nullptr, ar, s);
   std::vector<std::pair<int, int64_t>> ops;
   for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
   for (int k : best_order(C.dims, ops)) {
@@ -932,7 +1025,15 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       Us.push_back(st->U[id]);
       rs.push_back(st->rank[id]);
     }
-    if (ar.mixed && resid) {
+    if (ar.mixed && !ar.tight && resid && C.dtype == BHT_F32) {
+      std::vector<const double*> Qs;
+      std::vector<int64_t> qcs;
+      for (int id : ids) {
+        Qs.push_back(st->Q[id]);
+        qcs.push_back(qcols(id));
+      }
+      C = project_layer_tc(std::move(C), ids, Us, rs, &Qs, &qcs, resid, ar, s);
+    } else if (ar.mixed && resid) {
       std::vector<std::pair<int, int64_t>> ops;
       for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
       for (int k : best_order(C.dims, ops)) {
@@ -1518,8 +1619,12 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
         const int ax = C.axis_of(id);
         Arith ark = ar;
         ark.d_status = stat[k].as<int>();
-        LTensor W = ttm_any(C, ax, Q[id], 1, qc[k], qc[k], false, ark, sk);
-        gram_any(W, ax, Gs[k].as<double>(), ark, sk);
+        // W = Q^T C_(j): on the tensor cores (axis moved innermost) except at tight tolerances, where the
+        // FP32 products' 2^-24 keep the small residual resolved
+        LTensor W = (ar.mixed && !ar.tight && C.dtype == BHT_F32)
+                        ? project_layer_tc(C.view_copy(), {id}, {Q[id]}, {qc[k]}, nullptr, nullptr, nullptr, ark, sk)
+                        : ttm_any(C, ax, Q[id], 1, qc[k], qc[k], false, ark, sk);
+        gram_any(W, W.axis_of(id), Gs[k].as<double>(), ark, sk);
         ck(launch_trace(Gs[k].as<double>(), qc[k], trd.as<double>() + k, sk), "residual energy");
         if (want_feat)
           ck(launch_sketch_features(Gs[k].as<double>(), qc[k], 128, std::sqrt(eps_nw2), trd.as<double>() + k,

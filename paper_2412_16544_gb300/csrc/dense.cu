@@ -761,6 +761,42 @@ __global__ void transpose2d_kernel(const T* __restrict__ in, T* __restrict__ out
   }
 }
 
+// out[a][b][t] = in[a][t][b] for t < T and 0 for T <= t < Tp: the middle axis of [A][T][B] moved innermost
+// and padded (the tensor-core mode product reads rows of a multiple of four floats). 32 x 32 tiles
+// through shared memory, batches over blockIdx.z.
+__global__ void transpose_pad_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t A, int64_t T,
+                                     int64_t B, int64_t Tp) {
+  __shared__ float tile[32][33];
+  const int64_t t0 = (int64_t)blockIdx.x * 32, b0 = (int64_t)blockIdx.y * 32;
+  for (int64_t a = blockIdx.z; a < A; a += gridDim.z) {
+    const float* src = in + a * T * B;
+    float* dst = out + a * B * Tp;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+      const int64_t t = t0 + j, b = b0 + threadIdx.x;
+      tile[j][threadIdx.x] = (t < T && b < B) ? src[t * B + b] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+      const int64_t b = b0 + j, t = t0 + threadIdx.x;
+      if (b < B && t < Tp) dst[b * Tp + t] = tile[threadIdx.x][j];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_transpose_pad(const float* in, float* out, int64_t A, int64_t T, int64_t B, int64_t Tp,
+                                 cudaStream_t s) {
+  if (A <= 0 || T <= 0 || B <= 0) return cudaSuccess;
+  if (Tp < T) return cudaErrorInvalidValue;
+  const int64_t gx = (Tp + 31) / 32, gy = (B + 31) / 32;
+  if (gx > 2147483647LL || gy > 65535) return cudaErrorInvalidValue;
+  ProfScope prof(K_COPY, s, 0.0, 4.0 * (double)A * (double)B * (double)(T + Tp));
+  const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)std::min<int64_t>(A, 65535)), block(32, 8);
+  transpose_pad_kernel<<<grid, block, 0, s>>>(in, out, A, T, B, Tp);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transpose2d(const void* in, void* out, int64_t rows, int64_t cols, int elem_bytes,
                                cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;

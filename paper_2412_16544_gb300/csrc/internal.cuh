@@ -171,6 +171,10 @@ cudaError_t launch_permute_items(const void* Y, int dtype, int64_t N, int d, con
 cudaError_t launch_item_errors(const void* X, int dtype, const double* Xh, int64_t N, int64_t item, double* err2,
                                double* nrm2, cudaStream_t s);
 
+// out[a][b][t] = in[a][t][b] (t < T), 0 for T <= t < Tp: the middle axis of fp32 [A][T][B] moved innermost
+// and zero padded to Tp.
+cudaError_t launch_transpose_pad(const float* in, float* out, int64_t A, int64_t T, int64_t B, int64_t Tp,
+                                 cudaStream_t s);
 // out = in^T for a row-major [rows][cols] matrix of 4- or 8-byte elements (rows <= 2,097,120).
 cudaError_t launch_transpose2d(const void* in, void* out, int64_t rows, int64_t cols, int elem_bytes,
                                cudaStream_t s);
@@ -230,7 +234,8 @@ cudaError_t launch_ttm_tc(const float* X, int64_t rows, int64_t K, const float* 
 // Weights of the concatenated matrix M = [U | U2] (S1 + S2 output columns; U [K][S1] with row stride
 // ldu when transpose, U2 likewise).
 cudaError_t launch_prep_tc_weights2(const double* U, int64_t S1, int64_t ldu, const double* U2, int64_t S2,
-                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s);
+                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s,
+                                    int64_t k_valid = -1);
 // S computed output columns of which the first S_store are stored (the output's new axis has S_store
 // entries); the squares of the other S - S_store columns are added to *resid (nullable, FP64).
 cudaError_t launch_ttm_tc_resid(const float* X, int64_t rows, int64_t K, const float* W, int64_t S, int64_t S_store,

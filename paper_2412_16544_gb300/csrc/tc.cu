@@ -368,15 +368,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
 }
 
 // W[b][s][k] (b = 0: RN-rounded TF32 of M; b = 1: RN-rounded TF32 of the remainder), zero padded,
-// with M(s, k) from U for s < S1 and from U2 for S1 <= s < S1 + S2.
-__global__ void prep_weights_kernel(const double* __restrict__ U, const double* __restrict__ U2, int64_t K,
+// with M(s, k) from U for s < S1 and from U2 for S1 <= s < S1 + S2; rows k >= Kv (the padding of a
+// zero-padded input axis) are zero.
+__global__ void prep_weights_kernel(const double* __restrict__ U, const double* __restrict__ U2, int64_t Kv,
                                     int64_t S1, int64_t S2, int64_t ldu, int64_t ldu2, int transpose,
                                     float* __restrict__ W, int S_pad, int K_pad, int nb) {
   const int64_t total = (int64_t)S_pad * K_pad;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = e / K_pad, k = e - s * K_pad;
     float x = 0.f;
-    if (k < K) {
+    if (k < Kv) {
       if (s < S1)
         x = (float)(transpose ? U[k * ldu + s] : U[s * ldu + k]);
       else if (s < S1 + S2)
@@ -437,11 +438,13 @@ cudaError_t launch_prep_tc_weights(const double* U, int64_t K, int64_t S, int64_
 }
 
 cudaError_t launch_prep_tc_weights2(const double* U, int64_t S1, int64_t ldu, const double* U2, int64_t S2,
-                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s) {
+                                    int64_t ldu2, int64_t K, bool transpose, float* W, int nb, cudaStream_t s,
+                                    int64_t k_valid) {
   const int64_t S = S1 + S2;
   const int S_pad = (int)((S + 15) / 16 * 16), K_pad = (int)((K + 31) / 32 * 32);
+  const int64_t Kv = (k_valid < 0) ? K : std::min(k_valid, K);
   ProfScope prof(K_COPY, s);
-  prep_weights_kernel<<<64, 256, 0, s>>>(U, U2, K, S1, S2, ldu, ldu2, transpose ? 1 : 0, W, S_pad, K_pad, nb);
+  prep_weights_kernel<<<64, 256, 0, s>>>(U, U2, Kv, S1, S2, ldu, ldu2, transpose ? 1 : 0, W, S_pad, K_pad, nb);
   note_launch();
   return cudaGetLastError();
 }

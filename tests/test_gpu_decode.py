@@ -3,7 +3,10 @@
 
 Both sides run on the same cores: the GPU's cores are copied into an oracle state, so the comparison
 is element by element. Tolerances: FP64 path 1e-12 relative (rounding of a few contractions of length
-<= 4096); mixed path 1e-5 (its mode products run in split TF32 / FP32, about 2^-20 per level).
+<= 4096). Mixed path 5e-5: its mode products run on the tensor cores in split TF32, about 2^-20 relative
+per product, so an output summed over K terms of an orthonormal basis is off by up to about
+2^-20 sqrt(K) of its scale, 3e-5 for the K ~ 1000 of a transfer node. A relative test error inherits
+that as an absolute difference (each item's reconstruction is off by that fraction of the item).
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ import oracle.bht_oracle as OB
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-5}
+TOL = {"fp64": 1e-12, "mixed": 5e-5}
 
 
 @pytest.fixture(scope="module")
