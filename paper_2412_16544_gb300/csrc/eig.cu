@@ -225,10 +225,9 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
     pv = warp_sum(pv);
     if (lane == 0) red[warp] = pv;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int k2 = 0; k2 < nw; ++k2) sum += red[k2];
-      scal[0] = 0.5 * tc * sum;
+    if (warp == 0) {  // the warps' partial sums in log2(nw) shuffle steps, the scalar on lane 0
+      const double sum = warp_sum_first(lane < nw ? red[lane] : 0.0, nw);
+      if (lane == 0) scal[0] = 0.5 * tc * sum;
     }
     __syncthreads();
     const double Kc = scal[0];
@@ -246,10 +245,9 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
     xs = warp_sum(xs);
     if (lane == 0) red[warp] = xs;
     __syncthreads();
+    const double xn2 = (warp == 0) ? warp_sum_first(lane < nw ? red[lane] : 0.0, nw) : 0.0;
     if (threadIdx.x == 0) {
       // the reflector of column t + 1 (v[0] = 1), as in householder()
-      double xn2 = 0.0;
-      for (int k2 = 0; k2 < nw; ++k2) xn2 += red[k2];
       const double alpha = x[0];
       double tt = 0.0, bt = alpha, sc = 0.0;
       if (m1 >= 2 && xn2 > 0.0) {

@@ -58,6 +58,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Sum of the first `n` lanes' values (n <= 32) in log2(n) rounded up shuffle steps; lanes beyond n
+// must hold 0. Every lane of the group of the first `span` lanes gets the sum.
+__device__ __forceinline__ double warp_sum_first(double v, int n) {
+  int span = 1;
+  while (span < n) span <<= 1;
+  for (int o = span >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum over the block (every thread gets the result); red holds 33 doubles.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
