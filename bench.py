@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -175,6 +176,43 @@ def run_reference(a, rank):
 
 
 # ---------------------------------------------------------------------------
+# kernel source identity (for the DRAM traffic recorded from ncu)
+# ---------------------------------------------------------------------------
+# class -> (file, the device functions whose text does the class's work, headers of device helpers they use)
+KERNEL_SOURCES = {
+    "eig_tridiag_f64": ("paper_2412_16544_gb300/csrc/eig.cu", ["tridiag_rows_kernel", "householder"],
+                        ["paper_2412_16544_gb300/csrc/sync.cuh"]),
+}
+
+
+def function_text(src: str, name: str) -> str:
+    """The text of the device function `name` in `src`: from its declaration line to its matching brace."""
+    m = re.search(r"^[^\n;{}]*__(?:global|device)__[^\n;{}]*\b" + re.escape(name) + r"\(", src, flags=re.M)
+    if not m:
+        raise KeyError(name)
+    i = src.index("{", m.end())
+    depth = 0
+    for j in range(i, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        if depth == 0:
+            return src[m.start():j + 1]
+    raise ValueError(name)
+
+
+def kernel_source_hash(cls: str):
+    """sha256 of the source text a kernel class's work depends on, or None when it cannot be read."""
+    if cls not in KERNEL_SOURCES:
+        return None
+    path, funcs, headers = KERNEL_SOURCES[cls]
+    try:
+        src = open(os.path.join(ROOT, path)).read()
+        parts = [function_text(src, fn) for fn in funcs] + [open(os.path.join(ROOT, h)).read() for h in headers]
+    except (OSError, KeyError, ValueError):
+        return None
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 # algorithmic work per kernel class is attached by the library to every launch
@@ -329,8 +367,8 @@ def run_ours(a, rank, world, local_rank):
     # roofline of the dominant kernel class and of the tensor-core mode product (algorithmic work per launch
     # accumulated by the library, CUDA-event durations on the launch stream over the timed region)
     def traffic_of(name):
-        # per-launch DRAM bytes from a committed ncu capture, only while the kernel source is unchanged
-        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic.txt")
+        # per-launch DRAM bytes from a committed ncu capture, only while the kernel's source is unchanged
+        path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
         try:
             lines = open(path).read().splitlines()
         except OSError:
@@ -339,12 +377,8 @@ def run_ours(a, rank, world, local_rank):
         for ln in lines:
             f = ln.split()
             if len(f) == 5 and not ln.startswith("#") and f[0] == tag and f[1] == name:
-                src = os.path.join(os.path.dirname(os.path.abspath(__file__)), f[3])
-                try:
-                    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-                except OSError:
-                    return None
-                return float(f[2]) if h == f[4] else None
+                h = kernel_source_hash(name) if f[3] == "kernel-source" else None
+                return float(f[2]) if h is not None and h == f[4] else None
         return None
 
     def roof(name):

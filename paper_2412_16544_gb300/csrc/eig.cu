@@ -18,6 +18,9 @@
 // global-memory form with two barriers per column.
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
+#include <mutex>
+#include <vector>
 #include <cmath>
 
 #include "internal.cuh"
@@ -659,6 +662,109 @@ size_t eig_workspace_bytes(int64_t n) {
 
 size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 4 * (size_t)n * (size_t)r + 256; }
 
+// ---------------------------------------------------------------------------
+// Autotuned shape of the resident-rows tridiagonalisation. Rows per CTA trade the FP64 work each SM
+// does per column (fewer rows: more SMs share it) against the width of the grid barrier and the
+// occupancy (one or two CTAs per SM). The first matrix of each size bucket (32 rows wide) runs every
+// candidate that fits, timed with CUDA events on the launching stream, and the fastest is kept for the
+// bucket in this process; the candidates compute the same reduction, so any run's output is valid.
+// Off unless BHT_AUTOTUNE=1: timed alone the tuned shapes are a few per cent faster, but they take SMs
+// that the other nodes of a layer, solved at the same time on their own streams, then wait for. The
+// fixed rule (at least eight rows, at most one CTA per SM) leaves those SMs free.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::vector<std::pair<int64_t, int>> g_tune;  // (device * 4096 + bucket, rows per CTA)
+
+bool autotune_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("BHT_AUTOTUNE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+int tuned_rows(int64_t key) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& t : g_tune)
+    if (t.first == key) return t.second;
+  return -1;
+}
+
+void remember_rows(int64_t key, int rpb) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& t : g_tune)
+    if (t.first == key) {
+      t.second = rpb;
+      return;
+    }
+  g_tune.push_back({key, rpb});
+}
+
+// One launch of the resident-rows kernel with rpb rows per CTA (the barrier word is cleared first);
+// cudaErrorInvalidConfiguration when the shape does not fit (shared memory or co-residency).
+cudaError_t launch_rows(const double* G, int n, int rpb, const WorkLayout& L, int* status, int nsm, cudaStream_t s) {
+  const int nbk = (n + rpb - 1) / rpb;
+  const size_t smr = sizeof(double) * (size_t)(rpb + 4) * (size_t)n;
+  if (smr > 200 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(tridiag_rows_kernel));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(L.bar, 0, sizeof(Barrier), s);
+  if (e != cudaSuccess) return e;
+  int nn = n, r = rpb;
+  const double* Gc = G;
+  double *Vh = L.Vh, *d = L.d, *ee = L.e, *tau = L.tau, *pbuf = L.pbuf, *pub = L.pub;
+  Barrier* bar = L.bar;
+  if (nbk == 1) {
+    tridiag_rows_kernel<<<1, EIG_THREADS, smr, s>>>(Gc, nn, r, Vh, d, ee, tau, pbuf, pub, bar, status);
+    note_launch();
+    return cudaGetLastError();
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_rows_kernel, EIG_THREADS, smr);
+  if (e != cudaSuccess) return e;
+  if ((int64_t)per_sm * nsm < nbk) return cudaErrorInvalidConfiguration;
+  void* args[] = {&Gc, &nn, &r, &Vh, &d, &ee, &tau, &pbuf, &pub, &bar, &status};
+  e = cudaLaunchCooperativeKernel((void*)tridiag_rows_kernel, dim3(nbk), dim3(EIG_THREADS), args, smr, s);
+  note_launch();
+  return e;
+}
+
+// Time the candidates on G and return the fastest rows per CTA (the last run leaves a valid output).
+int tune_rows(const double* G, int n, const WorkLayout& L, int* status, int nsm, cudaStream_t s) {
+  const int warps = EIG_THREADS / 32;
+  std::vector<int> cand = {(n + nsm - 1) / nsm, (n + 2 * nsm - 1) / (2 * nsm), warps / 2, warps, 2 * warps};
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  int best = -1;
+  float best_ms = 0.f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1;
+  }
+  for (int rpb : cand) {
+    if (rpb < 1 || rpb > n) continue;
+    cudaEventRecord(e0, s);
+    if (launch_rows(G, n, rpb, L, status, nsm, s) != cudaSuccess) {
+      cudaGetLastError();  // a shape that does not fit is simply not a candidate
+      continue;
+    }
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    if (best < 0 || ms < best_ms) {
+      best = rpb;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+}  // namespace
+
 cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 4096) return cudaErrorInvalidValue;
@@ -674,6 +780,22 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (n > SMALL_N && autotune_on()) {
+    const int64_t key = (int64_t)dev * 4096 + (n + 31) / 32;
+    int rpb = tuned_rows(key);
+    if (rpb < 0) {
+      ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+      rpb = tune_rows(G, (int)n, L, status, nsm, s);
+      if (rpb > 0) {
+        remember_rows(key, rpb);
+        return cudaSuccess;  // the last candidate's output stands
+      }
+    } else {
+      ProfScope prof(K_EIG_TRIDIAG, s, flops, 16.0 * (double)n * (double)n);
+      if (launch_rows(G, (int)n, std::min<int>(rpb, (int)n), L, status, nsm, s) == cudaSuccess) return cudaSuccess;
+      cudaGetLastError();  // fall through to the fixed rule
+    }
+  }
   if (n >= 3) {
     // rows resident in shared memory: one CTA for a small matrix, else about one warp per row
     // (at least ceil(n / #SM) rows per CTA, at most one CTA per SM)

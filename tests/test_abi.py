@@ -93,3 +93,17 @@ def test_sweep_tensorisations_keep_the_snapshot_size():
             assert int(np.prod(shape)) == g ** 3 and len(shape) <= 16, name
     for name, perm in W.AXIS_ORDERS.items():
         assert sorted(perm) == list(range(6)), name
+
+
+def test_kernel_source_hash_follows_the_kernel_text_only():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    h = m.kernel_source_hash("eig_tridiag_f64")
+    assert h is not None and len(h) == 64
+    assert m.kernel_source_hash("no_such_class") is None
+    src = open(os.path.join(ROOT, "paper_2412_16544_gb300", "csrc", "eig.cu")).read()
+    body = m.function_text(src, "tridiag_rows_kernel")
+    assert body.lstrip().startswith("__global__") and body.rstrip().endswith("}")
+    assert body.count("{") == body.count("}")
