@@ -881,12 +881,12 @@ int num_sms() {
 }
 
 // Whether the Householder route to the complement of k orthonormal columns in R^c fits: its rows in
-// the shared memory of at most one CTA per SM, and a row of length c per warp when the reflectors are
-// applied.
+// the shared memory of at most one CTA per SM, and, when the reflectors are applied, a row of length c
+// per warp plus at least one staged reflector.
 bool house_fits(int64_t c, int64_t k) {
   const int64_t nsm = num_sms();
   const int64_t rpb = std::max<int64_t>(8, (c + nsm - 1) / nsm);
-  return sizeof(double) * (rpb * k + 2 * k + rpb) <= 200 * 1024 && sizeof(double) * c * 8 <= 200 * 1024;
+  return sizeof(double) * (rpb * k + 2 * k + rpb) <= 200 * 1024 && sizeof(double) * c * 9 <= 200 * 1024;
 }
 
 // Which route to the complement of k columns in R^c, applied to a rows, is cheaper. Householder: k

@@ -600,31 +600,48 @@ __global__ void __launch_bounds__(EIG_THREADS) cluster_orth_kernel(const double*
 }
 
 // ---------------------------------------------------------------------------
-// Back-transformation U = Q Z = H_0 H_1 ... H_{n-3} Z, one warp per column,
-// reflectors applied last-first; the column lives in shared memory.
+// Back-transformation U = Q Z = H_0 H_1 ... H_{n-3} Z, one warp per column, reflectors applied
+// last-first; the columns live in shared memory, and the reflectors stream through it in blocks of nb
+// rows loaded once per CTA (coalesced) for all its warps, instead of every warp reading each reflector
+// from L2 at the moment it needs it.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(EIG_THREADS) backtransform_kernel(const double* __restrict__ Vh,
                                                                     const double* __restrict__ tau, int n, int r,
-                                                                    double* __restrict__ Z) {
-  extern __shared__ double col[];  // (blockDim / 32) columns of n
+                                                                    int nb, double* __restrict__ Z) {
+  extern __shared__ double sm[];
+  const int ncols = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (c >= r) return;
-  double* z = col + (int64_t)wid * n;
-  for (int i = lane; i < n; i += 32) z[i] = Z[(int64_t)i * r + c];
-  __syncwarp();
-  for (int k = n - 3; k >= 0; --k) {
-    const double t = tau[k];
-    if (t == 0.0) continue;
-    const int m = n - k - 1;
-    const double* v = Vh + (int64_t)k * n;
-    double dot = 0.0;
-    for (int i = lane; i < m; i += 32) dot = fma(v[i], z[k + 1 + i], dot);
-    dot = warp_sum(dot) * t;
-    for (int i = lane; i < m; i += 32) z[k + 1 + i] -= dot * v[i];
-    __syncwarp();
+  const int c = blockIdx.x * ncols + wid;
+  const bool act = c < r;
+  double* z = sm + (int64_t)wid * n;           // this warp's column
+  double* vb = sm + (int64_t)ncols * n;        // nb reflectors, row (k - k0) holds v_k
+  if (act)
+    for (int i = lane; i < n; i += 32) z[i] = Z[(int64_t)i * r + c];
+  for (int k1 = n - 3; k1 >= 0; k1 -= nb) {
+    const int k0 = max(0, k1 - nb + 1);
+    __syncthreads();  // the previous block is consumed
+    for (int kk = k0; kk <= k1; ++kk) {
+      const int m = n - kk - 1;
+      const double* src = Vh + (int64_t)kk * n;
+      double* dst = vb + (int64_t)(kk - k0) * n;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (!act) continue;
+    for (int k = k1; k >= k0; --k) {
+      const double t = tau[k];
+      if (t == 0.0) continue;
+      const int m = n - k - 1;
+      const double* v = vb + (int64_t)(k - k0) * n;
+      double dot = 0.0;
+      for (int i = lane; i < m; i += 32) dot = fma(v[i], z[k + 1 + i], dot);
+      dot = warp_sum(dot) * t;
+      for (int i = lane; i < m; i += 32) z[k + 1 + i] -= dot * v[i];
+      __syncwarp();
+    }
   }
-  for (int i = lane; i < n; i += 32) Z[(int64_t)i * r + c] = z[i];
+  if (act)
+    for (int i = lane; i < n; i += 32) Z[(int64_t)i * r + c] = z[i];
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -925,8 +942,10 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t spread = (r + nsm - 1) / std::max(nsm, 1);
     const int cols_per_cta =
-        (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (200 * 1024) / (8 * n)));
-    const size_t sm = sizeof(double) * (size_t)n * cols_per_cta;
+        (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (100 * 1024) / (8 * n)));
+    // reflector rows staged per block: what is left of about 200 KB, at most 32
+    const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>(32, (200 * 1024) / (8 * n) - cols_per_cta));
+    const size_t sm = sizeof(double) * (size_t)n * (cols_per_cta + nbr);
     if (sm > 0) {  // dynamic + static must fit the cap
       e = allow_max_smem(reinterpret_cast<const void*>(backtransform_kernel));
       if (e != cudaSuccess) return e;
@@ -934,7 +953,7 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
     ProfScope prof(K_EIG_BACK, s, 2.0 * (double)n * (double)n * (double)r,
                    8.0 * (double)n * (0.5 * (double)n + 2.0 * (double)r));
     backtransform_kernel<<<(unsigned)((r + cols_per_cta - 1) / cols_per_cta), cols_per_cta * 32, sm, s>>>(
-        L.Vh, L.tau, (int)n, (int)r, U);
+        L.Vh, L.tau, (int)n, (int)r, nbr, U);
     note_launch();
     e = cudaGetLastError();
   }

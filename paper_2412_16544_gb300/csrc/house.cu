@@ -129,35 +129,52 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
   }
 }
 
-// out[m][0 .. c-k) = (Q[m] H_0 H_1 ... H_{k-1})[k .. c) for every row m of Q (a x c):
-// one warp per row, the row staged in shared memory. Q == nullptr stands for the identity (a == c):
-// then out is the complement of Z itself.
+// out[m][0 .. c-k) = (Q[m] H_0 H_1 ... H_{k-1})[k .. c) for every row m of Q (a x c): one warp per
+// row, a CTA's rows staged in shared memory together with blocks of nbr reflectors, each block loaded
+// once per CTA (coalesced) for all its warps. Q == nullptr stands for the identity (a == c): then out is
+// the complement of Z itself.
 __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const double* __restrict__ Q, int64_t a, int c,
-                                                                      int k, const double* __restrict__ V,
+                                                                      int k, int nbr, const double* __restrict__ V,
                                                                       const double* __restrict__ tau,
                                                                       double* __restrict__ out) {
   extern __shared__ double sm[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double* q = sm + (size_t)w * c;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < a; m += nw) {
-    if (Q)
-      for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
-    else
-      for (int i = lane; i < c; i += 32) q[i] = (i == m) ? 1.0 : 0.0;
-    __syncwarp();
-    for (int j = 0; j < k; ++j) {
-      const double tj = tau[j];
-      if (tj == 0.0) continue;
-      const double* v = V + (size_t)j * c;
-      double d = 0.0;
-      for (int i = j + lane; i < c; i += 32) d = fma(q[i], v[i], d);
-      d = warp_sum(d) * tj;
-      for (int i = j + lane; i < c; i += 32) q[i] -= d * v[i];
-      __syncwarp();
+  double* vb = sm + (size_t)nwarp * c;  // nbr reflectors, row (j - j0) holds v_j
+  const int64_t nbatch = (a + nwarp - 1) / nwarp;
+  for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+    const int64_t m = bt * nwarp + w;
+    const bool act = m < a;
+    __syncthreads();  // the previous batch's rows are written out
+    if (act) {
+      if (Q)
+        for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
+      else
+        for (int i = lane; i < c; i += 32) q[i] = (i == m) ? 1.0 : 0.0;
     }
-    for (int i = k + lane; i < c; i += 32) out[m * (c - k) + (i - k)] = q[i];
-    __syncwarp();
+    for (int j0 = 0; j0 < k; j0 += nbr) {
+      const int j1 = min(k, j0 + nbr);
+      __syncthreads();  // the previous reflector block is consumed
+      for (int jj = j0; jj < j1; ++jj) {
+        const double* src = V + (size_t)jj * c;
+        double* dst = vb + (size_t)(jj - j0) * c;
+        for (int i = jj + threadIdx.x; i < c; i += blockDim.x) dst[i] = src[i];
+      }
+      __syncthreads();
+      if (!act) continue;
+      for (int j = j0; j < j1; ++j) {
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
+        const double* v = vb + (size_t)(j - j0) * c;
+        double d = 0.0;
+        for (int i = j + lane; i < c; i += 32) d = fma(q[i], v[i], d);
+        d = warp_sum(d) * tj;
+        for (int i = j + lane; i < c; i += 32) q[i] -= d * v[i];
+        __syncwarp();
+      }
+    }
+    if (act)
+      for (int i = k + lane; i < c; i += 32) out[m * (c - k) + (i - k)] = q[i];
   }
 }
 
@@ -208,15 +225,18 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
     note_launch();
     if (e != cudaSuccess) return e;
   }
-  const size_t sma = sizeof(double) * (size_t)c * (HQ_THREADS / 32);
+  // rows of one CTA plus a block of reflectors, about 200 KB at most
+  const int nwarp = HQ_THREADS / 32;
+  const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>(32, (200 * 1024) / (8 * c) - nwarp));
+  const size_t sma = sizeof(double) * (size_t)c * (nwarp + nbr);
   if (sma > 200 * 1024) return cudaErrorInvalidValue;
   if (sma > 0) {  // dynamic + static must fit the cap
     e = allow_max_smem(reinterpret_cast<const void*>(apply_reflectors_kernel));
     if (e != cudaSuccess) return e;
   }
   ProfScope prof(K_HOUSE, s, 4.0 * (double)a * (double)c * (double)k, 8.0 * (double)a * (double)c * 2.0);
-  const int blocks = (int)std::min<int64_t>((a + 7) / 8, (int64_t)nsm * 4);
-  apply_reflectors_kernel<<<blocks, HQ_THREADS, sma, s>>>(Q, a, (int)c, (int)k, V, tau, out);
+  const int blocks = (int)std::min<int64_t>((a + nwarp - 1) / nwarp, (int64_t)nsm * 2);
+  apply_reflectors_kernel<<<blocks, HQ_THREADS, sma, s>>>(Q, a, (int)c, (int)k, nbr, V, tau, out);
   note_launch();
   return cudaGetLastError();
 }
