@@ -330,6 +330,17 @@ struct bht_state {
   int64_t n_items = 0;
   int* d_status = nullptr;      // device status word of bounded waits
   bool plain = false;           // plain HT of one tensor (n_1..n_d, N): the batch is a leaf, not the root's
+  // Tensor-core weight planes of committed cores (and their complements), prepared once: the cores of a
+  // skipped update do not change. Keyed by the core pointers; entries go when a core is released.
+  struct TcWeights {
+    const double* U;
+    const double* Q;
+    int64_t S1, S2, T, kv;
+    int transpose;
+    float* W;
+  };
+  mutable std::vector<TcWeights> wcache;
+  mutable std::mutex wmu;
 
   int64_t rows(int id) const {  // alpha of eq. compute_residual; n for a leaf
     const TNode& nd = tree.nodes[id];
@@ -492,6 +503,39 @@ void gram_any(const LTensor& C, int axis, double* G, const Arith& ar, cudaStream
     ck(launch_gram_f64<double>(static_cast<const double*>(C.ptr), G, A, I, B, s), "gram");
 }
 
+// Weights of a committed core (U [T][S1] read transposed, and Q [T][S2] when given) for the tensor-core
+// mode product: prepared on first use for the state, then reused until the core is released.
+const float* state_weights(const bht_state* st, const double* U, int64_t S1, const double* Q, int64_t S2, int64_t T,
+                           int64_t kv, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(st->wmu);
+  for (const auto& w : st->wcache)
+    if (w.U == U && w.Q == Q && w.S1 == S1 && w.S2 == S2 && w.T == T && w.kv == kv && w.transpose == 1) return w.W;
+  float* W = static_cast<float*>(dalloc(ttm_tc_weights_bytes(T, S1 + S2), s));
+  try {
+    ck(launch_prep_tc_weights2(U, S1, S1, Q, S2, S2, T, true, W, 2, s, kv), "tc weights");
+  } catch (...) {
+    dfree(W, s);
+    throw;
+  }
+  st->wcache.push_back({U, Q, S1, S2, T, kv, 1, W});
+  return W;
+}
+
+// Drop the cached weights that read the core or complement p (before p is released).
+void purge_weights(const bht_state* st, const double* p, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(st->wmu);
+  // every earlier use was in a call that has finished; later work on s is ordered after the release
+  auto& v = st->wcache;
+  for (auto it = v.begin(); it != v.end();) {
+    if (it->U == p || it->Q == p) {
+      dfree(it->W, s);
+      it = v.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 // Mode product of axis `axis`: the axis (size T) becomes size S, new(s) = sum_t M(s, t) old(t),
 // M(s, t) = U[s * ms + t * mt] (projection: U [T][S], ms = 1, mt = S; expansion: U [S][T], ms = T, mt = 1).
 // rotate: only for the innermost axis, the new axis moves to the front (right after the items).
@@ -500,7 +544,7 @@ void gram_any(const LTensor& C, int axis, double* G, const Arith& ar, cudaStream
 // only the tensor-core kernel takes such an axis.
 LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t mt, int64_t S, bool rotate,
                 const Arith& ar, cudaStream_t s, double* norm_in = nullptr, bool* used_norm = nullptr,
-                int64_t k_valid = -1) {
+                int64_t k_valid = -1, const bht_state* cache = nullptr) {
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
@@ -536,14 +580,21 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
   const int nb = 2;  // the basis enters as TF32 plus its TF32 remainder: no rounding bias in any norm
   const bool aligned = (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0;
   if (B == 1 && C.dtype == BHT_F32 && aligned && ttm_tc_supported(T, S, nb)) {
-    DBuf W(ttm_tc_weights_bytes(T, S), s);
     // W[s][t] = M(s, t): projection reads U transposed (ldu = S), expansion reads U as is (ldu = T)
     const bool transpose = (ms == 1);
-    ck(launch_prep_tc_weights2(U, S, transpose ? S : (k_valid >= 0 ? k_valid : T), nullptr, 0, 1, T, transpose,
-                               W.as<float>(), nb, s, k_valid),
-       "tc weights");
-    ck(launch_ttm_tc(static_cast<const float*>(C.ptr), A, T, W.as<float>(), S, nb, out.own.as<float>(), R2, norm_in,
-                     nullptr, ar.d_status, s),
+    DBuf Wb;
+    const float* W = nullptr;
+    if (cache && transpose) {
+      W = state_weights(cache, U, S, nullptr, 0, T, k_valid, s);
+    } else {
+      Wb = DBuf(ttm_tc_weights_bytes(T, S), s);
+      ck(launch_prep_tc_weights2(U, S, transpose ? S : (k_valid >= 0 ? k_valid : T), nullptr, 0, 1, T, transpose,
+                                 Wb.as<float>(), nb, s, k_valid),
+         "tc weights");
+      W = Wb.as<float>();
+    }
+    ck(launch_ttm_tc(static_cast<const float*>(C.ptr), A, T, W, S, nb, out.own.as<float>(), R2, norm_in, nullptr,
+                     ar.d_status, s),
        "tensor-core mode product");
     if (used_norm) *used_norm = norm_in != nullptr;
     return out;
@@ -571,9 +622,9 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
 // in ||Y||^2 - ||C||^2.
 LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, const double* Q, int64_t c,
                        bool rotate, const Arith& ar, cudaStream_t s, double* norm_in, bool* used_norm,
-                       double* resid, int64_t k_valid = -1) {
+                       double* resid, int64_t k_valid = -1, const bht_state* cache = nullptr) {
   if (!ar.mixed || !resid || c <= 0)
-    return ttm_any(C, axis, U, 1, r, r, rotate, ar, s, norm_in, used_norm, k_valid);
+    return ttm_any(C, axis, U, 1, r, r, rotate, ar, s, norm_in, used_norm, k_valid, cache);
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
@@ -594,10 +645,17 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
   const int nb = 2;
   const bool aligned = (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0;
   if (B == 1 && C.dtype == BHT_F32 && aligned && ttm_tc_supported(T, r + c, nb)) {
-    DBuf W(ttm_tc_weights_bytes(T, r + c), s);
-    ck(launch_prep_tc_weights2(U, r, r, Q, c, c, T, true, W.as<float>(), nb, s, k_valid), "tc weights");
-    ck(launch_ttm_tc_resid(static_cast<const float*>(C.ptr), A, T, W.as<float>(), r + c, r, nb, out.own.as<float>(), R2,
-                           norm_in, nullptr, resid, ar.d_status, s),
+    DBuf Wb;
+    const float* W = nullptr;
+    if (cache) {
+      W = state_weights(cache, U, r, Q, c, T, k_valid, s);
+    } else {
+      Wb = DBuf(ttm_tc_weights_bytes(T, r + c), s);
+      ck(launch_prep_tc_weights2(U, r, r, Q, c, c, T, true, Wb.as<float>(), nb, s, k_valid), "tc weights");
+      W = Wb.as<float>();
+    }
+    ck(launch_ttm_tc_resid(static_cast<const float*>(C.ptr), A, T, W, r + c, r, nb, out.own.as<float>(), R2, norm_in,
+                           nullptr, resid, ar.d_status, s),
        "tensor-core mode product");
     if (used_norm) *used_norm = norm_in != nullptr;
     return out;
@@ -670,7 +728,8 @@ void restore_axis_order(LTensor& C, const std::vector<int>& order, cudaStream_t 
 // and resid, each axis is projected onto [U | Q] and the complement energy is added to *resid.
 LTensor project_layer_tc(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
                          const std::vector<int64_t>& rs, const std::vector<const double*>* Qs,
-                         const std::vector<int64_t>* qcs, double* resid, const Arith& ar, cudaStream_t s) {
+                         const std::vector<int64_t>* qcs, double* resid, const Arith& ar, cudaStream_t s,
+                         const bht_state* cache = nullptr) {
   const std::vector<int> order0 = C.node;
   std::vector<int> ks(ids.size());
   for (size_t k = 0; k < ks.size(); ++k) ks[k] = (int)k;
@@ -684,8 +743,8 @@ LTensor project_layer_tc(LTensor C, const std::vector<int>& ids, const std::vect
       ax = (int)C.dims.size() - 1;
     }
     LTensor nxt = (resid && Qs) ? ttm_proj_resid(C, ax, Us[k], rs[k], (*Qs)[k], (*qcs)[k], true, ar, s, nullptr, nullptr,
-                                                 resid, kv)
-                                : ttm_any(C, ax, Us[k], 1, rs[k], rs[k], true, ar, s, nullptr, nullptr, kv);
+                                                 resid, kv, cache)
+                                : ttm_any(C, ax, Us[k], 1, rs[k], rs[k], true, ar, s, nullptr, nullptr, kv, cache);
     C = std::move(nxt);
   }
   restore_axis_order(C, order0, s);
@@ -998,7 +1057,7 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       const int id = C.node[ax];
       bool used = false;
       LTensor nxt = ttm_proj_resid(C, ax, st->U[id], st->rank[id], st->Q[id], qcols(id), true, ar, s,
-                                   step == 0 && !ar.tight ? norm_acc : nullptr, &used, resid);
+                                   step == 0 && !ar.tight ? norm_acc : nullptr, &used, resid, -1, st);
       if (step == 0 && norm_done) *norm_done = used;
       C = std::move(nxt);
     }
@@ -1032,7 +1091,9 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
         Qs.push_back(st->Q[id]);
         qcs.push_back(qcols(id));
       }
-      C = project_layer_tc(std::move(C), ids, Us, rs, &Qs, &qcs, resid, ar, s);
+      C = project_layer_tc(std::move(C), ids, Us, rs, &Qs, &qcs, resid, ar, s, st);
+    } else if (ar.mixed && !ar.tight && C.dtype == BHT_F32) {
+      C = project_layer_tc(std::move(C), ids, Us, rs, nullptr, nullptr, nullptr, ar, s, st);
     } else if (ar.mixed && resid) {
       std::vector<std::pair<int, int64_t>> ops;
       for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
@@ -1812,8 +1873,14 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   }
   // commit: release the replaced cores and any intermediate core superseded within this call
   for (size_t id = 1; id < U.size(); ++id) {
-    if (U[id] != st->U[id]) dfree(st->U[id], s);
-    if (Q[id] != st->Q[id]) dfree(st->Q[id], s);
+    if (U[id] != st->U[id]) {
+      purge_weights(st, st->U[id], s);
+      dfree(st->U[id], s);
+    }
+    if (Q[id] != st->Q[id]) {
+      purge_weights(st, st->Q[id], s);
+      dfree(st->Q[id], s);
+    }
   }
   for (double* p : fresh)
     if (std::find(U.begin(), U.end(), p) == U.end() && std::find(Q.begin(), Q.end(), p) == Q.end()) dfree(p, s);
@@ -2233,6 +2300,9 @@ bht_status bht_state_destroy(bht_state* st) {
   for (double* p : st->Q)
     if (p) cudaFreeAsync(p, nullptr);
   if (st->root) cudaFreeAsync(st->root, nullptr);
+  cudaDeviceSynchronize();
+  for (auto& w : st->wcache) cudaFreeAsync(w.W, nullptr);
+  st->wcache.clear();
   cudaDeviceSynchronize();
   if (st->d_status) cudaFree(st->d_status);
   delete st;
