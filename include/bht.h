@@ -12,7 +12,14 @@
  *                      (eq. htucker_reconstruction, Section 2.3);
  *   - ht_encode      : latent representation of unseen items on the current
  *                      cores (Step 1 of Algorithm 2, used for the relative
- *                      test error of eq. generalization_performance).
+ *                      test error of eq. generalization_performance);
+ *   - ht_decode, ht_relative_test_error : latent items back to tensors, and
+ *                      the mean per-item relative error of unseen items;
+ *   - ht_l2r         : the plain hierarchical Tucker baseline (the batch as a
+ *                      leaf, leaves-to-root of Section 2.3.1);
+ *   - bht_normalize, bht_denormalize, bht_permute_items : batch preparation
+ *                      (per-group normalisation, item axis orders);
+ *   - bht_mlp_*, bht_sketch_features : the rank / expansion predictor.
  *
  * Conventions shared by every call
  *   - Every function returns bht_status; BHT_OK (0) on success. Nothing is
@@ -42,6 +49,9 @@
  *   - Errors: on any error inside htrise_update the state is left exactly as
  *     it was before the call (updates are built in fresh buffers and
  *     committed only at the end).
+ *   - Environment: BHT_AUTOTUNE=1 lets the library time the launch shapes of
+ *     its tridiagonalisation per matrix-size bucket and keep the fastest for
+ *     the process (off by default).
  */
 #ifndef BHT_H_
 #define BHT_H_

@@ -40,7 +40,6 @@ namespace {
 constexpr int TC_THREADS = 256;
 constexpr int BM = 128;           // rows per tile (MMA M)
 constexpr int KC = 32;            // fp32 per 128-byte swizzle row (one K chunk)
-constexpr int NSLOT = 4;          // K-chunk ring depth
 constexpr int CHUNK_BYTES = BM * KC * 4;  // 16 KB
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
@@ -400,7 +399,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }
