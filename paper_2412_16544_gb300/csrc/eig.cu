@@ -599,51 +599,6 @@ __global__ void __launch_bounds__(EIG_THREADS) cluster_orth_kernel(const double*
   }
 }
 
-// ---------------------------------------------------------------------------
-// Back-transformation U = Q Z = H_0 H_1 ... H_{n-3} Z, one warp per column, reflectors applied
-// last-first; the columns live in shared memory, and the reflectors stream through it in blocks of nb
-// rows loaded once per CTA (coalesced) for all its warps, instead of every warp reading each reflector
-// from L2 at the moment it needs it.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(EIG_THREADS) backtransform_kernel(const double* __restrict__ Vh,
-                                                                    const double* __restrict__ tau, int n, int r,
-                                                                    int nb, double* __restrict__ Z) {
-  extern __shared__ double sm[];
-  const int ncols = blockDim.x >> 5;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * ncols + wid;
-  const bool act = c < r;
-  double* z = sm + (int64_t)wid * n;           // this warp's column
-  double* vb = sm + (int64_t)ncols * n;        // nb reflectors, row (k - k0) holds v_k
-  if (act)
-    for (int i = lane; i < n; i += 32) z[i] = Z[(int64_t)i * r + c];
-  for (int k1 = n - 3; k1 >= 0; k1 -= nb) {
-    const int k0 = max(0, k1 - nb + 1);
-    __syncthreads();  // the previous block is consumed
-    for (int kk = k0; kk <= k1; ++kk) {
-      const int m = n - kk - 1;
-      const double* src = Vh + (int64_t)kk * n;
-      double* dst = vb + (int64_t)(kk - k0) * n;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (!act) continue;
-    for (int k = k1; k >= k0; --k) {
-      const double t = tau[k];
-      if (t == 0.0) continue;
-      const int m = n - k - 1;
-      const double* v = vb + (int64_t)(k - k0) * n;
-      double dot = 0.0;
-      for (int i = lane; i < m; i += 32) dot = fma(v[i], z[k + 1 + i], dot);
-      dot = warp_sum(dot) * t;
-      for (int i = lane; i < m; i += 32) z[k + 1 + i] -= dot * v[i];
-      __syncwarp();
-    }
-  }
-  if (act)
-    for (int i = lane; i < n; i += 32) Z[(int64_t)i * r + c] = z[i];
-}
-
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct WorkLayout {
@@ -677,7 +632,9 @@ size_t eig_workspace_bytes(int64_t n) {
          256;
 }
 
-size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) { return sizeof(double) * 4 * (size_t)n * (size_t)r + 256; }
+size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) {
+  return std::max(sizeof(double) * 4 * (size_t)n * (size_t)r + 256, wy_workspace_bytes(n));
+}
 
 // ---------------------------------------------------------------------------
 // Autotuned shape of the resident-rows tridiagonalisation. Rows per CTA trade the FP64 work each SM
@@ -935,27 +892,11 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (n >= 3) {
-    // one warp per column, each column held in shared memory (at most ~200 KB per CTA); few enough
-    // columns per CTA that the CTAs cover every SM (each column is a chain of n - 2 reflections)
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t spread = (r + nsm - 1) / std::max(nsm, 1);
-    const int cols_per_cta =
-        (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(8, spread), (100 * 1024) / (8 * n)));
-    // reflector rows staged per block: what is left of about 200 KB, at most 32
-    const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>(32, (200 * 1024) / (8 * n) - cols_per_cta));
-    const size_t sm = sizeof(double) * (size_t)n * (cols_per_cta + nbr);
-    if (sm > 0) {  // dynamic + static must fit the cap
-      e = allow_max_smem(reinterpret_cast<const void*>(backtransform_kernel));
-      if (e != cudaSuccess) return e;
-    }
+    // U = H_0 H_1 ... H_{n-3} Z in blocks of reflectors (compact WY form, wy.cu); the block factors go to
+    // the scratch space, which the inverse iteration no longer needs
     ProfScope prof(K_EIG_BACK, s, 2.0 * (double)n * (double)n * (double)r,
                    8.0 * (double)n * (0.5 * (double)n + 2.0 * (double)r));
-    backtransform_kernel<<<(unsigned)((r + cols_per_cta - 1) / cols_per_cta), cols_per_cta * 32, sm, s>>>(
-        L.Vh, L.tau, (int)n, (int)r, nbr, U);
-    note_launch();
-    e = cudaGetLastError();
+    e = launch_wy_apply(L.Vh, n, 1, 1, L.tau, n - 2, n, U, r, 0, r, U, r, scratch, s);
   }
   return e;
 }

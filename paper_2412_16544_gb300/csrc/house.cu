@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(HQ_THREADS) house_qr_kernel(const double* __re
 
 // out[m][0 .. c-k) = (Q[m] H_0 H_1 ... H_{k-1})[k .. c) for every row m of Q (a x c): one warp per
 // row, a CTA's rows staged in shared memory together with blocks of nbr reflectors, each block loaded
-// once per CTA (coalesced) for all its warps. Q == nullptr stands for the identity (a == c): then out is
-// the complement of Z itself.
+// once per CTA (coalesced) for all its warps. With many rows the warps keep the FP64 pipe busy; the
+// complement of Z itself (Q the identity) goes through the blocked form in wy.cu instead.
 __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const double* __restrict__ Q, int64_t a, int c,
                                                                       int k, int nbr, const double* __restrict__ V,
                                                                       const double* __restrict__ tau,
@@ -146,12 +146,8 @@ __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const doub
     const int64_t m = bt * nwarp + w;
     const bool act = m < a;
     __syncthreads();  // the previous batch's rows are written out
-    if (act) {
-      if (Q)
-        for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
-      else
-        for (int i = lane; i < c; i += 32) q[i] = (i == m) ? 1.0 : 0.0;
-    }
+    if (act)
+      for (int i = lane; i < c; i += 32) q[i] = Q[m * c + i];
     for (int j0 = 0; j0 < k; j0 += nbr) {
       const int j1 = min(k, j0 + nbr);
       __syncthreads();  // the previous reflector block is consumed
@@ -180,9 +176,16 @@ __global__ void __launch_bounds__(HQ_THREADS) apply_reflectors_kernel(const doub
 
 }  // namespace
 
+// V [k][c], tau [k], hsum [3][k], prow [2][k], the barrier word, then the block factors of the
+// blocked application (identity case), 256-byte aligned.
+static size_t house_barrier_offset(int64_t c, int64_t k) { return sizeof(double) * ((size_t)k * c + 6 * (size_t)k); }
+static size_t house_factors_offset(int64_t c, int64_t k) {
+  return (house_barrier_offset(c, k) + sizeof(Barrier) + 255) & ~(size_t)255;
+}
+
 size_t house_workspace_bytes(int64_t c, int64_t k, int nsm) {
   (void)nsm;
-  return sizeof(double) * ((size_t)k * c + k + 5 * (size_t)k) + 2 * 256 + sizeof(Barrier);
+  return house_factors_offset(c, k) + wy_workspace_bytes(k) + 256;
 }
 
 cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const double* Z, int64_t k, double* out,
@@ -201,7 +204,7 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
   double* tau = V + (size_t)k * c;
   double* hsum = tau + k;
   double* prow = hsum + 3 * (size_t)k;
-  Barrier* bar = reinterpret_cast<Barrier*>(prow + 2 * (size_t)k);
+  Barrier* bar = reinterpret_cast<Barrier*>(p + house_barrier_offset(c, k));  // = prow + 2k
   cudaError_t e = cudaMemsetAsync(hsum, 0, sizeof(double) * 5 * (size_t)k + sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   if (smq > 0) {  // dynamic + static must fit the cap
@@ -224,6 +227,13 @@ cudaError_t launch_house_complement(const double* Q, int64_t a, int64_t c, const
     }
     note_launch();
     if (e != cudaSuccess) return e;
+  }
+  if (!Q) {
+    // the complement itself: H_0 ... H_{k-1} applied to e_k .. e_{c-1} in blocks of reflectors (wy.cu),
+    // c - k vectors instead of the c rows of the identity
+    ProfScope prof(K_HOUSE, s, 2.0 * (double)(c - k) * (2.0 * (double)c * (double)k - (double)k * (double)k),
+                   8.0 * (double)c * ((double)k + (double)(c - k)));
+    return launch_wy_apply(V, c, 0, 0, tau, k, c, nullptr, 0, k, c - k, out, c - k, p + house_factors_offset(c, k), s);
   }
   // rows of one CTA plus a block of reflectors, about 200 KB at most
   const int nwarp = HQ_THREADS / 32;

@@ -84,6 +84,16 @@ template <typename Tin>
 cudaError_t launch_ttm_f32(const Tin* X, float* out, const float* M, int64_t ms, int64_t mt, int64_t A, int64_t T,
                            int64_t B, int64_t S, int64_t R2, cudaStream_t s);
 
+// x <- H_0 H_1 ... H_{K-1} x for nvec vectors of length L (wy.cu), H_k = I - tau_k v_k v_k^T with v_k
+// zero above row k + off (off 0 or 1), 1 at that row, and its entry i stored at
+// V[k * ldv + i - rel * (k + off)] (rel 0: absolute rows; rel 1: from position 0). Vector c is
+// X[i * xrs + c] (X null: the unit vector e_{unit0 + c}) and is written to out[i * ors + c]; X and out
+// may be the same matrix. K <= L <= 4096. work: wy_workspace_bytes(K) bytes (the block factors).
+size_t wy_workspace_bytes(int64_t K);
+cudaError_t launch_wy_apply(const double* V, int64_t ldv, int off, int rel, const double* tau, int64_t K, int64_t L,
+                            const double* X, int64_t xrs, int64_t unit0, int64_t nvec, double* out, int64_t ors,
+                            void* work, cudaStream_t s);
+
 // Householder complement: out (a x (c - k)) = Q (a x c) times the last c - k columns of the
 // orthogonal factor of the QR factorisation of Z (c x k, orthonormal columns). work: at least
 // house_workspace_bytes(c, k, #SM) bytes; status: device word of the bounded grid barrier.
