@@ -351,16 +351,53 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const d
   return cnt;
 }
 
+// The same count in FP32 (the FP32 pipe issues 64 times faster than the FP64 one on this part), with
+// the carried minors kept within [2^-40, 2^40] and an exactly zero minor replaced by -2^-60 p_{i-1}.
+// With unit roundoff u = 2^-24, each step's three roundings and the rounding of d_i, e_i^2 and x to
+// FP32 make the count exact for a tridiagonal matrix T' with |d'_i - d_i| <= 2u (|d_i| + |x|) and
+// |e'_i - e_i| <= 1.5u |e_i| (the usual backward analysis of the ratio recurrence: the ratio of two
+// carried minors obeys it with the step's rounding factors folded into d_i and e_{i-1}^2), so on the
+// scaled T (|d_i|, |e_i|, |x| <= 1) ||T' - T|| <= 7u. A count of c at x thus brackets: the exact
+// counts at x - 7u and x + 7u lie below and above c.
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ d, const float* __restrict__ e2, int n,
+                                               float x) {
+  float a0 = 1.0f, a1 = d[0] - x;
+  if (a1 == 0.0f) a1 = -0x1p-60f;
+  int cnt = a1 < 0.0f;
+#pragma unroll 4
+  for (int i = 1; i < n; ++i) {
+    float t = fmaf(d[i] - x, a1, -e2[i - 1] * a0);
+    const unsigned ex = (__float_as_uint(t) >> 23) & 0xFFu;
+    if (ex - (127u - 40u) > 80u) {  // exponent outside [-40, 40], zero or subnormal
+      if (t == 0.0f) t = -0x1p-60f * a1;
+      const float f = fabsf(t) > 1.0f ? 0x1p-40f : 0x1p+40f;
+      if (fabsf(t) > 0x1p+40f || fabsf(t) < 0x1p-40f) {
+        t *= f;
+        a1 *= f;
+      }
+    }
+    cnt += (__float_as_int(t) ^ __float_as_int(a1)) < 0;
+    a0 = a1;
+    a1 = t;
+  }
+  return cnt;
+}
+
 // L lanes share an eigenvalue and evaluate L interior points of its interval
-// per round (multisection): the interval shrinks (L + 1)-fold per round. An
-// interval stops at a width of 2 eps |lambda| or 4 eps ||T||: the
-// tridiagonalisation already perturbs every eigenvalue by about eps ||T||.
+// per round (multisection): the interval shrinks (L + 1)-fold per round. The
+// first rounds count in FP32 until the interval is 2^-17 ||T|| wide; it is then
+// widened by 2^-18 ||T|| (over nine times the FP32 counts' error bound, see
+// sturm_count_f32) and the FP64 rounds take over. An interval stops at a width of
+// 2 eps |lambda| or 4 eps ||T||: the tridiagonalisation already perturbs every
+// eigenvalue by about eps ||T||.
 template <int L>
 __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ dg, const double* __restrict__ eg,
                                                      int n, double* __restrict__ lam, int j0, int j1) {
   extern __shared__ double tsm[];
   double* d = tsm;       // scaled diagonal
   double* e2 = tsm + n;  // scaled squared off-diagonal
+  float* d32 = reinterpret_cast<float*>(tsm + 2 * (size_t)n);  // the same in FP32
+  float* e32 = d32 + n;
   __shared__ double red_lo[4], red_hi[4];
   // Gershgorin interval of T, block-wide
   double gl = INFINITY, gu = -INFINITY;
@@ -391,6 +428,8 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
     d[i] = dg[i] * sc;
     const double ei = (i + 1 < n) ? eg[i] * sc : 0.0;
     e2[i] = ei * ei;
+    d32[i] = (float)d[i];
+    e32[i] = (float)e2[i];
   }
   __syncthreads();
   const int sub = (threadIdx.x & 31) / L;                   // eigenvalue slot in the warp
@@ -403,6 +442,29 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
   const double abs_floor = 4.0 * DBL_EPSILON * tn;
   double lo = gl * sc - 2.0 * DBL_EPSILON * tn * n, hi = gu * sc + 2.0 * DBL_EPSILON * tn * n;
   const unsigned gmask = (0xffffffffu >> (32 - L)) << (sub * L);
+  // FP32 rounds down to a width of 2^-17 (tn is in [0.5, 1)); an interval they moved is widened after
+  bool moved = false;
+  for (int it = 0; it < 16; ++it) {
+    const bool done = !active || hi - lo <= 0x1p-17;
+    if (__all_sync(0xffffffffu, done)) break;
+    const double step = (hi - lo) / (double)(L + 1);
+    const double x = lo + step * (double)(g + 1);
+    const bool above = !done && sturm_count_f32(d32, e32, n, (float)x) > k;
+    const unsigned bal = __ballot_sync(0xffffffffu, above) & gmask;
+    if (!done) {
+      const unsigned mine = bal >> (sub * L);
+      const int first = mine ? __ffs(mine) - 1 : L;
+      const double nlo = (first == 0) ? lo : lo + step * (double)first;
+      const double nhi = (first == L) ? hi : lo + step * (double)(first + 1);
+      lo = nlo;
+      hi = nhi;
+      moved = true;
+    }
+  }
+  if (moved) {
+    lo -= 0x1p-18;
+    hi += 0x1p-18;
+  }
   for (int it = 0; it < 64; ++it) {
     const bool done = !active || hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + abs_floor;
     if (__all_sync(0xffffffffu, done)) break;
@@ -824,7 +886,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
 template <int L>
 cudaError_t launch_bisect_l(int64_t n, const double* d, const double* e, double* lam, int64_t j0, int64_t j1,
                             cudaStream_t s) {
-  const size_t sm = 2 * sizeof(double) * (size_t)n;
+  const size_t sm = (2 * sizeof(double) + 2 * sizeof(float)) * (size_t)n;
   if (sm > 0) {  // dynamic + static must fit the cap
     cudaError_t e2 = allow_max_smem(reinterpret_cast<const void*>(bisect_kernel<L>));
     if (e2 != cudaSuccess) return e2;
