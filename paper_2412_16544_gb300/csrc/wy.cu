@@ -47,9 +47,17 @@ __global__ void __launch_bounds__(WY_THREADS) wy_tfactor_kernel(const double* __
     double acc = 0.0;
     if (tau[kp] != 0.0 && tau[kl] != 0.0) {
       // v_l starts at row kl + off, below the start of v_p
-      for (int i = kl + off + lane; i < L; i += 32)
-        acc = fma(V[refl_index(ldv, off, rel, kp, i)], V[refl_index(ldv, off, rel, kl, i)], acc);
-      acc = warp_sum(acc);
+      double part[4] = {0.0, 0.0, 0.0, 0.0};  // four loads of each vector in flight per lane
+      int i = kl + off + lane;
+      for (; i + 96 < L; i += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          part[u] = fma(V[refl_index(ldv, off, rel, kp, i + 32 * u)], V[refl_index(ldv, off, rel, kl, i + 32 * u)],
+                        part[u]);
+      }
+      for (; i < L; i += 32)
+        part[0] = fma(V[refl_index(ldv, off, rel, kp, i)], V[refl_index(ldv, off, rel, kl, i)], part[0]);
+      acc = warp_sum((part[0] + part[1]) + (part[2] + part[3]));
     }
     if (lane == 0) S[p][l] = acc;
   }
@@ -103,13 +111,27 @@ __global__ void __launch_bounds__(WY_THREADS, 1)
     const int k0 = b * nb, kb = min(nb, K - k0), i0 = k0 + off, span = L - i0;
     __syncthreads();  // the vectors are loaded / the previous block is applied
     if (span <= 0) continue;
-    for (int e = threadIdx.x; e < kb * span; e += blockDim.x) {
-      const int j = e / span, i = i0 + (e - j * span), k = k0 + j;
-      double v = 0.0;
-      if (i >= k + off && tau[k] != 0.0) v = V[refl_index(ldv, off, rel, k, i)];
-      vs[(size_t)j * L + i] = v;
+    // eight loads in flight per thread before their stores (one at a time, each waited for the L2)
+    const int tot = kb * span;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * WY_THREADS) {
+      double val[8];
+      int dst[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * WY_THREADS;
+        val[u] = 0.0;
+        dst[u] = -1;
+        if (e < tot) {
+          const int j = e / span, i = i0 + (e - j * span), k = k0 + j;
+          dst[u] = j * L + i;
+          if (i >= k + off && tau[k] != 0.0) val[u] = V[refl_index(ldv, off, rel, k, i)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (dst[u] >= 0) vs[dst[u]] = val[u];
     }
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) Ts[e] = Tg[(int64_t)b * nb * nb + e];
+    for (int e = threadIdx.x; e < nb * nb; e += WY_THREADS) Ts[e] = Tg[(int64_t)b * nb * nb + e];
     __syncthreads();
     // w = V^T x: one warp per reflector, every vector of the CTA in the same pass over v
     for (int j = warp; j < kb; j += nw) {
