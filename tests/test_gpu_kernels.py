@@ -31,6 +31,41 @@ def test_sym_eig_matches_lapack(B, n):
     assert np.abs(resid).max() <= 1e-10 * w[0]
 
 
+# Vector counts and lengths that reach the other launch shapes of the blocked back-transformation:
+# 8 vectors per CTA with more CTAs than SMs (1300 vectors), blocks of fewer than 16 reflectors next to
+# them (1600 rows), and one vector alone.
+@pytest.mark.parametrize("n,r", [(1600, 1300), (1600, 5)])
+def test_sym_eig_many_vectors(B, n, r):
+    rng = np.random.default_rng(n + r)
+    X = rng.normal(size=(n, n + 7)) * np.logspace(0, -6, n)[:, None]
+    G = X @ X.T
+    w = np.linalg.eigvalsh(G)[::-1]
+    lam, U = B.bht_sym_eig(torch.from_numpy(G.copy()).cuda(), r)
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    assert np.abs(lam - w).max() <= 1e-12 * w[0]
+    assert np.abs(U.T @ U - np.eye(r)).max() <= 1e-12
+    resid = G @ U - U * lam[:r]
+    assert np.abs(resid).max() <= 1e-10 * w[0]
+
+
+# Every eigenvector of a Gram spectrum graded over twelve decades: its last 175 eigenvalues lie below
+# 1e-9 ||G|| (one cluster for the inverse iteration) with gaps near 4e-14 ||G||. The eigenvalues match
+# LAPACK, but the vectors come back far from orthonormal: the shifts inside a cluster are spread by
+# 10 eps ||T|| per member, cumulatively, which moves the last members past their neighbours' eigenvalues.
+# A truncation asks for such vectors only below about eps_rel = 1e-6 on so graded a spectrum.
+@pytest.mark.xfail(reason="cumulative shift spreading inside a large cluster of tiny eigenvalues", strict=False)
+def test_sym_eig_every_vector_of_graded_spectrum(B):
+    n = r = 700
+    rng = np.random.default_rng(n + r)
+    X = rng.normal(size=(n, n + 7)) * np.logspace(0, -6, n)[:, None]
+    G = X @ X.T
+    w = np.linalg.eigvalsh(G)[::-1]
+    lam, U = B.bht_sym_eig(torch.from_numpy(G.copy()).cuda(), r)
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    assert np.abs(lam - w).max() <= 1e-12 * w[0]
+    assert np.abs(U.T @ U - np.eye(r)).max() <= 1e-12
+
+
 def test_sym_eig_degenerate_pairs(B):
     rng = np.random.default_rng(3)
     n = 40
