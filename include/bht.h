@@ -19,7 +19,10 @@
  *                      leaf, leaves-to-root of Section 2.3.1);
  *   - bht_normalize, bht_denormalize, bht_permute_items : batch preparation
  *                      (per-group normalisation, item axis orders);
- *   - bht_mlp_*, bht_sketch_features : the rank / expansion predictor.
+ *   - bht_mlp_*, bht_sketch_features : the rank / expansion predictor;
+ *   - bht_synth_chebyshev : a device generator of the smooth sensor-grid
+ *                      stream used to measure long streams (input synthesis,
+ *                      no counterpart in the paper).
  *
  * Conventions shared by every call
  *   - Every function returns bht_status; BHT_OK (0) on success. Nothing is
@@ -221,6 +224,24 @@ bht_status bht_denormalize(void* Y, int32_t dtype, int64_t groups, int64_t group
 bht_status bht_permute_items(const void* Y, int32_t dtype, int64_t N, int32_t d, const int64_t* dims,
                              const int32_t* perm, void* out, void* stream);
 
+/* Device generator of the smooth sensor-grid stream (input synthesis; the paper has no counterpart:
+ * its cyber-physical experiments read recorded data, which this stands in for). Item j of `count`:
+ *     item[i_1..i_d] = sum_{q < terms} prod_{m < d} f_qm(i_m) + noise_std * z_j(e),
+ *     f_qm(i) = sum_{k <= degree} coeffs[j][q][m][k] T_k(x_i),  x_i = -1 + 2 i / (n - 1),
+ * T_k the Chebyshev polynomials and e the element's C-order index within the item. z is a
+ * counter-based standard normal: with b = mix64(seed * 2^32 + first_item + j) and word w_k =
+ * mix64(b + (k + 1) * 0x9E3779B97F4A7C15) (SplitMix64's output function mix64; Steele, Lea and
+ * Flood, OOPSLA 2014), u1 = (bits 40..63 of w_k + 1/2) / 2^24, u2 = (bits 8..31 + 1/2) / 2^24,
+ * z(2k) = sqrt(-2 ln u1) cos(2 pi u2) and z(2k + 1) = sqrt(-2 ln u1) sin(2 pi u2), evaluated in FP32.
+ * coeffs: FP64 [count][terms][d][degree + 1], host or device; out: fp32 device
+ * [count][n]^d, item-major. 1 <= n <= 64, 2 <= d <= 8, 1 <= terms <= 64, 0 <= degree <= 32,
+ * count <= 65535 (0 does nothing); BHT_EINVAL otherwise or when out is not device memory.
+ * Asynchronous on `stream` for device coefficients; host coefficients are copied and the call
+ * synchronises `stream`. */
+bht_status bht_synth_chebyshev(const double* coeffs, int64_t count, int32_t n, int32_t d, int32_t terms,
+                               int32_t degree, double noise_std, uint64_t seed, int64_t first_item, float* out,
+                               void* stream);
+
 /* Latent representation of N unseen items on the current cores (Step 1 of
  * Algorithm 2), written item-major [N][r_11][r_12] as FP64 into `out`
  * (device or host). N = 0 does nothing; N < 0 is BHT_EINVAL. Never modifies the
@@ -247,7 +268,9 @@ bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const doubl
  * memory during the call, e.g. when another allocator owns the GPU's memory or
  * in a latency-critical loop where cudaMalloc / cudaFree could synchronise).
  * Same operation and arguments as bht_mode_product with precision
- * BHT_PREC_MIXED; X, U, out and norms are the caller's device buffers. The
+ * BHT_PREC_MIXED; X, U, out and norms are the caller's device buffers (a
+ * host pointer is BHT_EINVAL, found by a pointer-attribute query that
+ * allocates nothing). The
  * scratch (split TF32 weight planes and a status word, 1 MiB + 256 B) is a
  * file-scope device array that every GPU loading the library holds until the
  * process exits; it limits K <= 512 and S <= 256 (BHT_ECAPACITY beyond) and

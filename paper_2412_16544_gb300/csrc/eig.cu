@@ -491,9 +491,10 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
 // factorisations of T - lambda I, the twist index k minimising
 // |gamma_k| = |D+_k + D-_k - (d_k - lambda)| gives the eigenvector from
 // z_k = 1 and two one-sided recurrences. One lane per eigenvalue; inside a
-// cluster (a chain of eigenvalues closer than ctol) the shifts are spread by
-// 10 eps ||T|| per member so the members differ, and cluster_orth_kernel
-// then orthogonalises each cluster.
+// chain of numerically equal eigenvalues (gaps within 10 eps ||T||) the
+// shifts are spread by 10 eps ||T|| per member so the members differ, and
+// cluster_orth_kernel then orthogonalises each cluster (a chain of
+// eigenvalues closer than ctol = 1e-9 ||T||).
 // Z[i * r + j] receives component i of eigenvector j of T.
 // Scratch: 4 n r doubles.
 // ---------------------------------------------------------------------------
@@ -521,7 +522,6 @@ __global__ void __launch_bounds__(64) invit_kernel(const double* dg, const doubl
   const int j = blockIdx.x * 32 + lane;
   const bool act = j < r;
   const double tnorm = fmax(fabs(lam[0]), fabs(lam[n - 1])) + DBL_MIN;
-  const double ctol = cluster_tol(lam, n);
   const double tiny = 1e-3 * DBL_EPSILON * tnorm + DBL_MIN;
   // scratch [4][n][r]: D+, L+, D-, U- with the eigenvalue index innermost (coalesced per step)
   const int64_t R = r;
@@ -531,9 +531,13 @@ __global__ void __launch_bounds__(64) invit_kernel(const double* dg, const doubl
   double* Um = scratch + 3 * (int64_t)n * R + j;
   double s = 0.0;
   if (act) {
+    // the shift offset counts members of the chain of numerically equal eigenvalues only (gaps within
+    // 10 eps ||T||): spread over a whole 1e-9 ||T|| chain it would grow past the local gaps and move
+    // later members onto their neighbours' eigenvalues
+    const double etol = 10.0 * DBL_EPSILON * tnorm;
     int lead = j;
-    while (lead > 0 && fabs(lam[lead - 1] - lam[lead]) <= ctol) --lead;
-    s = lam[j] + (double)(j - lead) * 10.0 * DBL_EPSILON * tnorm;
+    while (lead > 0 && fabs(lam[lead - 1] - lam[lead]) <= etol) --lead;
+    s = lam[j] + (double)(j - lead) * etol;
     if (half == 0) {
       double dp = d[0] - s;
       for (int i = 0; i + 1 < n; ++i) {

@@ -41,6 +41,17 @@ bht_status set_error(bht_status st, const char* msg) {
   return st;
 }
 
+// Device (or managed) memory, by the pointer's attributes: a query that allocates nothing. A host
+// pointer handed to the tensor map or to the kernels would be a fault instead of an error code.
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" bht_status bht_mode_product_noalloc(const float* X, int64_t rows, int64_t K, const double* U, int64_t S,
@@ -49,6 +60,8 @@ extern "C" bht_status bht_mode_product_noalloc(const float* X, int64_t rows, int
   if (rows < 1 || K < 1 || S < 1 || R2 < 1 || rows % R2 != 0)
     return set_error(BHT_EINVAL, "bad sizes (rows must be a multiple of R2)");
   if (K % 4 != 0) return set_error(BHT_EINVAL, "K must be a multiple of 4 (tensor-map row pitch)");
+  if (!on_device(X) || !on_device(U) || !on_device(out) || (norms && !on_device(norms)))
+    return set_error(BHT_EINVAL, "bht_mode_product_noalloc takes device pointers (X, U, out, norms)");
   if (K > NOALLOC_MAX_K || S > NOALLOC_MAX_S)
     return set_error(BHT_ECAPACITY, "bht_mode_product_noalloc: K > 512 or S > 256 exceeds its static scratch");
   int dev = 0;
