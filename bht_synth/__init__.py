@@ -20,7 +20,12 @@ simulations and cyber-physical sensor streams), which are not available here:
 * ``multivar_field``   — 5 variables x 48^3 from the same spectral generator,
   independent phases per variable and a per-variable scale in U(0.1, 10).
 * ``chebyshev_sensor`` — 24^5 items, sums of 20 separable products of random
-  Chebyshev series of degree <= 6 plus 0.01 N(0, 1) noise.
+  Chebyshev series of degree <= 6 plus 0.01 N(0, 1) noise. The noise comes from
+  a counter-based generator (SplitMix64 words, Box-Muller) so that the device
+  generator of the library can draw the same stream at HBM rate.
+* ``graded_stream``    — two-way items whose mode-1 unfolding has singular
+  values graded geometrically over many decades (a numerical stress case for
+  tight tolerances, not a stand-in for a data set).
 """
 from __future__ import annotations
 
@@ -33,6 +38,9 @@ __all__ = [
     "chebyshev_sensor",
     "increment_sizes",
     "halfspace_wavevectors",
+    "graded_stream",
+    "chebyshev_coefficients",
+    "counter_normals",
 ]
 
 
@@ -169,21 +177,64 @@ def _chebyshev_basis(n: int, degree: int) -> np.ndarray:
     return T
 
 
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """The output function of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): a bijective mix of
+    64-bit words by two xor-shift-multiply steps and a final xor-shift (wrapping uint64 arithmetic)."""
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_normals(seed: int, item: int, count: int) -> np.ndarray:
+    """Standard normal draws 0 .. count-1 of one item, float64, from a counter-based generator that a
+    device kernel can evaluate element by element.
+
+    The item's base word is b = mix64(seed * 2^32 + item); word k is mix64(b + (k + 1) * gamma), the k-th
+    output of a SplitMix64 sequence started at b (gamma = 0x9E3779B97F4A7C15). Word k gives draws 2k and
+    2k + 1 by the Box-Muller transform: u1 from its bits 40..63 and u2 from its bits 8..31, each
+    (integer + 1/2) / 2^24, then sqrt(-2 ln u1) cos(2 pi u2) and sqrt(-2 ln u1) sin(2 pi u2).
+    """
+    with np.errstate(over="ignore"):
+        b = _mix64(np.array([(int(seed) << 32) + int(item)], dtype=np.uint64))[0]
+        k = np.arange((count + 1) // 2, dtype=np.uint64)
+        w = _mix64(b + (k + np.uint64(1)) * _GAMMA)
+    u1 = ((w >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    u2 = (((w >> np.uint64(8)) & np.uint64(0xFFFFFF)).astype(np.float64) + 0.5) * 2.0 ** -24
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * len(k))
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return z[:count]
+
+
+def chebyshev_coefficients(seed: int, first: int, count: int, d: int = 5, terms: int = 20,
+                           degree: int = 6) -> np.ndarray:
+    """The random coefficients c_{qmj} ~ N(0, 1) of items first .. first+count-1 of the Chebyshev
+    sensor stream, float64 [count, terms, d, degree + 1] (item m drawn from default_rng([seed, m]))."""
+    out = np.empty((count, terms, d, degree + 1))
+    for j in range(count):
+        out[j] = _item_rng(seed, first + j).normal(size=(terms, d, degree + 1))
+    return out
+
+
 def chebyshev_sensor(seed: int, first: int, count: int, n: int = 24, d: int = 5,
                      terms: int = 20, degree: int = 6, noise_std: float = 0.01,
                      dtype=np.float32) -> np.ndarray:
     """Items of the Chebyshev sensor stream, [count] + [n] * d.
 
     item = sum_{q=1..terms} prod_{m=1..d} (sum_{j=0..degree} c_{qmj} T_j(x_m))
-           + noise_std * N(0, 1),  c ~ N(0, 1).
+           + noise_std * z,  c ~ N(0, 1) (chebyshev_coefficients), z the counter-based standard
+    normal draws of counter_normals in C order of the item's elements; x on n uniform points of [-1, 1].
     """
     T = _chebyshev_basis(n, degree)
     out = np.empty((count,) + (n,) * d, dtype=dtype)
     h = (d + 1) // 2
+    coeffs = chebyshev_coefficients(seed, first, count, d, terms, degree)
     for j in range(count):
-        rng = _item_rng(seed, first + j)
-        c = rng.normal(size=(terms, d, degree + 1))
-        f = np.einsum("qmj,jn->qmn", c, T)  # [terms, d, n]
+        f = np.einsum("qmj,jn->qmn", coeffs[j], T)  # [terms, d, n]
         # the sum of separable products as (Khatri-Rao of the first h modes)^T x (of the rest)
         left = np.ones((terms, 1))
         for m in range(h):
@@ -193,6 +244,33 @@ def chebyshev_sensor(seed: int, first: int, count: int, n: int = 24, d: int = 5,
             right = (right[:, :, None] * f[:, m, None, :]).reshape(terms, -1)
         item = (left.T @ right).reshape((n,) * d)
         if noise_std:
-            item += noise_std * rng.standard_normal(size=item.shape)
+            item += noise_std * counter_normals(seed, first + j, item.size).reshape(item.shape)
         out[j] = item
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Graded spectrum: a numerical stress stream for tight tolerances
+# ---------------------------------------------------------------------------
+
+def graded_stream(seed: int, n1: int = 400, n2: int = 6, N: int = 48, rank: int = 288,
+                  decades: float = 6.0, offsets=(0, 112, 50)) -> list:
+    """Batches of two-way items [N, n1, n2], float64, one per entry of ``offsets``.
+
+    A fixed random orthonormal basis P of R^{n1} is drawn once per stream. In batch k the
+    mode-1 unfolding [n1, N * n2] equals P[:, o_k .. o_k + rank - 1] diag(s) W_k^T, with
+    s_i = 10^(-decades * i / (rank - 1)) and W_k random with orthonormal columns, so its
+    singular values are exactly s: the Gram spectrum spans 2 * decades decades and the
+    eigenvalues below 1e-9 of the largest are many and closely spaced.
+    """
+    rng = np.random.default_rng([int(seed), 7_000_003])
+    P = np.linalg.qr(rng.normal(size=(n1, n1)))[0]
+    s = 10.0 ** (-decades * np.arange(rank) / max(rank - 1, 1))
+    out = []
+    for o in offsets:
+        if o + rank > n1:
+            raise ValueError("offset + rank exceeds n1")
+        W = np.linalg.qr(rng.normal(size=(N * n2, rank)))[0]
+        M = (P[:, o:o + rank] * s) @ W.T
+        out.append(np.ascontiguousarray(M.reshape(n1, N, n2).transpose(1, 0, 2)))
     return out

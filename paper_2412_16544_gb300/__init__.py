@@ -87,6 +87,7 @@ def _load():
         "bht_mlp_loss_grad": [vp, vp, vp, i64, P(dbl), vp],
         "bht_mlp_adam_step": [vp, dbl, vp],
         "bht_sketch_features": [vp, i64, dbl, dbl, ctypes.c_uint64, vp, vp],
+        "bht_synth_chebyshev": [vp, i64, i32, i32, i32, i32, dbl, ctypes.c_uint64, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -108,7 +109,8 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
             "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode", "ht_l2r",
-            "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items"]
+            "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items",
+            "bht_synth_chebyshev"]
 KERNEL_CLASSES = 16
 
 
@@ -433,9 +435,22 @@ def bht_mode_product(X, U, S: int, precision="mixed", R2: int = 1, out=None, nor
 
 def bht_mode_product_noalloc(X, U, S: int, R2: int = 1, out=None, norms=None, stream=None):
     """bht_mode_product (tensor cores) with the library allocating nothing: out must be given by the caller."""
-    rows, K = X.shape
+    torch = _torch()
     if out is None:
         raise ValueError("bht_mode_product_noalloc writes into a caller-owned output")
+    if X.dim() != 2:
+        raise ValueError("X must be [rows, K]")
+    rows, K = X.shape
+    for name, t, dt in (("X", X, torch.float32), ("U", U, torch.float64), ("out", out, torch.float32)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor")
+    if U.dim() != 2 or U.shape[0] != K or U.shape[1] != S:
+        raise ValueError(f"U must be [{K}, {S}]")
+    if out.numel() < rows * S:
+        raise ValueError(f"out holds {out.numel()} elements, the product needs {rows * S}")
+    if norms is not None and not (norms.is_cuda and norms.dtype == torch.float64 and norms.is_contiguous()
+                                  and norms.numel() >= 2):
+        raise ValueError("norms must be a contiguous float64 CUDA tensor of at least 2 elements")
     nptr = ctypes.c_void_p(norms.data_ptr()) if norms is not None else None
     _check(_lib.bht_mode_product_noalloc(ctypes.c_void_p(X.data_ptr()), rows, K, ctypes.c_void_p(U.data_ptr()),
                                          int(S), ctypes.c_void_p(out.data_ptr()), int(R2), nptr, _stream(stream)),
@@ -549,3 +564,23 @@ def bht_sketch_features(G, tol: float, norm: float, seed: int = 0, stream=None) 
                                     ctypes.c_void_p(f.ctypes.data), _stream(stream)), "bht_sketch_features")
     del keep
     return f
+
+
+def bht_synth_chebyshev(coeffs, n: int, seed: int, first_item: int, noise_std: float = 0.01, out=None,
+                        stream=None):
+    """Items of the Chebyshev sensor stream drawn on the device from coefficients [count, terms, d, degree + 1]
+    (float64, host or device); returns (or fills) a float32 CUDA tensor [count] + [n] * d."""
+    torch = _torch()
+    ptr, code, shape, keep = _buffer(coeffs)
+    if code != BHT_F64 or len(shape) != 4:
+        raise ValueError("coefficients are float64 [count, terms, d, degree + 1]")
+    count, terms, d, deg1 = (int(x) for x in shape)
+    if out is None:
+        out = torch.empty((count,) + (n,) * d, dtype=torch.float32, device="cuda")
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == count * n ** d):
+        raise ValueError(f"out must be a contiguous float32 CUDA tensor of {count * n ** d} elements")
+    _check(_lib.bht_synth_chebyshev(ptr, count, int(n), d, terms, deg1 - 1, float(noise_std), int(seed),
+                                    int(first_item), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "bht_synth_chebyshev")
+    del keep
+    return out

@@ -898,15 +898,27 @@ double cross_error(const double* V, int64_t r0, const double* X, int64_t k, int6
 }
 
 // Newton-Schulz steps until the estimated orthonormality error is below 1e-12 (none when the
-// columns already are orthonormal to that level; at most max_iters).
+// columns already are orthonormal to that level; at most max_iters). When steps ran, the result is
+// probed again: columns still further than 1e-10 from orthonormal fail with BHT_ENUMERIC, so a basis
+// that is not orthonormal never reaches a truncation or a projection.
 void orthonormalise(double* X, int64_t rows, int64_t r, cudaStream_t s, int max_iters) {
-  double e = orth_error(X, rows, r, s);
+  const double e0 = orth_error(X, rows, r, s);
+  double e = e0;
   int iters = 0;
   while (e > 1e-12 && iters < max_iters) {
     e = 0.75 * e * e + 1e-16;
     ++iters;
   }
+  if (iters == 0) return;
   newton_schulz(X, rows, r, s, iters);
+  const double e1 = orth_error(X, rows, r, s);
+  if (!(e1 <= 1e-10)) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "a basis of %lld columns is not orthonormal (error %.3g; %.3g before %d Newton-Schulz steps)",
+                  (long long)r, e1, e0, iters);
+    fail(BHT_ENUMERIC, msg);
+  }
 }
 
 // Stage 2: orthonormal eigenvectors of the r largest eigenvalues, [n][r] row-major, owned by the caller.

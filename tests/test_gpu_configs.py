@@ -3,8 +3,10 @@
 * multi-variable simulation stream: 5 variables x 48^3, increments of uneven sizes drawn from 1..64,
   eps = 1e-3 (a 4-mode tree {1,2},{3,4});
 * the 64^3 advected spectral field at the tight tolerance eps = 1e-4;
-* the 24^5 Chebyshev sensor stream: a few items against the oracle, and two full increments of 64
-  items (509 MB each) checked through properties that hold at any size: the error bound per
+* a two-way stream whose spectrum is graded over twelve decades, at eps = 1e-6;
+* the 24^5 Chebyshev sensor stream: a few items against the oracle, one full increment of 64 items
+  (2.04 GB) against the oracle item by item, and two full increments checked through properties
+  that hold at any size: the error bound per
   increment, orthonormal cores, leaf ranks bounded by the polynomial degree, and the decode of
   sampled items against a host contraction of the same cores.
 
@@ -129,6 +131,16 @@ def test_chebyshev_sensor_small(B, monkeypatch, precision):
     check_stream(B, monkeypatch, [Y[:3], Y[3:]], 1e-2, precision, sample_items=(0, 5))
 
 
+def test_graded_spectrum_tight_tolerance(B, monkeypatch):
+    """A mode-1 spectrum graded over twelve decades at eps = 1e-6: BHT-l2r keeps 284 of 400 directions,
+    68 of them with eigenvalues below 1e-9 of the largest and gaps near 1e-13 of it (one chain for the
+    cluster Gram-Schmidt); the first update expands the leaf by a residual of the same grading, and the
+    last batch lies in the span already kept (a skip). The tail sums at the cuts sit at least 12 % away
+    from their thresholds, so the ranks are well defined in FP64."""
+    batches = S.graded_stream(0)
+    check_stream(B, monkeypatch, batches, 1e-6, "fp64", sample_items=(0, 47, 60, 143))
+
+
 def _host_decode(B, st, dims, item):
     """One item decoded on the host in FP64 from the cores the library holds (eq. htucker_reconstruction)."""
     tree = OB.dimension_tree(dims)
@@ -147,6 +159,13 @@ def _host_decode(B, st, dims, item):
 
     a, b = tree.nodes[0].children
     return (expand(a) @ root @ expand(b).T).reshape(dims)
+
+
+def test_chebyshev_sensor_full_increment_matches_oracle(B, monkeypatch):
+    """One whole increment of the 24^5 sensor stream (64 items, 2.04 GB of fp32; 4.1 GB in the FP64 oracle),
+    mixed path against the oracle item by item: every one of the 64 items is decoded on both sides."""
+    Y = S.chebyshev_sensor(0, 0, 64)
+    check_stream(B, monkeypatch, [Y], 1e-2, "mixed", sample_items=range(64))
 
 
 def test_chebyshev_sensor_full_increments_properties(B):
