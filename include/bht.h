@@ -125,7 +125,7 @@ typedef struct {
 /* Outcome of one htrise_update call. */
 typedef struct {
   int32_t skipped;        /* 1: projection error <= eps_des, only the root grew (Algorithm 2) */
-  int32_t reserved;
+  int32_t batch_reads;    /* kernels of this call that read the whole new batch (passes over Y) */
   double eps_proj;        /* projection error of eq. relative_error_threshold (FP64: sqrt(max(||Y||^2 -
                              ||C_1||^2, 0)); mixed: square root of the energy removed on the nodes'
                              complements) */
@@ -263,6 +263,22 @@ bht_status ht_encode(const bht_state* state, const void* Y, int32_t dtype, int64
 bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S,
                             int32_t precision, float* out, int64_t R2, double* norms, void* stream);
 
+/* The two-mode passes of the small leaves (eq. ht_leaf_svd through Gram matrices, and eq.
+ * ht_leaf_contraction / Step 1 of Algorithm 2 for two modes at once), exposed for direct tests. X is
+ * fp32 device data viewed as [A][na][nb][B] (B contiguous, B % 4 == 0, X 16-byte aligned), read once,
+ * tile by tile, through TMA.
+ * bht_pair_gram: Ga (na x na) and Gb (nb x nb), FP64 device, receive the Gram matrices of the two
+ *   mode unfoldings, G_a = X_(a) X_(a)^T and G_b = X_(b) X_(b)^T (FP32 products and partial sums
+ *   folded into FP64). na, nb <= 24.
+ * bht_pair_project: out[A][ra][rb][B] (fp32 device) = X x_a Ua^T x_b Ub^T with Ua [na][ra] and
+ *   Ub [nb][rb] FP64 device bases (row-major); norms (nullable, 3 FP64 device values) receives
+ *   ||X||^2, ||out||^2 and their difference added in FP64. na, nb <= 32, ra, rb <= 16.
+ * Shapes outside these limits give BHT_EUNSUPPORTED. Both synchronise `stream`. */
+bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, double* Ga, double* Gb,
+                         void* stream);
+bht_status bht_pair_project(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, const double* Ua,
+                            int64_t ra, const double* Ub, int64_t rb, float* out, double* norms, void* stream);
+
 /* bht_mode_product without any device allocation (the paper has no
  * counterpart: this is an interface for callers that may not allocate device
  * memory during the call, e.g. when another allocator owns the GPU's memory or
@@ -306,6 +322,25 @@ bht_status bht_state_destroy(bht_state* state);
 /* Device kernels launched by the calling thread's library calls since the
  * last reset (a plain counter kept by the host side of the library). */
 bht_status bht_launch_count(int64_t* count, int32_t reset);
+
+/* Kernels launched by the calling thread's compression calls (bht_l2r, ht_l2r, htrise_update) that
+ * read the call's whole input batch, since the last reset: the number of passes over the data. */
+bht_status bht_batch_reads(int64_t* count, int32_t reset);
+
+/* Test of the timeout path (no counterpart in the paper): the next `launches` cooperative
+ * tridiagonalisations of the node eigensolver that run on more than one CTA start with CTA 0
+ * withholding its first grid-barrier arrival, and every wait of those launches gives up after
+ * `wait_ms` milliseconds (1..65535). The waiting CTAs then set the call's device status word and
+ * return, the context stays usable, and the library call that launched the eigensolve fails with
+ * BHT_ETIMEOUT (htrise_update leaves its state as it was). launches = 0 disarms. Process-wide. */
+bht_status bht_debug_withhold_barrier(int32_t launches, int32_t wait_ms);
+
+/* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA) for dtype BHT_F64 or
+ * BHT_F32: a launch of independent FMA chains on every SM, about 10 ms at the nominal rate, timed
+ * with CUDA events on `stream` after a warm-up launch. This is the denominator of the ALU rooflines
+ * of the FP64 node linear algebra and of the FP32 SIMT kernels (the paper has no counterpart).
+ * Synchronises `stream`. */
+bht_status bht_probe_fma_rate(int32_t dtype, double* tflops, void* stream);
 
 /* Optional kernel timing. With bit c of class_mask set, every launch of
  * kernel class c made by the calling thread is bracketed by a CUDA event pair

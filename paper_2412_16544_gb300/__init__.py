@@ -40,7 +40,7 @@ class _Opts(ctypes.Structure):
 
 
 class _Info(ctypes.Structure):
-    _fields_ = [("skipped", ctypes.c_int32), ("reserved", ctypes.c_int32), ("eps_proj", ctypes.c_double),
+    _fields_ = [("skipped", ctypes.c_int32), ("batch_reads", ctypes.c_int32), ("eps_proj", ctypes.c_double),
                 ("eps_des", ctypes.c_double), ("norm_y", ctypes.c_double), ("n_items_total", ctypes.c_int64),
                 ("pred_nodes", ctypes.c_int32), ("pred_skipped", ctypes.c_int32), ("pred_fallback", ctypes.c_int32),
                 ("pred_missed", ctypes.c_int32)]
@@ -68,6 +68,8 @@ def _load():
         "bht_num_elements": [vp, P(i64)],
         "bht_state_destroy": [vp],
         "bht_launch_count": [P(i64), i32],
+        "bht_batch_reads": [P(i64), i32],
+        "bht_debug_withhold_barrier": [i32, i32],
         "bht_profile_enable": [ctypes.c_uint32],
         "bht_mode_product": [vp, i64, i64, vp, i64, i32, vp, i64, vp, vp],
         "bht_sym_eig": [vp, i64, vp, vp, i64, vp],
@@ -88,6 +90,9 @@ def _load():
         "bht_mlp_adam_step": [vp, dbl, vp],
         "bht_sketch_features": [vp, i64, dbl, dbl, ctypes.c_uint64, vp, vp],
         "bht_synth_chebyshev": [vp, i64, i32, i32, i32, i32, dbl, ctypes.c_uint64, i64, vp, vp],
+        "bht_probe_fma_rate": [i32, P(dbl), vp],
+        "bht_pair_gram": [vp, i64, i64, i64, i64, vp, vp, vp],
+        "bht_pair_project": [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -110,7 +115,8 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
             "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode", "ht_l2r",
             "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items",
-            "bht_synth_chebyshev"]
+            "bht_synth_chebyshev", "bht_probe_fma_rate", "bht_pair_gram", "bht_pair_project", "bht_batch_reads",
+            "bht_debug_withhold_barrier"]
 KERNEL_CLASSES = 16
 
 
@@ -197,6 +203,7 @@ class UpdateInfo:
     pred_skipped: int = 0
     pred_fallback: int = 0
     pred_missed: int = 0
+    batch_reads: int = 0
 
 
 def bht_tree_create_balanced(dims) -> ctypes.c_void_p:
@@ -251,7 +258,7 @@ def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predict
                               ctypes.byref(info)), "htrise_update")
     del keep
     return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total,
-                      info.pred_nodes, info.pred_skipped, info.pred_fallback, info.pred_missed)
+                      info.pred_nodes, info.pred_skipped, info.pred_fallback, info.pred_missed, info.batch_reads)
 
 
 def bht_get_dims(state):
@@ -419,6 +426,19 @@ def bht_launch_count(reset: bool = False) -> int:
     return n.value
 
 
+def bht_batch_reads(reset: bool = False) -> int:
+    """Kernels of this thread's compression calls that read a whole input batch, since the last reset."""
+    n = ctypes.c_int64()
+    _check(_lib.bht_batch_reads(ctypes.byref(n), 1 if reset else 0), "bht_batch_reads")
+    return n.value
+
+
+def bht_debug_withhold_barrier(launches: int, wait_ms: int = 20) -> None:
+    """Arm the timeout-path test: the next `launches` multi-CTA tridiagonalisations withhold one grid-barrier
+    arrival and give up their waits after wait_ms (the call then fails with BHT_ETIMEOUT)."""
+    _check(_lib.bht_debug_withhold_barrier(int(launches), int(wait_ms)), "bht_debug_withhold_barrier")
+
+
 def bht_mode_product(X, U, S: int, precision="mixed", R2: int = 1, out=None, norms=None, stream=None):
     """out[(o S + s) R2 + i] = sum_k X[o R2 + i, k] U[k, s] on device tensors (X fp32 [rows, K], U fp64 [K, S])."""
     torch = _torch()
@@ -458,6 +478,30 @@ def bht_mode_product_noalloc(X, U, S: int, R2: int = 1, out=None, norms=None, st
     return out
 
 
+def bht_pair_gram(X, stream=None):
+    """Gram matrices of modes 1 and 2 of a contiguous fp32 CUDA tensor X [A, na, nb, B] (one read of X)."""
+    torch = _torch()
+    A, na, nb, B = X.shape
+    Ga = torch.empty((na, na), dtype=torch.float64, device=X.device)
+    Gb = torch.empty((nb, nb), dtype=torch.float64, device=X.device)
+    _check(_lib.bht_pair_gram(ctypes.c_void_p(X.data_ptr()), A, na, nb, B, ctypes.c_void_p(Ga.data_ptr()),
+                              ctypes.c_void_p(Gb.data_ptr()), _stream(stream)), "bht_pair_gram")
+    return Ga, Gb
+
+
+def bht_pair_project(X, Ua, Ub, norms=None, stream=None):
+    """X [A, na, nb, B] x_1 Ua^T x_2 Ub^T -> [A, ra, rb, B] (fp32 CUDA X, FP64 CUDA bases)."""
+    torch = _torch()
+    A, na, nb, B = X.shape
+    ra, rb = Ua.shape[1], Ub.shape[1]
+    out = torch.empty((A, ra, rb, B), dtype=torch.float32, device=X.device)
+    nptr = ctypes.c_void_p(norms.data_ptr()) if norms is not None else None
+    _check(_lib.bht_pair_project(ctypes.c_void_p(X.data_ptr()), A, na, nb, B, ctypes.c_void_p(Ua.data_ptr()), ra,
+                                 ctypes.c_void_p(Ub.data_ptr()), rb, ctypes.c_void_p(out.data_ptr()), nptr,
+                                 _stream(stream)), "bht_pair_project")
+    return out
+
+
 def bht_sym_eig(G, r: int, stream=None):
     """Eigenvalues (descending) and the r leading eigenvectors of a symmetric fp64 CUDA tensor G (overwritten)."""
     torch = _torch()
@@ -467,6 +511,14 @@ def bht_sym_eig(G, r: int, stream=None):
     _check(_lib.bht_sym_eig(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
                             ctypes.c_void_p(U.data_ptr()), int(r), _stream(stream)), "bht_sym_eig")
     return lam, U[:, :r]
+
+
+def bht_probe_fma_rate(dtype: str = "float64", stream=None) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s for "float64" or "float32"."""
+    v = ctypes.c_double()
+    code = BHT_F64 if dtype in ("float64", BHT_F64) else BHT_F32
+    _check(_lib.bht_probe_fma_rate(code, ctypes.byref(v), _stream(stream)), "bht_probe_fma_rate")
+    return v.value
 
 
 def bht_profile_enable(class_mask: int) -> None:

@@ -27,6 +27,19 @@
 namespace {
 thread_local std::string g_err;
 thread_local int64_t g_launches = 0;
+// the device batch of the compression call running on this thread, and the kernels that read it whole
+thread_local const void* g_batch = nullptr;
+thread_local int64_t g_batch_reads = 0;
+
+void note_read(const void* p) {
+  if (p && p == g_batch) ++g_batch_reads;
+}
+
+// Marks the batch of one compression call for the read count, for the lifetime of the call.
+struct BatchScope {
+  explicit BatchScope(const void* p) { g_batch = p; }
+  ~BatchScope() { g_batch = nullptr; }
+};
 
 struct Fail {
   bht_status st;
@@ -91,7 +104,7 @@ void prof_resolve() {
 // The thread-local counters of a worker thread (launches, per-class profile), carried back to the
 // thread that made the library call.
 struct ThreadCounters {
-  int64_t launches = 0;
+  int64_t launches = 0, batch_reads = 0;
   double ms[bht::K_NUM_CLASSES] = {}, flops[bht::K_NUM_CLASSES] = {}, bytes[bht::K_NUM_CLASSES] = {};
   int64_t n[bht::K_NUM_CLASSES] = {};
 };
@@ -101,6 +114,8 @@ ThreadCounters take_thread_counters() {
   ThreadCounters c;
   c.launches = g_launches;
   g_launches = 0;
+  c.batch_reads = g_batch_reads;
+  g_batch_reads = 0;
   for (int i = 0; i < bht::K_NUM_CLASSES; ++i) {
     c.ms[i] = g_prof_ms[i];
     c.n[i] = g_prof_n[i];
@@ -114,6 +129,7 @@ ThreadCounters take_thread_counters() {
 
 void add_thread_counters(const ThreadCounters& c) {
   g_launches += c.launches;
+  g_batch_reads += c.batch_reads;
   for (int i = 0; i < bht::K_NUM_CLASSES; ++i) {
     g_prof_ms[i] += c.ms[i];
     g_prof_n[i] += c.n[i];
@@ -488,12 +504,17 @@ std::vector<int> best_order(const std::vector<int64_t>& dims, const std::vector<
 struct Arith {
   bool mixed = false;
   bool tight = false;
+  // the two-mode FP32 SIMT passes of small leaves (pair.cu) may replace the per-mode products: their
+  // bases are rounded to FP32, which moves the projection energies of the skip test by about 2e-8 of
+  // ||Y||^2 (measured on the sensor stream), below 0.1 % of eps^2 ||Y||^2 for eps_rel >= 5e-3
+  bool pairs = false;
   int* d_status = nullptr;
 };
 
 void gram_any(const LTensor& C, int axis, double* G, const Arith& ar, cudaStream_t s) {
   int64_t A, I, B;
   C.view(axis, A, I, B);
+  note_read(C.ptr);
   ck(cudaMemsetAsync(G, 0, sizeof(double) * I * I, s), "memset gram");
   if (C.dtype == BHT_F32 && ar.mixed && !ar.tight)
     ck(launch_gram_f32(static_cast<const float*>(C.ptr), G, A, I, B, s), "gram");
@@ -548,6 +569,7 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
+  note_read(C.ptr);
   LTensor out;
   out.N = C.N;
   out.dims = C.dims;
@@ -628,6 +650,7 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
   int64_t A, T, B;
   C.view(axis, A, T, B);
   if (rotate && B != 1) fail(BHT_EINVAL, "internal: rotation of a non-innermost axis");
+  note_read(C.ptr);
   LTensor out;
   out.N = C.N;
   out.dims = C.dims;
@@ -682,6 +705,7 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
 LTensor move_axis_innermost(const LTensor& C, int ax, int64_t* k_valid, cudaStream_t s) {
   int64_t A, T, B;
   C.view(ax, A, T, B);
+  note_read(C.ptr);
   const int64_t Tp = (T + 3) / 4 * 4;
   LTensor out;
   out.dtype = BHT_F32;
@@ -1013,6 +1037,7 @@ double* complement_of(const double* V, int64_t n, int64_t r, uint64_t seed, int*
        "X^T X");
     EigOut eo;
     eig_tridiag64(M.as<double>(), k, eo, d_status, s);
+    check_status_word(d_status, s);
     ck(launch_eig_bisect(k, eo.work.p, eo.lam.as<double>(), 0, k, s), "eigenvalues");
     eo.computed = k;
     DBuf Z;
@@ -1044,6 +1069,7 @@ const void* stage_input(const void* Y, int dtype, int64_t numel, DBuf& staging, 
 }
 
 double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_t s) {
+  note_read(x);
   ck(cudaMemsetAsync(d_acc, 0, sizeof(double), s), "memset");
   if (dtype == BHT_F32)
     ck(launch_sqnorm<float>(static_cast<const float*>(x), n, d_acc, s), "sqnorm");
@@ -1064,14 +1090,52 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
   if (norm_done) *norm_done = false;
   auto qcols = [&](int id) { return st->rows(id) - st->rank[id]; };
   if (ar.mixed) {
-    for (int step = 0; step < t.d; ++step) {
-      const int ax = (int)C.dims.size() - 1;
-      const int id = C.node[ax];
-      bool used = false;
-      LTensor nxt = ttm_proj_resid(C, ax, st->U[id], st->rank[id], st->Q[id], qcols(id), true, ar, s,
-                                   step == 0 && !ar.tight ? norm_acc : nullptr, &used, resid, -1, st);
-      if (step == 0 && norm_done) *norm_done = used;
+    // small leaves two modes at a time from the outermost mode (one read of the batch for the first
+    // two); the energy each pass removes, ||in||^2 - ||out||^2, goes to the skip test's sum
+    int m0 = 0;
+    while (ar.pairs && m0 + 1 < t.d && C.dtype == BHT_F32 && (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0) {
+      const int ida = t.leaf_of_mode[m0], idb = t.leaf_of_mode[m0 + 1];
+      int64_t A = N, B = 1;
+      for (int k = 0; k < m0; ++k) A *= C.dims[k];
+      for (int k = m0 + 2; k < t.d; ++k) B *= C.dims[k];
+      const int64_t na = C.dims[m0], nb = C.dims[m0 + 1], ra = st->rank[ida], rb = st->rank[idb];
+      if (!pair_project_supported(A, na, nb, B, ra, rb)) break;
+      LTensor nxt;
+      nxt.dtype = BHT_F32;
+      nxt.N = C.N;
+      nxt.dims = C.dims;
+      nxt.node = C.node;
+      nxt.dims[m0] = ra;
+      nxt.dims[m0 + 1] = rb;
+      nxt.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(nxt.numel(), 1), s);
+      nxt.ptr = nxt.own.p;
+      note_read(C.ptr);
+      ck(launch_pair_project(static_cast<const float*>(C.ptr), A, (int)na, (int)nb, B, st->U[ida], (int)ra, (int)ra,
+                             st->U[idb], (int)rb, (int)rb, nxt.own.as<float>(), m0 == 0 ? norm_acc : nullptr, nullptr,
+                             resid, ar.d_status, s),
+         "two-mode projection");
+      if (m0 == 0 && norm_done) *norm_done = norm_acc != nullptr;
       C = std::move(nxt);
+      m0 += 2;
+    }
+    if (m0 == 0) {
+      for (int step = 0; step < t.d; ++step) {
+        const int ax = (int)C.dims.size() - 1;
+        const int id = C.node[ax];
+        bool used = false;
+        LTensor nxt = ttm_proj_resid(C, ax, st->U[id], st->rank[id], st->Q[id], qcols(id), true, ar, s,
+                                     step == 0 && !ar.tight ? norm_acc : nullptr, &used, resid, -1, st);
+        if (step == 0 && norm_done) *norm_done = used;
+        C = std::move(nxt);
+      }
+    } else {
+      // the remaining leaves one axis at a time, in place
+      for (int m = m0; m < t.d; ++m) {
+        const int id = t.leaf_of_mode[m];
+        LTensor nxt = ttm_proj_resid(C, C.axis_of(id), st->U[id], st->rank[id], st->Q[id], qcols(id), false, ar, s,
+                                     nullptr, nullptr, resid, -1, st);
+        C = std::move(nxt);
+      }
     }
   } else {
     std::vector<int> ids;
@@ -1138,6 +1202,7 @@ void run_nodes(int n, cudaStream_t s, F&& work) {
   int dev = 0;
   ck(cudaGetDevice(&dev), "cudaGetDevice");
   const uint32_t mask = g_prof_mask;
+  const void* batch = g_batch;
   cudaEvent_t ready = nullptr;
   ck(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "event");
   ck(cudaEventRecord(ready, s), "event record");
@@ -1156,6 +1221,7 @@ void run_nodes(int n, cudaStream_t s, F&& work) {
     th.emplace_back([&, k] {
       cudaSetDevice(dev);
       g_prof_mask = mask;
+      g_batch = batch;
       try {
         work(k, ss[k]);
       } catch (const Fail& f) {
@@ -1170,6 +1236,7 @@ void run_nodes(int n, cudaStream_t s, F&& work) {
       }
       cudaEventRecord(done[k], ss[k]);
       cnt[k] = take_thread_counters();
+      g_batch = nullptr;
     });
   }
   for (auto& t : th) t.join();
@@ -1245,6 +1312,7 @@ Arith make_arith(int precision, double eps_rel, int* d_status) {
   Arith ar;
   ar.mixed = precision == BHT_PREC_MIXED;
   ar.tight = eps_rel < 1e-3;
+  ar.pairs = ar.mixed && eps_rel >= 5e-3;
   ar.d_status = d_status;
   return ar;
 }
@@ -1366,6 +1434,13 @@ void decode_latent(const bht_state* st, const double* Z, int64_t count, void* ou
 extern "C" {
 
 const char* bht_last_error(void) { return g_err.c_str(); }
+
+bht_status bht_batch_reads(int64_t* count, int32_t reset) {
+  if (!count) return BHT_EINVAL;
+  *count = g_batch_reads;
+  if (reset) g_batch_reads = 0;
+  return BHT_OK;
+}
 const char* bht_version(void) { return "bht-gb300 0.1 (sm_103a)"; }
 
 bht_status bht_profile_enable(uint32_t class_mask) {
@@ -1443,6 +1518,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
   for (auto v : t.dims) total *= v;
   DBuf staging;
   const void* dY = stage_input(Y, dtype, total, staging, s);
+  BatchScope batch_scope(dY);
 
   bht_state* st = new bht_state();
   st->tree = t;
@@ -1455,18 +1531,51 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
   try {
     ck(cudaMalloc(&st->d_status, sizeof(int)), "cudaMalloc status");
     ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
+    const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
+    const bool adaptive = st->budget == BHT_BUDGET_ADAPTIVE;
+    // Sibling leaves of the deepest layer at adjacent axes (a, a + 1) whose two-mode pass applies: both
+    // Gram matrices from one read of the batch, and ||Y||^2 as the trace of the first of them.
+    struct LeafPair {
+      int ax, ida, idb;
+      int64_t A, B;
+      DBuf Ga, Gb;
+    };
+    std::vector<LeafPair> pairs;
+    if (ar.pairs && !plain && !adaptive && dtype == BHT_F32 && (reinterpret_cast<uintptr_t>(dY) & 15) == 0) {
+      for (int m = 0; m + 1 < t.d; ++m) {
+        const int ida = t.leaf_of_mode[m], idb = t.leaf_of_mode[m + 1];
+        if (t.nodes[ida].parent != t.nodes[idb].parent || t.nodes[ida].layer != t.p || t.nodes[idb].layer != t.p) continue;
+        int64_t A = N, B = 1;
+        for (int k = 0; k < m; ++k) A *= t.dims[k];
+        for (int k = m + 2; k < t.d; ++k) B *= t.dims[k];
+        if (!pair_gram_supported(A, t.dims[m], t.dims[m + 1], B)) continue;
+        LeafPair lp{m, ida, idb, A, B, DBuf(sizeof(double) * t.dims[m] * t.dims[m], s),
+                    DBuf(sizeof(double) * t.dims[m + 1] * t.dims[m + 1], s)};
+        ck(cudaMemsetAsync(lp.Ga.p, 0, sizeof(double) * t.dims[m] * t.dims[m], s), "memset");
+        ck(cudaMemsetAsync(lp.Gb.p, 0, sizeof(double) * t.dims[m + 1] * t.dims[m + 1], s), "memset");
+        note_read(dY);
+        ck(launch_pair_gram(static_cast<const float*>(dY), A, (int)t.dims[m], (int)t.dims[m + 1], B,
+                            lp.Ga.as<double>(), lp.Gb.as<double>(), st->d_status, s),
+           "two-mode Gram pass");
+        pairs.push_back(std::move(lp));
+        ++m;
+      }
+    }
     DBuf acc(sizeof(double) * 2, s);
-    sqnorm_of(dY, dtype, total, acc.as<double>(), s);
+    ck(cudaMemsetAsync(acc.p, 0, sizeof(double), s), "memset");
+    if (!pairs.empty())
+      ck(launch_trace(pairs[0].Ga.as<double>(), t.dims[pairs[0].ax], acc.as<double>(), s), "trace");
+    else
+      sqnorm_of(dY, dtype, total, acc.as<double>(), s);
     double normY2 = 0.0;
     ck(cudaMemcpyAsync(&normY2, acc.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norm");
     ck(cudaStreamSynchronize(s), "sync");
+    check_status(st, s);
     if (!std::isfinite(normY2)) fail(BHT_ENUMERIC, "the batch holds non-finite values");
     // node-wise tolerance eps_nw = eps_rel ||Y|| / sqrt(2d - 2) (Algorithm 1). The plain HT tree has d + 1
     // modes and one SVD fewer: its layer-1 nodes split one matrix, whose left and right truncations at
     // the same rank remove the same energy, hence sqrt(2 (d + 1) - 3) (Theorem ht_nodewise_error).
     double eps_nw2 = eps_rel * eps_rel * normY2 / (plain ? 2.0 * t.d - 3.0 : 2.0 * t.d - 2.0);
-    const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
-    const bool adaptive = st->budget == BHT_BUDGET_ADAPTIVE;
     DBuf removed(sizeof(double), s);
     ck(cudaMemsetAsync(removed.p, 0, sizeof(double), s), "memset");
 
@@ -1513,7 +1622,13 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         EigOut eo;
         {
           DBuf G(sizeof(double) * I * I, sk);
-          gram_any(C, ax, G.as<double>(), ark, sk);
+          const DBuf* pg = nullptr;
+          if (layer == t.p)
+            for (const LeafPair& lp : pairs) pg = (lp.ida == id) ? &lp.Ga : (lp.idb == id) ? &lp.Gb : pg;
+          if (pg)
+            ck(cudaMemcpyAsync(G.p, pg->p, sizeof(double) * I * I, cudaMemcpyDeviceToDevice, sk), "pair Gram");
+          else
+            gram_any(C, ax, G.as<double>(), ark, sk);
           eig_tridiag64(G.as<double>(), I, eo, status.as<int>(), sk);
           check_status_word(status.as<int>(), sk);
         }
@@ -1535,7 +1650,51 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         for (int id : ids) rows[id] = st->rows(id);
         C = project_layer_removed(std::move(C), ids, st->U, st->Q, st->rank, t, rows, ar, s, removed.as<double>());
       } else {
-        C = project_layer(std::move(C), ids, Us, rs, ar, s);
+        // the leaf pairs two modes at a time (pairs later in the mode order first, so that the views of
+        // the earlier ones keep their sizes), then any other node of the layer
+        std::vector<int> rest_ids;
+        std::vector<const double*> rest_Us;
+        std::vector<int64_t> rest_rs;
+        if (layer == t.p && !pairs.empty()) {
+          for (auto it = pairs.rbegin(); it != pairs.rend(); ++it) {
+            const int64_t ra = st->rank[it->ida], rb = st->rank[it->idb];
+            const int64_t na = C.dims[it->ax], nb = C.dims[it->ax + 1];
+            int64_t B = 1;
+            for (size_t k = it->ax + 2; k < C.dims.size(); ++k) B *= C.dims[k];
+            if (!pair_project_supported(it->A, na, nb, B, ra, rb) || (reinterpret_cast<uintptr_t>(C.ptr) & 15) != 0) {
+              rest_ids.push_back(it->ida);
+              rest_ids.push_back(it->idb);
+              continue;
+            }
+            LTensor nxt;
+            nxt.dtype = BHT_F32;
+            nxt.N = C.N;
+            nxt.dims = C.dims;
+            nxt.node = C.node;
+            nxt.dims[it->ax] = ra;
+            nxt.dims[it->ax + 1] = rb;
+            nxt.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(nxt.numel(), 1), s);
+            nxt.ptr = nxt.own.p;
+            note_read(C.ptr);
+            ck(launch_pair_project(static_cast<const float*>(C.ptr), it->A, (int)na, (int)nb, B, st->U[it->ida],
+                                   (int)ra, (int)ra, st->U[it->idb], (int)rb, (int)rb, nxt.own.as<float>(), nullptr,
+                                   nullptr, nullptr, st->d_status, s),
+               "two-mode projection");
+            C = std::move(nxt);
+          }
+          for (size_t k = 0; k < ids.size(); ++k) {
+            bool paired = false;
+            for (const LeafPair& lp : pairs) paired = paired || lp.ida == ids[k] || lp.idb == ids[k];
+            if (!paired) rest_ids.push_back(ids[k]);
+          }
+          for (int id : rest_ids) {
+            rest_Us.push_back(st->U[id]);
+            rest_rs.push_back(st->rank[id]);
+          }
+          if (!rest_ids.empty()) C = project_layer(std::move(C), rest_ids, rest_Us, rest_rs, ar, s);
+        } else {
+          C = project_layer(std::move(C), ids, Us, rs, ar, s);
+        }
       }
       if (adaptive && layer > 1) {
         // App. C: the rest of the budget over the truncations still to come
@@ -1616,6 +1775,8 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   for (auto v : t.dims) item *= v;
   DBuf staging;
   const void* dY = stage_input(Y, dtype, N * item, staging, s);
+  BatchScope batch_scope(dY);
+  const int64_t reads0 = g_batch_reads;
 
   // Step 1: project onto the existing cores. ||Y||^2 in FP64; the projection error of
   // eq. relative_error_threshold in FP64 as ||Y||^2 - ||C||^2 (FP64 form), or in the mixed form as the
@@ -1642,7 +1803,9 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
     copy_convert(Cbar, st->root + st->n_items * r11_old * r12_old, BHT_F64, s);
     st->n_items += N;
     ck(cudaStreamSynchronize(s), "sync");
-    if (info) *info = bht_update_info{1, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items, 0, 0, 0, 0};
+    if (info)
+      *info = bht_update_info{1, (int32_t)(g_batch_reads - reads0), eps_proj, eps_des, std::sqrt(h[0]), st->n_items,
+                              0, 0, 0, 0};
     return BHT_OK;
   }
   Cbar = LTensor();
@@ -1741,6 +1904,11 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
       } else {
         ck(cudaStreamSynchronize(s), "sync");
       }
+      // the tail rule of eq. svd_on_residual keeps nothing when the whole residual energy is within the
+      // node's budget (tail(0) = trace(R R^T) <= eps_nw^2 gives r_R = 0): no eigensolve, with or without
+      // a predictor
+      for (int k = 0; k < nn; ++k)
+        if (qc[k] > 0 && tr[k] <= eps_nw2) skip_eig[k] = 1;
       // phase 2, the nodes side by side: eigensolve, truncation and expansion
       std::mutex own_mu;
       auto own_locked = [&](double* p) {
@@ -1902,7 +2070,7 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   st->n_items += N;
   ck(cudaStreamSynchronize(s), "sync");
   if (info)
-    *info = bht_update_info{0, 0, eps_proj, eps_des, std::sqrt(h[0]), st->n_items, pstat.nodes, pstat.skipped,
+    *info = bht_update_info{0, (int32_t)(g_batch_reads - reads0), eps_proj, eps_des, std::sqrt(h[0]), st->n_items, pstat.nodes, pstat.skipped,
                             pstat.fallback, pstat.missed};
   BHT_API_END
 }
@@ -2061,6 +2229,42 @@ bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t 
   BHT_API_END
 }
 
+bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, double* Ga, double* Gb,
+                         void* stream) {
+  BHT_API_BEGIN
+  if (!X || !Ga || !Gb) fail(BHT_EINVAL, "null argument");
+  if (!pair_gram_supported(A, na, nb, B)) fail(BHT_EUNSUPPORTED, "shape outside the two-mode Gram pass");
+  if (!is_device_ptr(X) || !is_device_ptr(Ga) || !is_device_ptr(Gb)) fail(BHT_EINVAL, "device pointers required");
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) fail(BHT_EINVAL, "X must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  ck(cudaMemsetAsync(Ga, 0, sizeof(double) * na * na, s), "memset");
+  ck(cudaMemsetAsync(Gb, 0, sizeof(double) * nb * nb, s), "memset");
+  ck(launch_pair_gram(X, A, (int)na, (int)nb, B, Ga, Gb, status.as<int>(), s), "two-mode Gram pass");
+  check_status_word(status.as<int>(), s);
+  BHT_API_END
+}
+
+bht_status bht_pair_project(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, const double* Ua,
+                            int64_t ra, const double* Ub, int64_t rb, float* out, double* norms, void* stream) {
+  BHT_API_BEGIN
+  if (!X || !Ua || !Ub || !out) fail(BHT_EINVAL, "null argument");
+  if (!pair_project_supported(A, na, nb, B, ra, rb)) fail(BHT_EUNSUPPORTED, "shape outside the two-mode projection");
+  if (!is_device_ptr(X) || !is_device_ptr(Ua) || !is_device_ptr(Ub) || !is_device_ptr(out) ||
+      (norms && !is_device_ptr(norms)))
+    fail(BHT_EINVAL, "device pointers required");
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) fail(BHT_EINVAL, "X must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  ck(launch_pair_project(X, A, (int)na, (int)nb, B, Ua, (int)ra, (int)ra, Ub, (int)rb, (int)rb, out,
+                         norms, norms ? norms + 1 : nullptr, norms ? norms + 2 : nullptr, status.as<int>(), s),
+     "two-mode projection");
+  check_status_word(status.as<int>(), s);
+  BHT_API_END
+}
+
 bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S, int32_t precision,
                             float* out, int64_t R2, double* norms, void* stream) {
   BHT_API_BEGIN
@@ -2104,6 +2308,7 @@ bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, 
   ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
   EigOut eo;
   eig_values64(G, n, eo, status.as<int>(), s);
+  check_status_word(status.as<int>(), s);  // a tridiagonalisation that gave up leaves no valid T
   ck(cudaMemcpyAsync(lam, eo.lam.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s), "copy");
   if (r > 0) {
     DBuf Ur;

@@ -429,6 +429,48 @@ __global__ void sqnorm_kernel(const T* __restrict__ x, int64_t n, double* __rest
   }
 }
 
+// ||x||^2 of fp32 data at the FP32 rate with FP64-class accuracy: each square is split exactly into
+// p + e (p = x*x rounded, e = fma(x, x, -p)) and added to a double-single accumulator (hi, lo) by
+// Knuth's TwoSum, so the FP64 units (1/64 of the FP32 rate here) only see one value per thread.
+__device__ __forceinline__ void ds_add_sq(float x, float& hi, float& lo) {
+  const float p = x * x;
+  const float e = fmaf(x, x, -p);
+  const float s = hi + p;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (p - bp);
+  hi = s;
+  lo += err + e;
+}
+
+__global__ void sqnorm_f32_kernel(const float* __restrict__ x, int64_t n, double* __restrict__ acc) {
+  float hi = 0.f, lo = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // scalar head up to a 16-byte boundary, float4 body, scalar tail
+  const int64_t head = std::min<int64_t>(n, (int64_t)(((16 - (reinterpret_cast<uintptr_t>(x) & 15)) & 15) / 4));
+  if (tid < head) ds_add_sq(x[tid], hi, lo);
+  const int64_t n4 = (n - head) / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x + head);
+  for (int64_t i = tid; i < n4; i += stride) {
+    const float4 v = x4[i];
+    ds_add_sq(v.x, hi, lo);
+    ds_add_sq(v.y, hi, lo);
+    ds_add_sq(v.z, hi, lo);
+    ds_add_sq(v.w, hi, lo);
+  }
+  for (int64_t i = head + 4 * n4 + tid; i < n; i += stride) ds_add_sq(x[i], hi, lo);
+  double s = (double)hi + (double)lo;
+  __shared__ double red[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+  }
+}
+
 __global__ void trace_kernel(const double* __restrict__ G, int64_t n, double* __restrict__ acc) {
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += G[i * n + i];
@@ -655,7 +697,10 @@ template <typename T>
 cudaError_t launch_sqnorm(const T* x, int64_t n, double* acc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   ProfScope prof(K_NORM, s, 2.0 * (double)n, (double)sizeof(T) * (double)n);
-  sqnorm_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, acc);
+  if constexpr (sizeof(T) == 4)
+    sqnorm_f32_kernel<<<grid_for((n + 3) / 4, 256, 152 * 8), 256, 0, s>>>(x, n, acc);
+  else
+    sqnorm_kernel<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, n, acc);
   note_launch();
   return cudaGetLastError();
 }

@@ -19,10 +19,12 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdlib>
+#include <atomic>
 #include <mutex>
 #include <vector>
 #include <cmath>
 
+#include "bht.h"
 #include "internal.cuh"
 #include "sync.cuh"
 
@@ -176,6 +178,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
   const int nb = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned int epoch = 0;  // barriers passed (grid_barrier_count)
+  const unsigned int bflags = (threadIdx.x == 0) ? bar->flags : 0u;  // test hooks of the barrier (zero normally)
   for (int l = 0; l < rpb; ++l) {
     const int gi = b + l * nb;
     if (gi >= n) break;
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
     if (gi == 1)
       for (int c = 1 + lane; c < n; c += 32) pub[n + c] = r[c];
   }
-  if (!grid_barrier_count(bar, epoch, status)) return;
+  if (!grid_barrier_count(bar, epoch, status, bflags)) return;
 
   for (int t = 0; t + 2 < n; ++t) {
     const int m = n - t - 1;  // length of v_t; index q <-> column t + 1 + q
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_rows_kernel(const double*
       if (gi == n - 1 && m1 < 2 && lane == 0) d[n - 1] = r[n - 1];
     }
     tc = tn;
-    if (!grid_barrier_count(bar, epoch, status)) return;
+    if (!grid_barrier_count(bar, epoch, status, bflags)) return;
   }
   if (b == 0 && threadIdx.x == 0) {
     e[n - 1] = 0.0;
@@ -713,6 +716,31 @@ size_t eig_vectors_scratch_bytes(int64_t n, int64_t r) {
 // fixed rule (at least eight rows, at most one CTA per SM) leaves those SMs free.
 // ---------------------------------------------------------------------------
 namespace {
+// Test hook of the timeout path: the next g_withhold cooperative tridiagonalisations with more than
+// one CTA run with CTA 0 withholding its first grid-barrier arrival and a wait limit of g_wait_ms.
+std::atomic<int> g_withhold{0};
+std::atomic<int> g_wait_ms{0};
+
+unsigned int take_barrier_test_flags() {
+  int n = g_withhold.load();
+  while (n > 0 && !g_withhold.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n <= 0) return 0u;
+  const unsigned int ms = (unsigned int)std::min(std::max(g_wait_ms.load(), 1), 65535);
+  return 1u | (ms << 16);
+}
+
+__global__ void set_barrier_flags_kernel(Barrier* bar, unsigned int flags) { bar->flags = flags; }
+
+// Before a multi-CTA launch of the resident-rows tridiagonalisation (its barrier word already cleared).
+cudaError_t arm_barrier_test(Barrier* bar, cudaStream_t s) {
+  const unsigned int flags = take_barrier_test_flags();
+  if (!flags) return cudaSuccess;
+  set_barrier_flags_kernel<<<1, 1, 0, s>>>(bar, flags);
+  note_launch();
+  return cudaGetLastError();
+}
+
 std::mutex g_tune_mu;
 std::vector<std::pair<int64_t, int>> g_tune;  // (device * 4096 + bucket, rows per CTA)
 
@@ -751,6 +779,10 @@ cudaError_t launch_rows(const double* G, int n, int rpb, const WorkLayout& L, in
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(L.bar, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
+  if (nbk > 1) {
+    e = arm_barrier_test(L.bar, s);
+    if (e != cudaSuccess) return e;
+  }
   int nn = n, r = rpb;
   const double* Gc = G;
   double *Vh = L.Vh, *d = L.d, *ee = L.e, *tau = L.tau, *pbuf = L.pbuf, *pub = L.pub;
@@ -860,6 +892,8 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_rows_kernel, EIG_THREADS, smr);
       if (e != cudaSuccess) return e;
       if ((int64_t)per_sm * nsm >= nbk) {
+        e = arm_barrier_test(L.bar, s);
+        if (e != cudaSuccess) return e;
         void* args[] = {&Gc, &nn, &r, &L.Vh, &L.d, &L.e, &L.tau, &L.pbuf, &L.pub, &L.bar, &status};
         e = cudaLaunchCooperativeKernel((void*)tridiag_rows_kernel, dim3(nbk), dim3(EIG_THREADS), args, smr, s);
         note_launch();
@@ -968,3 +1002,13 @@ cudaError_t launch_eig_vectors(int64_t n, int64_t r, const double* lam, double* 
 }
 
 }  // namespace bht
+
+extern "C" bht_status bht_debug_withhold_barrier(int32_t launches, int32_t wait_ms) {
+  if (launches < 0 || wait_ms < 1 || wait_ms > 65535) {
+    bht::set_last_error("launches >= 0 and 1 <= wait_ms <= 65535");
+    return BHT_EINVAL;
+  }
+  bht::g_wait_ms.store(wait_ms);
+  bht::g_withhold.store(launches);
+  return BHT_OK;
+}

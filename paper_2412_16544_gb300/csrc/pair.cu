@@ -1,0 +1,847 @@
+// pair.cu — single-read passes over two adjacent modes (a, b) of a layer intermediate viewed as
+// X[A][na][nb][B] (B contiguous, fp32), for the small leaves of a dimension tree:
+//
+//   pair_gram    : G_a = X_(a) X_(a)^T and G_b = X_(b) X_(b)^T, the Gram matrices of both mode
+//                  unfoldings (the error-truncated SVD of eq. ht_leaf_svd is taken through them), in
+//                  one read of X;
+//   pair_project : out[A][ra][rb][B] = X x_a U_a^T x_b U_b^T (eq. ht_leaf_contraction for both modes,
+//                  and Step 1 of Algorithm 2), with ||X||^2 and ||out||^2.
+//
+// These passes are HBM-bound (a few to twenty-five FMAs per element for leaves of at most 24 or 32
+// rows), so they run on the FP32 SIMT pipes; a tile is the full (na, nb) block for 32 consecutive
+// columns of B, staged by 3-D TMA loads with the 128-byte swizzle (conflict-free column reads) in a
+// ring of shared-memory stages (two whole tiles for the Gram pass, up to six half-tile bands for the
+// projection), by persistent CTAs (one per SM). Lanes of a warp own the 32 columns of a tile.
+//
+// Precision: products and sums in FP32 with round-to-nearest (no bias in any sum of squares); the Gram
+// pass keeps FP32 partial sums per lane and folds them into FP64 every few tiles, the projection folds
+// per-tile FP32 norms into FP64. Every TMA wait is bounded; a wait that gives up sets the status word
+// (BHT_ETIMEOUT), the CTA drains its loads in flight (again bounded) and returns.
+#include <algorithm>
+
+#include "bht.h"
+#include "internal.cuh"
+#include "tma.cuh"
+
+namespace bht {
+namespace {
+
+constexpr int PCOLS = 32;               // columns of B per tile (one swizzled 128-byte row)
+constexpr int PAIR_MAX_GRAM = 24;       // mode sizes of the Gram pass (8 x 8 blocks, <= 12 warps)
+constexpr int PAIR_MAX_PROJ = 32;       // mode sizes of the projection pass
+constexpr int PROJ_THREADS = 384;
+constexpr int GRAM_FOLD = 8;            // tiles between FP64 folds of the Gram partial sums
+constexpr uint64_t DRAIN_NS = 100000000ull;
+
+struct PairGeom {
+  int64_t A, B, ncb, ntiles;
+  int na, nb;
+  uint32_t tile_bytes;   // na * nb * 128
+  uint32_t stage_bytes;  // tile_bytes rounded up to 1024
+};
+
+__device__ __forceinline__ float tile_at(const uint8_t* T, uint32_t row, uint32_t c) {
+  return *reinterpret_cast<const float*>(T + tma::sw128_offset(row, c));
+}
+
+__device__ __forceinline__ void issue_tile(const CUtensorMap* map, uint64_t* bar, uint8_t* buf, const PairGeom& g,
+                                           int64_t t) {
+  const int64_t a = t / g.ncb, cb = t - a * g.ncb;
+  tma::mbar_expect_tx(bar, g.tile_bytes);
+  tma::load_3d(map, bar, buf, (int)(cb * PCOLS), 0, (int)(a * g.na));
+}
+
+// After a failed wait: wait (bounded, ignoring the status word) for the loads this CTA still has in
+// flight, so that no copy lands in shared memory after the CTA has left.
+__device__ void drain_loads(uint64_t* full, const int64_t* issued, int64_t done0, int64_t done1) {
+  const int64_t done[2] = {done0, done1};
+  for (int s = 0; s < 2; ++s) {
+    for (int64_t n = done[s]; n < issued[s]; ++n) {
+      const uint32_t par = (uint32_t)(n & 1);
+      const uint64_t t0 = tma::gtimer();
+      uint32_t ok = 0;
+      while (!ok && tma::gtimer() - t0 < DRAIN_NS) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tma::smem_u32(&full[s])), "r"(par)
+            : "memory");
+      }
+      if (!ok) return;
+    }
+  }
+}
+
+__device__ __forceinline__ double block_sum2(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < nw) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid on thread 0
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projection of both modes. The unit of work is a band of ka rows of mode a (ka = ceil(na / 2) for
+// na >= 16, else na) of one tile, staged NST units deep. Stage 1: Z[i][b][c] = sum_j T[i][j][c] Ub[j][b]
+// (one thread per (i, c)). Stage 2: W[a][b][c] += sum_i Ua[i][a] Z[i][b][c] (one thread per (b, c),
+// accumulated in registers over the bands of a tile), stored after the last band with the 32 lanes of
+// a warp on 32 consecutive columns.
+// ---------------------------------------------------------------------------------------------
+constexpr int PROJ_STAGES_MAX = 6;
+
+struct ProjGeom {
+  int ka, nbands, nst;
+  uint32_t unit_bytes, stage_bytes;
+};
+
+__device__ __forceinline__ void issue_band(const CUtensorMap* map, uint64_t* bar, uint8_t* buf, const PairGeom& g,
+                                           const ProjGeom& pg, int64_t u) {
+  const int64_t t = u / pg.nbands;
+  const int band = (int)(u - t * pg.nbands);
+  const int64_t a = t / g.ncb, cb = t - a * g.ncb;
+  tma::mbar_expect_tx(bar, pg.unit_bytes);
+  tma::load_3d(map, bar, buf, (int)(cb * PCOLS), 0, (int)(a * g.na + band * pg.ka));
+}
+
+template <int RA, int RB>
+__global__ void __launch_bounds__(PROJ_THREADS, 1)
+    pair_project_kernel(const __grid_constant__ CUtensorMap map, const PairGeom g, const ProjGeom pg,
+                        const double* __restrict__ Ua, int ra, int lda, const double* __restrict__ Ub, int rb,
+                        int ldb, float* __restrict__ out, double* norm_in, double* norm_out, double* resid,
+                        int* status) {
+  extern __shared__ __align__(1024) uint8_t psm[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(psm) + 1023) & ~(uintptr_t)1023);
+  float* Z = reinterpret_cast<float*>(base + (size_t)pg.nst * pg.stage_bytes);  // [ka][RB][32]
+  float* Uas = Z + (size_t)pg.ka * RB * PCOLS;                                   // [na][RA]
+  float* Ubs = Uas + (size_t)g.na * RA;                                          // [nb][RB]
+  __shared__ __align__(8) uint64_t full[PROJ_STAGES_MAX];
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < g.na * RA; e += blockDim.x) {
+    const int i = e / RA, a = e - i * RA;
+    Uas[e] = a < ra ? (float)Ua[(int64_t)i * lda + a] : 0.f;
+  }
+  for (int e = tid; e < g.nb * RB; e += blockDim.x) {
+    const int j = e / RB, b = e - j * RB;
+    Ubs[e] = b < rb ? (float)Ub[(int64_t)j * ldb + b] : 0.f;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < pg.nst; ++s) tma::mbar_init(&full[s], 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  // this CTA's units: the bands of its tiles t = blockIdx.x + k * gridDim.x, in order
+  const int64_t G = gridDim.x;
+  const int64_t my_tiles = (g.ntiles > blockIdx.x) ? (g.ntiles - 1 - blockIdx.x) / G + 1 : 0;
+  const int64_t my_units = my_tiles * pg.nbands;
+  auto unit_id = [&](int64_t k) { return (blockIdx.x + (k / pg.nbands) * G) * pg.nbands + k % pg.nbands; };
+  int64_t issued = 0;
+  if (tid == 0)
+    for (; issued < my_units && issued < pg.nst; ++issued)
+      issue_band(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg, unit_id(issued));
+  double sx = 0.0, sy = 0.0;
+  float acc2[2][RA];  // stage 2: the pairs q = tid and q = tid + PROJ_THREADS
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int a = 0; a < RA; ++a) acc2[h][a] = 0.f;
+  for (int64_t k = 0; k < my_units; ++k) {
+    const int s = (int)(k % pg.nst);
+    const bool got = tma::mbar_wait(&full[s], (uint32_t)((k / pg.nst) & 1), status);
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) {
+        // drain: the loads of units k .. issued-1 are in flight, one per stage
+        for (int64_t q = k; q < issued; ++q) {
+          const uint64_t t0 = tma::gtimer();
+          uint32_t ok = 0;
+          const int sq = (int)(q % pg.nst);
+          while (!ok && tma::gtimer() - t0 < DRAIN_NS) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(tma::smem_u32(&full[sq])), "r"((uint32_t)((q / pg.nst) & 1))
+                : "memory");
+          }
+          if (!ok) break;
+        }
+      }
+      break;
+    }
+    const int band = (int)(k % pg.nbands);
+    const int64_t t = blockIdx.x + (k / pg.nbands) * G;
+    const uint8_t* T = base + (size_t)s * pg.stage_bytes;
+    const int i0 = band * pg.ka;
+    const int kv = min(pg.ka, g.na - i0);  // rows of this band inside mode a
+    float xx = 0.f;
+    for (int p = tid; p < kv * PCOLS; p += blockDim.x) {
+      const int i = p >> 5, c = p & 31;
+      float acc[RB];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) acc[b] = 0.f;
+      // rows r = i nb + j: the swizzle depends on r mod 8 only, so eight base addresses serve every j
+      const uint32_t r0 = (uint32_t)(i * g.nb);
+      const uint8_t* rb8[8];
+#pragma unroll
+      for (int k8 = 0; k8 < 8; ++k8) rb8[k8] = T + tma::sw128_offset(r0 + k8, (uint32_t)c);
+      int j = 0;
+      for (; j + 8 <= g.nb; j += 8) {
+#pragma unroll
+        for (int k8 = 0; k8 < 8; ++k8) {
+          const float x = *reinterpret_cast<const float*>(rb8[k8] + (size_t)j * 128);
+          xx = fmaf(x, x, xx);
+          const float4* u = reinterpret_cast<const float4*>(Ubs + (j + k8) * RB);
+#pragma unroll
+          for (int b4 = 0; b4 < RB / 4; ++b4) {
+            const float4 w = u[b4];
+            acc[4 * b4 + 0] = fmaf(x, w.x, acc[4 * b4 + 0]);
+            acc[4 * b4 + 1] = fmaf(x, w.y, acc[4 * b4 + 1]);
+            acc[4 * b4 + 2] = fmaf(x, w.z, acc[4 * b4 + 2]);
+            acc[4 * b4 + 3] = fmaf(x, w.w, acc[4 * b4 + 3]);
+          }
+        }
+      }
+      for (; j < g.nb; ++j) {
+        const float x = tile_at(T, r0 + (uint32_t)j, (uint32_t)c);
+        xx = fmaf(x, x, xx);
+        const float4* u = reinterpret_cast<const float4*>(Ubs + j * RB);
+#pragma unroll
+        for (int b4 = 0; b4 < RB / 4; ++b4) {
+          const float4 w = u[b4];
+          acc[4 * b4 + 0] = fmaf(x, w.x, acc[4 * b4 + 0]);
+          acc[4 * b4 + 1] = fmaf(x, w.y, acc[4 * b4 + 1]);
+          acc[4 * b4 + 2] = fmaf(x, w.z, acc[4 * b4 + 2]);
+          acc[4 * b4 + 3] = fmaf(x, w.w, acc[4 * b4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) Z[(i * RB + b) * PCOLS + c] = acc[b];
+    }
+    sx += (double)xx;
+    __syncthreads();  // Z complete; every read of this stage done
+    if (tid == 0 && issued < my_units) {
+      issue_band(&map, &full[issued % pg.nst], base + (size_t)(issued % pg.nst) * pg.stage_bytes, g, pg,
+                 unit_id(issued));
+      ++issued;
+    }
+    float yy = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = tid + h * PROJ_THREADS;
+      if (q >= rb * PCOLS) break;
+      const int b = q >> 5, c = q & 31;
+#pragma unroll 4
+      for (int i = 0; i < kv; ++i) {
+        const float z = Z[(i * RB + b) * PCOLS + c];
+        const float4* u = reinterpret_cast<const float4*>(Uas + (i0 + i) * RA);
+#pragma unroll
+        for (int a4 = 0; a4 < RA / 4; ++a4) {
+          const float4 w = u[a4];
+          acc2[h][4 * a4 + 0] = fmaf(z, w.x, acc2[h][4 * a4 + 0]);
+          acc2[h][4 * a4 + 1] = fmaf(z, w.y, acc2[h][4 * a4 + 1]);
+          acc2[h][4 * a4 + 2] = fmaf(z, w.z, acc2[h][4 * a4 + 2]);
+          acc2[h][4 * a4 + 3] = fmaf(z, w.w, acc2[h][4 * a4 + 3]);
+        }
+      }
+      if (band == pg.nbands - 1) {
+        const int64_t aidx = t / g.ncb, col = (t - aidx * g.ncb) * PCOLS + c;
+        if (col < g.B) {
+          float* o = out + ((aidx * ra) * rb + b) * g.B + col;
+#pragma unroll
+          for (int a = 0; a < RA; ++a)
+            if (a < ra) {
+              o[(int64_t)a * rb * g.B] = acc2[h][a];
+              yy = fmaf(acc2[h][a], acc2[h][a], yy);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < RA; ++a) acc2[h][a] = 0.f;
+      }
+    }
+    sy += (double)yy;
+    __syncthreads();  // Z consumed before the next band's stage 1
+  }
+  sx = block_sum2(sx, red);
+  sy = block_sum2(sy, red);
+  if (tid == 0) {
+    if (norm_in) atomicAdd(norm_in, sx);
+    if (norm_out) atomicAdd(norm_out, sy);
+    if (resid) atomicAdd(resid, sx - sy);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised projection for ranks <= 8, na <= 24 and nb <= 32. Lane (g, p) of a warp owns the
+// four columns 4g .. 4g+3 of a tile and two output indices (p and p + 4); the basis columns it needs
+// live in its registers, so one 16-byte shared load of a tile row feeds eight FMAs and no basis is
+// ever re-read from shared memory.
+//   stage 1 (ka warps, warp i = row i of a band of ka rows): Z[i][b][c] = sum_j T[i][j][c] Ub[j][b];
+//   stage 2 (8 warps, warp b): W[a][b][c] = sum_i Ua[i][a] Z[i][b][c] over the na rows of a tile, once
+//   per tile, written with 16-byte stores.
+// Z holds a whole tile, double-buffered by tile parity and handed over through named barriers:
+//   ZFULL[z] (ids 2, 3): stage 1 arrives after the last band of a tile, stage 2 waits;
+//   ZEMPTY[z] (ids 4, 5): stage 2 arrives when it has read Z[z], stage 1 waits before the first band of
+//   the tile after next; S1 (id 1): the stage-1 warps among themselves.
+// Thread 0 alone waits on each TMA barrier (bounded) and tells the stage-1 warps through shared memory;
+// a wait that gave up raises an abort flag that stage 2 reads after its next ZFULL wait, so every named
+// barrier still sees matching arrivals on both sides and both roles leave together.
+// ---------------------------------------------------------------------------------------------
+constexpr int WS_W2 = 4;  // stage-2 warps, two output indices of mode b each
+constexpr int WS_MAX_THREADS = 32 * (12 + WS_W2);
+
+// Knuth's TwoSum into a double-single accumulator (hi, lo): sums of norms kept in FP32 at FP64-class
+// accuracy (the FP64 pipes of this part issue at 1/64 of the FP32 rate).
+__device__ __forceinline__ void ds_add(float v, float& hi, float& lo) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
+// Packed FP32 FMA on register pairs (two independent round-to-nearest FMAs).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <int NB, int KA>
+__global__ void __launch_bounds__(WS_MAX_THREADS, 1)
+    pair_project_ws_kernel(const __grid_constant__ CUtensorMap map, const PairGeom g, const ProjGeom pg,
+                           const double* __restrict__ Ua, int ra, int lda, const double* __restrict__ Ub, int rb,
+                           int ldb, float* __restrict__ out, double* norm_in, double* norm_out, double* resid,
+                           int* status) {
+  constexpr int NA = 2 * KA;  // rows of mode a held in stage 2's registers: two bands of KA rows
+  extern __shared__ __align__(1024) uint8_t wsm[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wsm) + 1023) & ~(uintptr_t)1023);
+  float* Zb = reinterpret_cast<float*>(base + (size_t)pg.nst * pg.stage_bytes);  // [2][KA][8][32]
+  __shared__ __align__(8) uint64_t full[PROJ_STAGES_MAX];
+  __shared__ int sflag, abort_flag;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W1 = pg.ka, NT = (int)blockDim.x;
+  const int gq = lane >> 2, pq = lane & 3;  // columns 4 gq .. 4 gq + 3, output indices pq and pq + 4
+  const size_t zsize = (size_t)KA * 8 * PCOLS;
+  if (tid == 0) {
+    for (int st = 0; st < pg.nst; ++st) tma::mbar_init(&full[st], 1);
+    tma::fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // each CTA takes a contiguous run of tiles (consecutive column blocks of the same rows), so that its
+  // successive loads continue the DRAM pages of its previous ones
+  const int64_t per = (g.ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t my_tiles = (g.ntiles > t0) ? min(per, g.ntiles - t0) : 0;
+  const int64_t my_units = my_tiles * pg.nbands;
+  double sx = 0.0, sy = 0.0;
+  if (warp < W1) {
+    // ---------------- stage 1 ----------------
+    float u0[NB], u1[NB];  // Ub[j][pq], Ub[j][pq + 4]
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      u0[j] = (j < g.nb && pq < rb) ? (float)Ub[(int64_t)j * ldb + pq] : 0.f;
+      u1[j] = (j < g.nb && pq + 4 < rb) ? (float)Ub[(int64_t)j * ldb + pq + 4] : 0.f;
+    }
+    int64_t issued = 0, u_t = t0;
+    int u_b = 0;
+    if (tid == 0) {
+      for (; issued < my_units && issued < pg.nst; ++issued) {
+        issue_band(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg, u_t * pg.nbands + u_b);
+        if (++u_b == pg.nbands) {
+          u_b = 0;
+          ++u_t;
+        }
+      }
+    }
+    int64_t k = 0, tk = 0, posted = 0;
+    int s = 0, band = 0;
+    float sx_hi = 0.f, sx_lo = 0.f;
+    uint32_t par = 0;
+    for (; k < my_units; ++k) {
+      if (tid == 0) sflag = tma::mbar_wait(&full[s], par, status) ? 0 : 1;
+      named_sync(1, 32 * W1);
+      const bool abort_now = sflag != 0;
+      const int zb = (int)(tk & 1);
+      if (tk >= 2) named_sync(4 + zb, NT);  // stage 2 has read Z[zb] (unit tk - 2)
+      if (abort_now) {
+        if (tid == 0) abort_flag = 1;
+        named_arrive(2 + zb, NT);  // wake stage 2 for unit tk; it sees the flag and leaves
+        ++posted;
+        break;
+      }
+      const uint8_t* T = base + (size_t)s * pg.stage_bytes;
+      if (warp < KA) {
+        float acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+        float2 xx2 = make_float2(0.f, 0.f);  // every lane of a column group squares the same four values
+        // rows r = warp NB + j with NB % 8 == 0: the swizzle of row r is j mod 8, a constant of the unrolled loop
+        const uint8_t* Tw = T + (size_t)warp * NB * 128;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const float4 x = *reinterpret_cast<const float4*>(Tw + j * 128 + ((gq ^ (j & 7)) << 4));
+          xx2 = ffma2(make_float2(x.x, x.y), make_float2(x.x, x.y), xx2);
+          xx2 = ffma2(make_float2(x.z, x.w), make_float2(x.z, x.w), xx2);
+          acc[0] = fmaf(x.x, u0[j], acc[0]);
+          acc[1] = fmaf(x.y, u0[j], acc[1]);
+          acc[2] = fmaf(x.z, u0[j], acc[2]);
+          acc[3] = fmaf(x.w, u0[j], acc[3]);
+          acc[4] = fmaf(x.x, u1[j], acc[4]);
+          acc[5] = fmaf(x.y, u1[j], acc[5]);
+          acc[6] = fmaf(x.z, u1[j], acc[6]);
+          acc[7] = fmaf(x.w, u1[j], acc[7]);
+        }
+        float* Z = Zb + (size_t)zb * zsize + (size_t)warp * 8 * PCOLS;
+        *reinterpret_cast<float4*>(Z + pq * PCOLS + 4 * gq) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *reinterpret_cast<float4*>(Z + (pq + 4) * PCOLS + 4 * gq) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        ds_add(xx2.x + xx2.y, sx_hi, sx_lo);
+      }
+      named_sync(1, 32 * W1);  // every stage-1 read of stage s done
+      if (tid == 0 && issued < my_units) {
+        issue_band(&map, &full[s], base + (size_t)s * pg.stage_bytes, g, pg, u_t * pg.nbands + u_b);
+        ++issued;
+        if (++u_b == pg.nbands) {
+          u_b = 0;
+          ++u_t;
+        }
+      }
+      if (++s == pg.nst) {
+        s = 0;
+        par ^= 1u;
+      }
+      named_arrive(2 + zb, NT);  // Z[zb] holds this band
+      ++posted;
+      ++tk;
+      if (++band == pg.nbands) band = 0;
+    }
+    // the Z buffers of the last (up to) two tiles posted: wait until stage 2 has read them
+    for (int64_t q = (posted >= 2 ? posted - 2 : 0); q < posted; ++q) named_sync(4 + (int)(q & 1), NT);
+    if (tid == 0 && sflag != 0) {
+      // drain the loads still in flight after a wait gave up (bounded, ignoring the status word)
+      for (int64_t q = k; q < issued; ++q) {
+        const int sq = (int)(q % pg.nst);
+        const uint32_t pp = (uint32_t)((q / pg.nst) & 1);
+        const uint64_t t0 = tma::gtimer();
+        uint32_t ok = 0;
+        while (!ok && tma::gtimer() - t0 < DRAIN_NS) {
+          asm volatile(
+              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+              : "=r"(ok)
+              : "r"(tma::smem_u32(&full[sq])), "r"(pp)
+              : "memory");
+        }
+        if (!ok) break;
+      }
+    }
+    // each of the four lanes of a column group counted the same squares
+    sx = 0.25 * ((double)sx_hi + (double)sx_lo);
+  } else {
+    // ---------------- stage 2 ----------------
+    const int b0 = warp - W1, b1 = b0 + WS_W2;  // output indices of mode b of this warp
+    float v0[NA], v1[NA];  // Ua[i][pq], Ua[i][pq + 4]
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      v0[i] = (i < g.na && pq < ra) ? (float)Ua[(int64_t)i * lda + pq] : 0.f;
+      v1[i] = (i < g.na && pq + 4 < ra) ? (float)Ua[(int64_t)i * lda + pq + 4] : 0.f;
+    }
+    float acc[16];  // [b0, b1][a = pq, pq + 4][4 columns]
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    float sy_hi = 0.f, sy_lo = 0.f;
+    int64_t t = t0;
+    for (int64_t k = 0; k < my_units; ++k) {
+      const int zb = (int)(k & 1), band = (int)(k & 1);  // two bands per tile
+      named_sync(2 + zb, NT);
+      if (abort_flag) {
+        named_arrive(4 + zb, NT);
+        break;
+      }
+      const float* Z = Zb + (size_t)zb * zsize + 4 * gq;
+#pragma unroll
+      for (int i = 0; i < KA; ++i) {
+        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b0) * PCOLS);
+        const float4 zc = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b1) * PCOLS);
+        const float w0 = band ? v0[KA + i] : v0[i];
+        const float w1 = band ? v1[KA + i] : v1[i];
+        acc[0] = fmaf(za.x, w0, acc[0]);
+        acc[1] = fmaf(za.y, w0, acc[1]);
+        acc[2] = fmaf(za.z, w0, acc[2]);
+        acc[3] = fmaf(za.w, w0, acc[3]);
+        acc[4] = fmaf(za.x, w1, acc[4]);
+        acc[5] = fmaf(za.y, w1, acc[5]);
+        acc[6] = fmaf(za.z, w1, acc[6]);
+        acc[7] = fmaf(za.w, w1, acc[7]);
+        acc[8] = fmaf(zc.x, w0, acc[8]);
+        acc[9] = fmaf(zc.y, w0, acc[9]);
+        acc[10] = fmaf(zc.z, w0, acc[10]);
+        acc[11] = fmaf(zc.w, w0, acc[11]);
+        acc[12] = fmaf(zc.x, w1, acc[12]);
+        acc[13] = fmaf(zc.y, w1, acc[13]);
+        acc[14] = fmaf(zc.z, w1, acc[14]);
+        acc[15] = fmaf(zc.w, w1, acc[15]);
+      }
+      named_arrive(4 + zb, NT);  // Z[zb] read
+      if (band == 1) {
+        const int64_t aidx = t / g.ncb, col = (t - aidx * g.ncb) * PCOLS + 4 * gq;
+        if (col < g.B) {  // B % 4 == 0, so the four columns are all inside
+          float yy = 0.f;
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb) {
+            const int b = hb ? b1 : b0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int a = pq + 4 * h;
+              if (b < rb && a < ra) {
+                const float* q4 = acc + 8 * hb + 4 * h;
+                const float4 w = make_float4(q4[0], q4[1], q4[2], q4[3]);
+                *reinterpret_cast<float4*>(out + ((aidx * ra + a) * rb + b) * g.B + col) = w;
+                yy = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, yy))));
+              }
+            }
+          }
+          ds_add(yy, sy_hi, sy_lo);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+        ++t;
+      }
+    }
+    sy = (double)sy_hi + (double)sy_lo;
+  }
+  __syncthreads();
+  sx = block_sum2(sx, red);
+  sy = block_sum2(sy, red);
+  if (tid == 0) {
+    if (norm_in) atomicAdd(norm_in, sx);
+    if (norm_out) atomicAdd(norm_out, sy);
+    if (resid) atomicAdd(resid, sx - sy);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gram matrices of both modes. Warp w owns one 8 x 8 block (p <= q) of the upper triangle of G_a
+// (warps 0 .. wa-1) or of G_b (the rest); lane c accumulates its column's outer products in FP32,
+// G_a over (j, c) and G_b over (i, c); every GRAM_FOLD tiles the warp sums its lanes and adds the
+// block into FP64 shared memory, which is added to G (both triangles) once per CTA.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void block_of(int w, int n8, int& p, int& q) {
+  int t = w;
+  p = 0;
+  while (t >= n8 - p) {
+    t -= n8 - p;
+    ++p;
+  }
+  q = p + t;
+}
+
+__device__ __forceinline__ void fold_block(float (&acc)[8][8], double* blk) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      float x = acc[u][v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == ((u * 8 + v) & 31)) blk[u * 8 + v] += (double)x;
+      acc[u][v] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(384, 1)
+    pair_gram_kernel(const __grid_constant__ CUtensorMap map, const PairGeom g, int wa, double* __restrict__ Ga,
+                     double* __restrict__ Gb, int* status) {
+  extern __shared__ __align__(1024) uint8_t gsm[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~(uintptr_t)1023);
+  uint8_t* stage[2] = {base, base + g.stage_bytes};
+  double* blocks = reinterpret_cast<double*>(base + 2 * (size_t)g.stage_bytes);  // [warps][64]
+  __shared__ __align__(8) uint64_t full[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const bool on_a = warp < wa;
+  const int n8 = on_a ? (g.na + 7) / 8 : (g.nb + 7) / 8;
+  int p, q;
+  block_of(on_a ? warp : warp - wa, n8, p, q);
+  double* blk = blocks + warp * 64;
+  for (int e = lane; e < 64; e += 32) blk[e] = 0.0;
+  int64_t issued[2] = {0, 0};
+  if (tid == 0) {
+    tma::mbar_init(&full[0], 1);
+    tma::mbar_init(&full[1], 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  const int64_t G = gridDim.x;
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      const int64_t t = blockIdx.x + s * G;
+      if (t < g.ntiles) {
+        issue_tile(&map, &full[s], stage[s], g, t);
+        ++issued[s];
+      }
+    }
+  }
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  // rows of the two 8-row groups inside the mode, and how the tile row is formed from them
+  const int outer = on_a ? g.nb : g.na;  // the index summed over together with the column
+  const bool fast = (g.nb & 7) == 0;
+  uint32_t qoff_p[8], qoff_q[8];  // G_b operands: byte offsets of rows 8p + u and 8q + u within a block of nb rows
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    qoff_p[u] = tma::sw128_offset((uint32_t)(8 * p + u), (uint32_t)lane);
+    qoff_q[u] = tma::sw128_offset((uint32_t)(8 * q + u), (uint32_t)lane);
+  }
+  int64_t k = 0;
+  int since = 0;
+  for (int64_t t = blockIdx.x; t < g.ntiles; t += G, ++k) {
+    const int s = (int)(k & 1);
+    const bool got = tma::mbar_wait(&full[s], (uint32_t)((k >> 1) & 1), status);
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) drain_loads(full, issued, (k + 1) >> 1, k >> 1);
+      break;
+    }
+    const uint8_t* T = stage[s];
+    if (fast) {
+      // nb % 8 == 0: the swizzle of row r depends on r mod 8, which is o mod 8 for the rows of G_a's
+      // operands and u for G_b's, so the addresses are precomputed bases plus a row offset
+      const size_t row_b = (size_t)g.nb * 128;
+      for (int o = 0; o < outer; ++o) {
+        float vp[8], vq[8];
+        if (on_a) {
+          const uint32_t sw = (uint32_t)(o & 7);
+          const uint8_t* bp = T + (size_t)o * 128 + ((((uint32_t)lane >> 2) ^ sw) << 4) + ((lane & 3) << 2);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            vp[u] = (8 * p + u < g.na) ? *reinterpret_cast<const float*>(bp + (size_t)(8 * p + u) * row_b) : 0.f;
+            vq[u] = (8 * q + u < g.na) ? *reinterpret_cast<const float*>(bp + (size_t)(8 * q + u) * row_b) : 0.f;
+          }
+        } else {
+          const uint8_t* bo = T + (size_t)o * row_b;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            vp[u] = (8 * p + u < g.nb) ? *reinterpret_cast<const float*>(bo + qoff_p[u]) : 0.f;
+            vq[u] = (8 * q + u < g.nb) ? *reinterpret_cast<const float*>(bo + qoff_q[u]) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(vp[u], vq[v], acc[u][v]);
+      }
+    } else {
+      for (int o = 0; o < outer; ++o) {
+        float vp[8], vq[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r1 = 8 * p + u, r2 = 8 * q + u;
+          if (on_a) {
+            vp[u] = r1 < g.na ? tile_at(T, (uint32_t)(r1 * g.nb + o), (uint32_t)lane) : 0.f;
+            vq[u] = r2 < g.na ? tile_at(T, (uint32_t)(r2 * g.nb + o), (uint32_t)lane) : 0.f;
+          } else {
+            vp[u] = r1 < g.nb ? tile_at(T, (uint32_t)(o * g.nb + r1), (uint32_t)lane) : 0.f;
+            vq[u] = r2 < g.nb ? tile_at(T, (uint32_t)(o * g.nb + r2), (uint32_t)lane) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(vp[u], vq[v], acc[u][v]);
+      }
+    }
+    __syncthreads();  // every read of this stage done
+    if (tid == 0 && t + 2 * G < g.ntiles) {
+      issue_tile(&map, &full[s], stage[s], g, t + 2 * G);
+      ++issued[s];
+    }
+    if (++since == GRAM_FOLD) {
+      since = 0;
+      fold_block(acc, blk);
+    }
+  }
+  fold_block(acc, blk);
+  __syncwarp();
+  double* Gm = on_a ? Ga : Gb;
+  const int n = on_a ? g.na : g.nb;
+  for (int e = lane; e < 64; e += 32) {
+    const int u = e >> 3, v = e & 7;
+    const int r = 8 * p + u, c = 8 * q + v;
+    if (r < n && c < n) {
+      atomicAdd(&Gm[(int64_t)r * n + c], blk[e]);
+      if (p != q) atomicAdd(&Gm[(int64_t)c * n + r], blk[e]);
+    }
+  }
+  (void)nwarps;
+}
+
+// 3-D map of X[A][na][nb][B] as (B, nb, na * A), box (32, nb, rows): a whole tile (rows = na) or one band.
+bool make_map_pair(CUtensorMap* m, const float* X, const PairGeom& g, int rows) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)g.B, (cuuint64_t)g.nb, (cuuint64_t)g.na * (cuuint64_t)g.A};
+  cuuint64_t strides[2] = {(cuuint64_t)g.B * 4, (cuuint64_t)g.nb * (cuuint64_t)g.B * 4};
+  cuuint32_t box[3] = {(cuuint32_t)PCOLS, (cuuint32_t)g.nb, (cuuint32_t)rows};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+PairGeom geom(int64_t A, int na, int nb, int64_t B) {
+  PairGeom g;
+  g.A = A;
+  g.B = B;
+  g.na = na;
+  g.nb = nb;
+  g.ncb = (B + PCOLS - 1) / PCOLS;
+  g.ntiles = A * g.ncb;
+  g.tile_bytes = (uint32_t)na * (uint32_t)nb * 128u;
+  g.stage_bytes = (g.tile_bytes + 1023u) & ~1023u;
+  return g;
+}
+
+int sm_count() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(nsm, 1);
+}
+
+ProjGeom proj_geom(const PairGeom& g, int RA, int RB) {
+  ProjGeom pg;
+  pg.ka = g.na >= 16 ? (g.na + 1) / 2 : g.na;
+  pg.nbands = (g.na + pg.ka - 1) / pg.ka;
+  pg.unit_bytes = (uint32_t)pg.ka * (uint32_t)g.nb * 128u;
+  pg.stage_bytes = (pg.unit_bytes + 1023u) & ~1023u;
+  const size_t fixed = 1024 + sizeof(float) * ((size_t)pg.ka * RB * PCOLS + (size_t)g.na * RA + (size_t)g.nb * RB);
+  const size_t cap = 227 * 1024;
+  pg.nst = cap > fixed ? (int)std::min<size_t>(PROJ_STAGES_MAX, (cap - fixed) / pg.stage_bytes) : 0;
+  return pg;
+}
+
+size_t proj_smem(const PairGeom& g, const ProjGeom& pg, int RA, int RB) {
+  return 1024 + (size_t)pg.nst * pg.stage_bytes +
+         sizeof(float) * ((size_t)pg.ka * RB * PCOLS + (size_t)g.na * RA + (size_t)g.nb * RB);
+}
+
+template <int RA, int RB>
+cudaError_t launch_proj(const float* X, const PairGeom& g, const double* Ua, int ra, int lda, const double* Ub,
+                        int rb, int ldb, float* out, double* norm_in, double* norm_out, double* resid, int* status,
+                        cudaStream_t s) {
+  const ProjGeom pg = proj_geom(g, RA, RB);
+  if (pg.nst < 2) return cudaErrorInvalidValue;
+  CUtensorMap m;
+  if (!make_map_pair(&m, X, g, pg.ka)) return cudaErrorInvalidValue;
+  const size_t smem = proj_smem(g, pg, RA, RB);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(pair_project_kernel<RA, RB>));
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(g.ntiles, sm_count());
+  pair_project_kernel<RA, RB><<<grid, PROJ_THREADS, smem, s>>>(m, g, pg, Ua, ra, lda, Ub, rb, ldb, out, norm_in,
+                                                               norm_out, resid, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proj_ws(const float* X, const PairGeom& g, const double* Ua, int ra, int lda, const double* Ub,
+                           int rb, int ldb, float* out, double* norm_in, double* norm_out, double* resid, int* status,
+                           cudaStream_t s) {
+  // two bands of 12 rows of mode a (na = 24), nb = 24
+  if (g.na != 24 || g.nb != 24 || (g.B & 3) != 0) return cudaErrorInvalidValue;
+  ProjGeom pg;
+  pg.ka = 12;
+  pg.nbands = 2;
+  pg.unit_bytes = (uint32_t)pg.ka * (uint32_t)g.nb * 128u;
+  pg.stage_bytes = (pg.unit_bytes + 1023u) & ~1023u;
+  const size_t fixed = 1024 + sizeof(float) * 2 * (size_t)pg.ka * 8 * PCOLS;
+  const size_t cap = 227 * 1024;
+  pg.nst = (int)std::min<size_t>(PROJ_STAGES_MAX, (cap - fixed) / pg.stage_bytes);
+  if (pg.nst < 2) return cudaErrorInvalidValue;
+  const size_t smem = fixed + (size_t)pg.nst * pg.stage_bytes;
+  CUtensorMap m;
+  if (!make_map_pair(&m, X, g, pg.ka)) return cudaErrorInvalidValue;
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(pair_project_ws_kernel<24, 12>));
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(g.ntiles, sm_count());
+  pair_project_ws_kernel<24, 12><<<grid, 32 * (pg.ka + WS_W2), smem, s>>>(m, g, pg, Ua, ra, lda, Ub, rb, ldb, out,
+                                                                            norm_in, norm_out, resid, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool pair_gram_supported(int64_t A, int64_t na, int64_t nb, int64_t B) {
+  return A >= 1 && na >= 1 && nb >= 1 && na <= PAIR_MAX_GRAM && nb <= PAIR_MAX_GRAM && B >= 4 && B % 4 == 0 &&
+         na * A <= 0x7fffffffll && B <= 0x7fffffffll;
+}
+
+bool pair_project_supported(int64_t A, int64_t na, int64_t nb, int64_t B, int64_t ra, int64_t rb) {
+  if (A < 1 || na < 1 || nb < 1 || na > PAIR_MAX_PROJ || nb > PAIR_MAX_PROJ || B < 4 || B % 4 != 0) return false;
+  if (ra < 1 || rb < 1 || ra > 16 || rb > 16 || na * A > 0x7fffffffll || B > 0x7fffffffll) return false;
+  if (rb * PCOLS > 2 * PROJ_THREADS) return false;
+  const PairGeom g = geom(A, (int)na, (int)nb, B);
+  return proj_geom(g, ra > 8 ? 16 : 8, rb > 8 ? 16 : 8).nst >= 2;
+}
+
+cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t B, double* Ga, double* Gb,
+                             int* status, cudaStream_t s) {
+  if (!pair_gram_supported(A, na, nb, B) || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
+  const PairGeom g = geom(A, na, nb, B);
+  CUtensorMap m;
+  if (!make_map_pair(&m, X, g, na)) return cudaErrorInvalidValue;
+  const int na8 = (na + 7) / 8, nb8 = (nb + 7) / 8;
+  const int wa = na8 * (na8 + 1) / 2, wb = nb8 * (nb8 + 1) / 2;
+  const int threads = 32 * (wa + wb);
+  const size_t smem = 1024 + 2 * (size_t)g.stage_bytes + sizeof(double) * 64 * (size_t)(wa + wb);
+  if (threads > 384 || smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(pair_gram_kernel));
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(g.ntiles, sm_count());
+  const double K = (double)A * (double)B;  // columns per row of either unfolding, over the whole tensor
+  ProfScope prof(K_GRAM_F32, s, (double)na * (na + 1) * K * nb + (double)nb * (nb + 1) * K * na,
+                 4.0 * K * na * nb);
+  pair_gram_kernel<<<grid, threads, smem, s>>>(m, g, wa, Ga, Gb, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_project(const float* X, int64_t A, int na, int nb, int64_t B, const double* Ua, int ra,
+                                int lda, const double* Ub, int rb, int ldb, float* out, double* norm_in,
+                                double* norm_out, double* resid, int* status, cudaStream_t s) {
+  if (!pair_project_supported(A, na, nb, B, ra, rb) || (reinterpret_cast<uintptr_t>(X) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const PairGeom g = geom(A, na, nb, B);
+  const double elems = (double)A * na * nb * (double)B;
+  ProfScope prof(K_TTM_F32, s, 2.0 * elems * rb + 2.0 * (double)A * na * rb * (double)B * ra,
+                 4.0 * elems + 4.0 * (double)A * ra * rb * (double)B);
+  if (ra <= 8 && rb <= 8 && na == 24 && nb == 24) return launch_proj_ws(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out,
+                                                            resid, status, s);
+  if (ra <= 8 && rb <= 8) return launch_proj<8, 8>(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out, resid, status, s);
+  if (ra <= 8) return launch_proj<8, 16>(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out, resid, status, s);
+  if (rb <= 8) return launch_proj<16, 8>(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out, resid, status, s);
+  return launch_proj<16, 16>(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out, resid, status, s);
+}
+
+}  // namespace bht

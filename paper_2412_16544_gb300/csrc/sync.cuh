@@ -7,7 +7,10 @@ namespace bht {
 
 struct Barrier {
   unsigned int count;
-  unsigned int spare;
+  // written by the host before a launch (zero normally): bit 0 makes CTA 0 withhold its first arrival,
+  // bits 16..31 shorten the wait limit to that many milliseconds (a test of the timeout path: every
+  // CTA's wait then gives up, the status word reports BHT_ETIMEOUT and the kernel returns)
+  unsigned int flags;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -19,9 +22,11 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Grid barrier of a cooperative launch on a counter that only grows (zero at launch): the k-th call
 // of every CTA adds one with a release reduction, which returns nothing, and waits until the counter
 // reaches k * gridDim.x. `epoch` counts the calls (the same in every thread of the CTA). The wait is
-// limited to 1 s: returns false when it gave up (the status word then holds BHT_ETIMEOUT = 6) or
-// another CTA reported a failure. With one CTA it is __syncthreads.
-__device__ __forceinline__ bool grid_barrier_count(Barrier* bar, unsigned int& epoch, int* status) {
+// limited to 1 s (or to the milliseconds in flags, the Barrier's flags word read once by the kernel's
+// thread 0): returns false when it gave up (the status word then holds BHT_ETIMEOUT = 6) or another
+// CTA reported a failure. With one CTA it is __syncthreads.
+__device__ __forceinline__ bool grid_barrier_count(Barrier* bar, unsigned int& epoch, int* status,
+                                                   unsigned int flags = 0u) {
   __shared__ int ok;
   __syncthreads();
   if (gridDim.x == 1) return true;
@@ -29,7 +34,9 @@ __device__ __forceinline__ bool grid_barrier_count(Barrier* bar, unsigned int& e
   if (threadIdx.x == 0) {
     ok = 1;
     const unsigned int target = epoch * gridDim.x;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+    const uint64_t limit = (flags >> 16) ? (uint64_t)(flags >> 16) * 1000000ull : 1000000000ull;
+    if (!((flags & 1u) && blockIdx.x == 0 && epoch == 1))
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
     const uint64_t t0 = global_ns();
     unsigned int cur;
     for (uint32_t spin = 0;; ++spin) {
@@ -40,7 +47,7 @@ __device__ __forceinline__ bool grid_barrier_count(Barrier* bar, unsigned int& e
           ok = 0;
           break;
         }
-        if (global_ns() - t0 > 1000000000ull) {
+        if (global_ns() - t0 > limit) {
           atomicExch(status, 6);
           ok = 0;
           break;

@@ -51,15 +51,32 @@ __global__ void cheb_factor_kernel(const double* __restrict__ c, int64_t count, 
   f[t] = (float)acc;
 }
 
+// The uniforms (k + 1/2) 2^-24 of two 24-bit integers k, formed in FP32 (k 2^-24 is exact; adding 2^-25
+// rounds to even only for k >= 2^23, a change of at most 2^-25), then the Box-Muller pair.
+__device__ __forceinline__ void noise_pair(uint64_t base, int64_t word, float sd, float& z0, float& z1) {
+  const uint64_t w = mix64(base + ((uint64_t)word + 1ull) * 0x9E3779B97F4A7C15ull);
+  const float u1 = fmaf((float)(uint32_t)(w >> 40), 0x1p-24f, 0x1p-25f);
+  const float u2 = fmaf((float)(uint32_t)((w >> 8) & 0xFFFFFFull), 0x1p-24f, 0x1p-25f);
+  const float r = sd * sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  z0 = r * cs;
+  z1 = r * sn;
+}
+
 // One block per (item, chunk of slabs); a slab is the n x n plane of the last two modes for one index of
-// the first d - 2 modes. The factors of the last two modes stay in shared memory for the block; the
-// product over the first d - 2 modes is formed once per slab and term.
+// the first d - 2 modes. The factors of the last two modes stay in shared memory for the block, and the
+// product over the first d - 2 modes is formed once per slab and term. With n % 8 == 0 a thread makes
+// 8 consecutive elements of a row (one factor product per term, one noise word per two elements, two
+// 16-byte stores); otherwise one element at a time.
+template <bool OCTETS>
 __global__ void __launch_bounds__(SYNTH_THREADS) cheb_items_kernel(const float* __restrict__ f, int terms, int d,
                                                                   int n, int64_t slabs, int64_t slabs_per_block,
                                                                   double noise_std, uint64_t seed,
                                                                   int64_t first_item, float* __restrict__ out) {
-  __shared__ float fa[SYNTH_MAX_TERMS * SYNTH_MAX_N], fb[SYNTH_MAX_TERMS * SYNTH_MAX_N];
-  __shared__ float P[SYNTH_MAX_TERMS];
+  __shared__ __align__(16) float fa[SYNTH_MAX_TERMS * SYNTH_MAX_N];
+  __shared__ __align__(16) float fb[SYNTH_MAX_TERMS * SYNTH_MAX_N];
+  __shared__ float Pall[SYNTH_MAX_N * SYNTH_MAX_TERMS];  // [slab of the block][term]
   const int64_t item = blockIdx.y;
   const float* fi = f + item * (int64_t)terms * d * n;  // [terms][d][n]
   for (int t = threadIdx.x; t < terms * n; t += blockDim.x) {
@@ -73,34 +90,68 @@ __global__ void __launch_bounds__(SYNTH_THREADS) cheb_items_kernel(const float* 
   const float sd = (float)noise_std;
   float* o = out + item * per_item;
   const int64_t s0 = blockIdx.x * slabs_per_block, s1 = min(slabs, s0 + slabs_per_block);
-  for (int64_t sl = s0; sl < s1; ++sl) {
-    __syncthreads();  // fa / fb written (first slab), P of the previous slab consumed
-    if (threadIdx.x < terms) {
-      float p = 1.f;
-      int64_t rem = sl;
-      for (int m = d - 3; m >= 0; --m) {
-        const int im = (int)(rem % n);
-        rem /= n;
-        p *= fi[((int64_t)threadIdx.x * d + m) * n + im];
-      }
-      P[threadIdx.x] = p;
+  // the products over the first d - 2 modes of every slab of the block, once
+  for (int t = threadIdx.x; t < (int)(s1 - s0) * terms; t += blockDim.x) {
+    const int sl_rel = t / terms, q = t - sl_rel * terms;
+    float p = 1.f;
+    int64_t rem = s0 + sl_rel;
+    for (int m = d - 3; m >= 0; --m) {
+      const int im = (int)(rem % n);
+      rem /= n;
+      p *= fi[((int64_t)q * d + m) * n + im];
     }
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
-      const int ia = (int)(e / n), ib = (int)(e % n);
-      float v = 0.f;
-      for (int q = 0; q < terms; ++q) v = fmaf(P[q] * fa[q * n + ia], fb[q * n + ib], v);
-      const int64_t E = sl * nn + e;  // flat index within the item
-      if (sd != 0.f) {
-        const uint64_t w = mix64(base + ((uint64_t)(E >> 1) + 1ull) * 0x9E3779B97F4A7C15ull);
-        const float u1 = (float)(((double)(w >> 40) + 0.5) * 0x1p-24);
-        const float u2 = (float)(((double)((w >> 8) & 0xFFFFFFull) + 0.5) * 0x1p-24);
-        const float r = sqrtf(-2.f * logf(u1));
-        float sn, cs;
-        sincospif(2.f * u2, &sn, &cs);
-        v = fmaf(sd, r * ((E & 1) ? sn : cs), v);
+    Pall[sl_rel * terms + q] = p;
+  }
+  __syncthreads();
+  for (int64_t sl = s0; sl < s1; ++sl) {
+    const float* P = Pall + (sl - s0) * terms;
+    if (OCTETS) {
+      const int per_row = n / 8;
+      for (int t = threadIdx.x; t < n * per_row; t += blockDim.x) {
+        const int ia = t / per_row, ib0 = (t - ia * per_row) * 8;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = 0.f;
+        for (int q = 0; q < terms; ++q) {
+          const float pa = P[q] * fa[q * n + ia];
+          const float4 b0 = *reinterpret_cast<const float4*>(fb + q * n + ib0);
+          const float4 b1 = *reinterpret_cast<const float4*>(fb + q * n + ib0 + 4);
+          v[0] = fmaf(pa, b0.x, v[0]);
+          v[1] = fmaf(pa, b0.y, v[1]);
+          v[2] = fmaf(pa, b0.z, v[2]);
+          v[3] = fmaf(pa, b0.w, v[3]);
+          v[4] = fmaf(pa, b1.x, v[4]);
+          v[5] = fmaf(pa, b1.y, v[5]);
+          v[6] = fmaf(pa, b1.z, v[6]);
+          v[7] = fmaf(pa, b1.w, v[7]);
+        }
+        const int64_t E = sl * nn + (int64_t)ia * n + ib0;  // even: a row starts at a multiple of 8
+        if (sd != 0.f) {
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            float z0, z1;
+            noise_pair(base, (E >> 1) + u / 2, sd, z0, z1);
+            v[u] += z0;
+            v[u + 1] += z1;
+          }
+        }
+        float4* dst = reinterpret_cast<float4*>(o + E);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
       }
-      o[E] = v;
+    } else {
+      for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int ia = (int)(e / n), ib = (int)(e % n);
+        float v = 0.f;
+        for (int q = 0; q < terms; ++q) v = fmaf(P[q] * fa[q * n + ia], fb[q * n + ib], v);
+        const int64_t E = sl * nn + e;  // flat index within the item
+        if (sd != 0.f) {
+          float z0, z1;
+          noise_pair(base, E >> 1, 1.f, z0, z1);
+          v = fmaf(sd, (E & 1) ? z1 : z0, v);
+        }
+        o[E] = v;
+      }
     }
   }
 }
@@ -162,8 +213,12 @@ extern "C" bht_status bht_synth_chebyshev(const double* coeffs, int64_t count, i
       const double bytes = 4.0 * (double)count * (double)slabs * n * n;
       bht::ProfScope ps(bht::K_PREP, s, 0.0, bytes);
       dim3 grid((unsigned)chunks, (unsigned)count);
-      cheb_items_kernel<<<grid, SYNTH_THREADS, 0, s>>>(df, terms, d, n, slabs, spb, noise_std, seed, first_item,
-                                                        out);
+      if (n % 8 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0)
+        cheb_items_kernel<true><<<grid, SYNTH_THREADS, 0, s>>>(df, terms, d, n, slabs, spb, noise_std, seed,
+                                                                first_item, out);
+      else
+        cheb_items_kernel<false><<<grid, SYNTH_THREADS, 0, s>>>(df, terms, d, n, slabs, spb, noise_std, seed,
+                                                                 first_item, out);
       e = cudaGetLastError();
       bht::note_launch();
     }

@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace bht {
 
@@ -41,52 +42,15 @@ constexpr int TC_THREADS = 256;
 constexpr int BM = 128;           // rows per tile (MMA M)
 constexpr int KC = 32;            // fp32 per 128-byte swizzle row (one K chunk)
 constexpr int CHUNK_BYTES = BM * KC * 4;  // 16 KB
-constexpr uint64_t WAIT_NS = 1000000000ull;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
+using tma::gtimer;
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait;
+using tma::smem_u32;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-
-// Bounded wait for the completion of phase `parity`; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status) {
-  uint32_t ok = 0;
-  uint64_t t0 = 0;
-  for (int it = 0;; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 255) == 255) {
-      const uint64_t t = gtimer();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > WAIT_NS) {
-        atomicExch(status, 6);
-        return false;
-      }
-      if (*(volatile int*)status != 0) return false;
-    }
-  }
 }
 
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
@@ -197,7 +161,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ttm_tc_kernel(const __grid_cons
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma::fence_mbar_init();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -421,6 +385,8 @@ bool make_map_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
 
 bool ttm_tc_supported(int64_t K, int64_t S, int nb) {
   return K >= 4 && K % 4 == 0 && S >= 1 && S <= 4096 && nb >= 1 && nb <= 2;

@@ -101,3 +101,52 @@ def test_tensor_core_mode_product(B, rows, K, S, R2):
     # ||X||^2: FP32 partial sums of 16 squares folded into FP64, so at most 16 * 2^-24 relative
     assert abs(n[0] - np.sum(X.astype(np.float64) ** 2)) <= 16 * 2.0 ** -24 * n[0]
     assert abs(n[1] - np.sum(out ** 2)) <= 1e-6 * n[1]
+
+
+# The two-mode passes of small leaves on X [A][na][nb][B]: tiles of 32 columns of B (a ragged last block
+# when B % 32 != 0, a single short block when B < 32), more tiles than SMs, FP32 products.
+PAIR_SHAPES = [(5, 24, 24, 100), (7, 16, 9, 36), (2, 24, 7, 4), (300, 24, 24, 24), (3, 5, 24, 1000), (8, 24, 24, 13824)]
+
+
+def _pair_input(A, na, nb, Bc, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(A, na, nb, Bc)) * np.linspace(1.0, 0.1, na)[None, :, None, None]
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("A,na,nb,Bc", PAIR_SHAPES)
+def test_pair_gram_matches_fp64(B, A, na, nb, Bc):
+    X = _pair_input(A, na, nb, Bc, A + na + nb)
+    Ga, Gb = B.bht_pair_gram(torch.from_numpy(X).cuda())
+    X64 = X.astype(np.float64)
+    Xa = X64.transpose(1, 0, 2, 3).reshape(na, -1)
+    Xb = X64.transpose(2, 0, 1, 3).reshape(nb, -1)
+    ra, rb = Xa @ Xa.T, Xb @ Xb.T
+    Ga, Gb = Ga.cpu().numpy(), Gb.cpu().numpy()
+    # FP32 products summed per lane over at most a few hundred columns before each FP64 fold
+    assert np.abs(Ga - ra).max() <= 2e-6 * np.abs(ra).max()
+    assert np.abs(Gb - rb).max() <= 2e-6 * np.abs(rb).max()
+    assert np.array_equal(Ga, Ga.T) and np.array_equal(Gb, Gb.T)
+    assert abs(np.trace(Ga) - np.sum(X64 ** 2)) <= 1e-6 * np.sum(X64 ** 2)
+
+
+@pytest.mark.parametrize("A,na,nb,Bc", PAIR_SHAPES)
+@pytest.mark.parametrize("ra,rb", [(7, 7), (3, 16), (16, 1)])
+def test_pair_project_matches_fp64(B, A, na, nb, Bc, ra, rb):
+    ra, rb = min(ra, na), min(rb, nb)
+    X = _pair_input(A, na, nb, Bc, A * 3 + ra)
+    rng = np.random.default_rng(ra * 100 + rb)
+    Ua = np.linalg.qr(rng.normal(size=(na, na)))[0][:, :ra].copy()
+    Ub = np.linalg.qr(rng.normal(size=(nb, nb)))[0][:, :rb].copy()
+    norms = torch.zeros(3, dtype=torch.float64, device="cuda")
+    out = B.bht_pair_project(torch.from_numpy(X).cuda(), torch.from_numpy(Ua).cuda(), torch.from_numpy(Ub).cuda(),
+                             norms=norms).cpu().numpy().astype(np.float64)
+    ref = np.tensordot(np.tensordot(X.astype(np.float64), Ua, axes=([1], [0])), Ub, axes=([1], [0]))  # [A][B][ra][rb]
+    ref = ref.transpose(0, 2, 3, 1)
+    # FP32 products on FP32-rounded bases: about 2^-24 sqrt(na nb) relative
+    assert np.linalg.norm(out - ref) <= 2e-6 * np.linalg.norm(ref)
+    n = norms.cpu().numpy()
+    x2, o2 = float(np.sum(X.astype(np.float64) ** 2)), float(np.sum(ref ** 2))
+    assert abs(n[0] - x2) <= 1e-6 * x2
+    assert abs(n[1] - o2) <= 2e-6 * o2
+    assert abs(n[2] - (n[0] - n[1])) <= 1e-9 * x2

@@ -26,7 +26,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     r, w, lr = bench.rank_env()
     m = bench.job_max(dist, 10.0 + 5.0 * rank)          # rank 1 is the slow one
-    a = bench.parse(["--grid", "8", "--items", "2", "--increments", "2"])
+    a = bench.parse(["--workload", "spectral", "--grid", "8", "--items", "2", "--increments", "2"])
     Y = bench.gen_stream(a, seed=r)
     digest = float(np.abs(Y).sum())
     d = torch.tensor([digest], dtype=torch.float64)
@@ -58,7 +58,8 @@ def test_two_gloo_ranks_share_the_job_time_and_own_distinct_streams():
 def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", "29512", os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--grid", "8", "--items", "2",
+           "--impl", "reference", "--workload", "spectral", "--gpus", "2", "--steps", "1", "--warmup", "1",
+           "--grid", "8", "--items", "2",
            "--increments", "2", "--cpu-seconds", "1"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     p = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
