@@ -249,7 +249,7 @@ def run_reference(a, rank):
 KERNEL_SOURCES = {
     "eig_tridiag_f64": ("paper_2412_16544_gb300/csrc/eig.cu", ["tridiag_rows_kernel", "householder"],
                         ["paper_2412_16544_gb300/csrc/sync.cuh"]),
-    "ttm_f32": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_project_kernel"],
+    "ttm_f32": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_project_ws_kernel", "ds_add", "ffma2"],
                 ["paper_2412_16544_gb300/csrc/tma.cuh"]),
     "gram_f32": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_gram_kernel"], ["paper_2412_16544_gb300/csrc/tma.cuh"]),
 }

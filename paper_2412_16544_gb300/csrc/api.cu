@@ -775,10 +775,20 @@ LTensor project_layer_tc(LTensor C, const std::vector<int>& ids, const std::vect
   return C;
 }
 
+// Whether every product of a layer is small enough (at most about a GFLOP, 2 numel S with S the new
+// size) for the FP32 SIMT kernel in place: there the tensor cores' transposes and permutations cost
+// more than the product. BHT-l2r, Step 1 and Step 3 of HT-RISE take the same rule, so that a batch is
+// encoded in the same arithmetic by each of them.
+bool small_products(const LTensor& C, const std::vector<int64_t>& sizes) {
+  double mx = 0.0;
+  for (int64_t v : sizes) mx = std::max(mx, 2.0 * (double)C.numel() * (double)v);
+  return C.dtype == BHT_F32 && mx <= 1e9;
+}
+
 // Project a layer's axes onto bases (C x_j U_j^T), U_j = [rows_j][r_j], cheapest order first.
 LTensor project_layer(LTensor C, const std::vector<int>& ids, const std::vector<const double*>& Us,
                       const std::vector<int64_t>& rs, const Arith& ar, cudaStream_t s) {
-  if (ar.mixed && !ar.tight && C.dtype == BHT_F32 && !ids.empty())
+  if (ar.mixed && !ar.tight && C.dtype == BHT_F32 && !ids.empty() && !small_products(C, rs))
     return project_layer_tc(std::move(C), ids, Us, rs, nullptr, nullptr, nullptr, ar, s);
   std::vector<std::pair<int, int64_t>> ops;
   for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
@@ -1160,7 +1170,9 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       Us.push_back(st->U[id]);
       rs.push_back(st->rank[id]);
     }
-    if (ar.mixed && !ar.tight && resid && C.dtype == BHT_F32) {
+    // small products in place on the FP32 SIMT kernel (the rule of project_layer)
+    const bool small = ar.mixed && small_products(C, rs);
+    if (ar.mixed && !ar.tight && !small && resid && C.dtype == BHT_F32) {
       std::vector<const double*> Qs;
       std::vector<int64_t> qcs;
       for (int id : ids) {
@@ -1168,9 +1180,9 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
         qcs.push_back(qcols(id));
       }
       C = project_layer_tc(std::move(C), ids, Us, rs, &Qs, &qcs, resid, ar, s, st);
-    } else if (ar.mixed && !ar.tight && C.dtype == BHT_F32) {
+    } else if (ar.mixed && !ar.tight && !small && C.dtype == BHT_F32) {
       C = project_layer_tc(std::move(C), ids, Us, rs, nullptr, nullptr, nullptr, ar, s, st);
-    } else if (ar.mixed && resid) {
+    } else if (ar.mixed && (resid || small)) {
       std::vector<std::pair<int, int64_t>> ops;
       for (size_t k = 0; k < ids.size(); ++k) ops.push_back({C.axis_of(ids[k]), rs[k]});
       for (int k : best_order(C.dims, ops)) {
@@ -1533,34 +1545,43 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
     ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
     const Arith ar = make_arith(st->precision, eps_rel, st->d_status);
     const bool adaptive = st->budget == BHT_BUDGET_ADAPTIVE;
-    // Sibling leaves of the deepest layer at adjacent axes (a, a + 1) whose two-mode pass applies: both
-    // Gram matrices from one read of the batch, and ||Y||^2 as the trace of the first of them.
+    // Adjacent axes (a, a + 1) of a layer's intermediate whose two-mode pass applies: both Gram matrices
+    // from one read of the intermediate (at the deepest layer, the batch: ||Y||^2 is then the trace of
+    // the first of them), and later both projections from one more read.
     struct LeafPair {
       int ax, ida, idb;
       int64_t A, B;
       DBuf Ga, Gb;
     };
-    std::vector<LeafPair> pairs;
-    if (ar.pairs && !plain && !adaptive && dtype == BHT_F32 && (reinterpret_cast<uintptr_t>(dY) & 15) == 0) {
-      for (int m = 0; m + 1 < t.d; ++m) {
-        const int ida = t.leaf_of_mode[m], idb = t.leaf_of_mode[m + 1];
-        if (t.nodes[ida].parent != t.nodes[idb].parent || t.nodes[ida].layer != t.p || t.nodes[idb].layer != t.p) continue;
-        int64_t A = N, B = 1;
-        for (int k = 0; k < m; ++k) A *= t.dims[k];
-        for (int k = m + 2; k < t.d; ++k) B *= t.dims[k];
-        if (!pair_gram_supported(A, t.dims[m], t.dims[m + 1], B)) continue;
-        LeafPair lp{m, ida, idb, A, B, DBuf(sizeof(double) * t.dims[m] * t.dims[m], s),
-                    DBuf(sizeof(double) * t.dims[m + 1] * t.dims[m + 1], s)};
-        ck(cudaMemsetAsync(lp.Ga.p, 0, sizeof(double) * t.dims[m] * t.dims[m], s), "memset");
-        ck(cudaMemsetAsync(lp.Gb.p, 0, sizeof(double) * t.dims[m + 1] * t.dims[m + 1], s), "memset");
-        note_read(dY);
-        ck(launch_pair_gram(static_cast<const float*>(dY), A, (int)t.dims[m], (int)t.dims[m + 1], B,
-                            lp.Ga.as<double>(), lp.Gb.as<double>(), st->d_status, s),
+    auto find_pairs = [&](const LTensor& Cl, const std::vector<int>& lids) {
+      std::vector<LeafPair> out;
+      if (!ar.pairs || plain || adaptive || Cl.dtype != BHT_F32 || (reinterpret_cast<uintptr_t>(Cl.ptr) & 15) != 0)
+        return out;
+      const int na_ax = (int)Cl.dims.size();
+      for (int m = 0; m + 1 < na_ax; ++m) {
+        const int ida = Cl.node[m], idb = Cl.node[m + 1];
+        if (std::find(lids.begin(), lids.end(), ida) == lids.end() ||
+            std::find(lids.begin(), lids.end(), idb) == lids.end())
+          continue;
+        int64_t A = Cl.N, B = 1;
+        for (int k = 0; k < m; ++k) A *= Cl.dims[k];
+        for (int k = m + 2; k < na_ax; ++k) B *= Cl.dims[k];
+        if (!pair_gram_supported(A, Cl.dims[m], Cl.dims[m + 1], B)) continue;
+        const int64_t na = Cl.dims[m], nb = Cl.dims[m + 1];
+        LeafPair lp{m, ida, idb, A, B, DBuf(sizeof(double) * na * na, s), DBuf(sizeof(double) * nb * nb, s)};
+        ck(cudaMemsetAsync(lp.Ga.p, 0, sizeof(double) * na * na, s), "memset");
+        ck(cudaMemsetAsync(lp.Gb.p, 0, sizeof(double) * nb * nb, s), "memset");
+        note_read(Cl.ptr);
+        ck(launch_pair_gram(static_cast<const float*>(Cl.ptr), A, (int)na, (int)nb, B, lp.Ga.as<double>(),
+                            lp.Gb.as<double>(), st->d_status, s),
            "two-mode Gram pass");
-        pairs.push_back(std::move(lp));
+        out.push_back(std::move(lp));
         ++m;
       }
-    }
+      return out;
+    };
+    std::vector<LeafPair> pairs =
+        find_pairs(input_tensor(t, dY, dtype, N), std::vector<int>(t.layers[t.p].begin(), t.layers[t.p].end()));
     DBuf acc(sizeof(double) * 2, s);
     ck(cudaMemsetAsync(acc.p, 0, sizeof(double), s), "memset");
     if (!pairs.empty())
@@ -1607,6 +1628,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
       }
       if (layer < t.p) reshape_to_layer(t, C, layer);
       const auto& ids = t.layers[layer];
+      if (layer < t.p) pairs = find_pairs(C, std::vector<int>(ids.begin(), ids.end()));
       for (int id : ids)
         if (C.dims[C.axis_of(id)] > 4096)
           fail(BHT_ECAPACITY, "a node's unfolding has more than 4096 rows (the eigensolver's limit)");
@@ -1623,8 +1645,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         {
           DBuf G(sizeof(double) * I * I, sk);
           const DBuf* pg = nullptr;
-          if (layer == t.p)
-            for (const LeafPair& lp : pairs) pg = (lp.ida == id) ? &lp.Ga : (lp.idb == id) ? &lp.Gb : pg;
+          for (const LeafPair& lp : pairs) pg = (lp.ida == id) ? &lp.Ga : (lp.idb == id) ? &lp.Gb : pg;
           if (pg)
             ck(cudaMemcpyAsync(G.p, pg->p, sizeof(double) * I * I, cudaMemcpyDeviceToDevice, sk), "pair Gram");
           else
@@ -1650,12 +1671,12 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         for (int id : ids) rows[id] = st->rows(id);
         C = project_layer_removed(std::move(C), ids, st->U, st->Q, st->rank, t, rows, ar, s, removed.as<double>());
       } else {
-        // the leaf pairs two modes at a time (pairs later in the mode order first, so that the views of
-        // the earlier ones keep their sizes), then any other node of the layer
+        // the pairs two axes at a time (pairs later in the axis order first, so that the views of the
+        // earlier ones keep their sizes), then any other node of the layer
         std::vector<int> rest_ids;
         std::vector<const double*> rest_Us;
         std::vector<int64_t> rest_rs;
-        if (layer == t.p && !pairs.empty()) {
+        if (!pairs.empty()) {
           for (auto it = pairs.rbegin(); it != pairs.rend(); ++it) {
             const int64_t ra = st->rank[it->ida], rb = st->rank[it->idb];
             const int64_t na = C.dims[it->ax], nb = C.dims[it->ax + 1];
