@@ -345,7 +345,7 @@ bht_status bht_probe_fma_rate(int32_t dtype, double* tflops, void* stream);
 /* Optional kernel timing. With bit c of class_mask set, every launch of
  * kernel class c made by the calling thread is bracketed by a CUDA event pair
  * recorded on its launch stream. bht_profile_read() waits for the recorded
- * events and returns, per class c < n (n >= 10), the summed durations in ms,
+ * events and returns, per class c < n (n >= 18), the summed durations in ms,
  * the launch counts and the algorithmic work of the timed launches (flops and
  * bytes the mathematics of each launch requires); reset != 0 clears them.
  * Any output pointer may be NULL. Class names come from bht_kernel_class_name(c). */

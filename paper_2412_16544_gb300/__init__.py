@@ -117,7 +117,7 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items",
             "bht_synth_chebyshev", "bht_probe_fma_rate", "bht_pair_gram", "bht_pair_project", "bht_batch_reads",
             "bht_debug_withhold_barrier"]
-KERNEL_CLASSES = 16
+KERNEL_CLASSES = 18
 
 
 def _check(status: int, where: str):

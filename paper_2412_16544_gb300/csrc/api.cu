@@ -168,7 +168,8 @@ const char* kernel_class_name(int cls) {
   static const char* names[K_NUM_CLASSES] = {"gram_f64",       "ttm_f64",        "eig_tridiag_f64", "eig_bisect_f64",
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
-                                             "house_f64",      "mlp",            "prep",            "other"};
+                                             "house_f64",      "mlp",            "prep",            "other",
+                                             "pair_proj",      "pair_gram"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -346,14 +347,17 @@ struct bht_state {
   int64_t n_items = 0;
   int* d_status = nullptr;      // device status word of bounded waits
   bool plain = false;           // plain HT of one tensor (n_1..n_d, N): the batch is a leaf, not the root's
-  // Tensor-core weight planes of committed cores (and their complements), prepared once: the cores of a
-  // skipped update do not change. Keyed by the core pointers; entries go when a core is released.
+  // Tensor-core weight planes (kind 1) and FP32 copies [S1 + S2][T] for the SIMT kernel (kind 2, the
+  // basis read as M(s, t) = U[s ms + t mt]) of committed cores and their complements, prepared once:
+  // the cores of a skipped update do not change. Keyed by the core pointers; entries go when a core is
+  // released.
   struct TcWeights {
     const double* U;
     const double* Q;
     int64_t S1, S2, T, kv;
     int transpose;
     float* W;
+    int64_t ms = 0, mt = 0;
   };
   mutable std::vector<TcWeights> wcache;
   mutable std::mutex wmu;
@@ -542,6 +546,30 @@ const float* state_weights(const bht_state* st, const double* U, int64_t S1, con
   return W;
 }
 
+// FP32 copy [S1 + S2][T] of a committed core (M(s, t) = U[s ms + t mt], s < S1) followed by its
+// complement Q [T][S2] read transposed, for the FP32 SIMT mode product: made on first use for the
+// state, then reused until the core is released.
+const float* state_basis32(const bht_state* st, const double* U, int64_t ms, int64_t mt, int64_t S1, const double* Q,
+                           int64_t S2, int64_t T, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(st->wmu);
+  for (const auto& w : st->wcache)
+    if (w.transpose == 2 && w.U == U && w.Q == Q && w.S1 == S1 && w.S2 == S2 && w.T == T && w.ms == ms && w.mt == mt)
+      return w.W;
+  float* W = static_cast<float*>(dalloc(sizeof(float) * (size_t)std::max<int64_t>((S1 + S2) * T, 1), s));
+  try {
+    ck(launch_cast_matrix(U, ms, mt, S1, T, W, s), "basis to FP32");
+    if (Q && S2 > 0) ck(launch_cast_matrix(Q, 1, S2, S2, T, W + S1 * T, s), "complement to FP32");
+  } catch (...) {
+    dfree(W, s);
+    throw;
+  }
+  bht_state::TcWeights e{U, Q, S1, S2, T, -1, 2, W};
+  e.ms = ms;
+  e.mt = mt;
+  st->wcache.push_back(e);
+  return W;
+}
+
 // Drop the cached weights that read the core or complement p (before p is released).
 void purge_weights(const bht_state* st, const double* p, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(st->wmu);
@@ -622,16 +650,21 @@ LTensor ttm_any(const LTensor& C, int axis, const double* U, int64_t ms, int64_t
     return out;
   }
   if (k_valid >= 0) fail(BHT_EINVAL, "internal: padded axis outside the tensor-core kernel");
-  // the basis enters the FP32 SIMT kernel as an FP32 copy [S][T]
-  DBuf M32(sizeof(float) * (size_t)std::max<int64_t>(S * T, 1), s);
-  ck(launch_cast_matrix(U, ms, mt, S, T, M32.as<float>(), s), "basis to FP32");
+  // the basis enters the FP32 SIMT kernel as an FP32 copy [S][T] (the state's, for a committed core)
+  DBuf M32b;
+  const float* M32 = nullptr;
+  if (cache) {
+    M32 = state_basis32(cache, U, ms, mt, S, nullptr, 0, T, s);
+  } else {
+    M32b = DBuf(sizeof(float) * (size_t)std::max<int64_t>(S * T, 1), s);
+    ck(launch_cast_matrix(U, ms, mt, S, T, M32b.as<float>(), s), "basis to FP32");
+    M32 = M32b.as<float>();
+  }
   if (C.dtype == BHT_F32)
-    ck(launch_ttm_f32<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T, B, S,
-                             R2, s),
+    ck(launch_ttm_f32<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32, T, 1, A, T, B, S, R2, s),
        "ttm");
   else
-    ck(launch_ttm_f32<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T, B,
-                              S, R2, s),
+    ck(launch_ttm_f32<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32, T, 1, A, T, B, S, R2, s),
        "ttm");
   return out;
 }
@@ -684,17 +717,24 @@ LTensor ttm_proj_resid(const LTensor& C, int axis, const double* U, int64_t r, c
     return out;
   }
   if (k_valid >= 0) fail(BHT_EINVAL, "internal: padded axis outside the tensor-core kernel");
-  // FP32 SIMT on [U | Q] cast to fp32 [r + c][T]
-  DBuf M32(sizeof(float) * (size_t)std::max<int64_t>((r + c) * T, 1), s);
-  ck(launch_cast_matrix(U, 1, r, r, T, M32.as<float>(), s), "basis to FP32");
-  ck(launch_cast_matrix(Q, 1, c, c, T, M32.as<float>() + r * T, s), "complement to FP32");
+  // FP32 SIMT on [U | Q] cast to fp32 [r + c][T] (the state's copy, for a committed core)
+  DBuf M32b;
+  const float* M32 = nullptr;
+  if (cache) {
+    M32 = state_basis32(cache, U, 1, r, r, Q, c, T, s);
+  } else {
+    M32b = DBuf(sizeof(float) * (size_t)std::max<int64_t>((r + c) * T, 1), s);
+    ck(launch_cast_matrix(U, 1, r, r, T, M32b.as<float>(), s), "basis to FP32");
+    ck(launch_cast_matrix(Q, 1, c, c, T, M32b.as<float>() + r * T, s), "complement to FP32");
+    M32 = M32b.as<float>();
+  }
   if (C.dtype == BHT_F32)
-    ck(launch_ttm_f32_resid<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A, T,
-                                   B, r + c, r, R2, resid, s),
+    ck(launch_ttm_f32_resid<float>(static_cast<const float*>(C.ptr), out.own.as<float>(), M32, T, 1, A, T, B, r + c,
+                                   r, R2, resid, s),
        "ttm");
   else
-    ck(launch_ttm_f32_resid<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32.as<float>(), T, 1, A,
-                                    T, B, r + c, r, R2, resid, s),
+    ck(launch_ttm_f32_resid<double>(static_cast<const double*>(C.ptr), out.own.as<float>(), M32, T, 1, A, T, B,
+                                    r + c, r, R2, resid, s),
        "ttm");
   return out;
 }
@@ -1188,7 +1228,7 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
       for (int k : best_order(C.dims, ops)) {
         const int id = ids[k];
         LTensor nxt = ttm_proj_resid(C, C.axis_of(id), st->U[id], rs[k], st->Q[id], qcols(id), false, ar, s,
-                                     nullptr, nullptr, resid);
+                                     nullptr, nullptr, resid, -1, st);
         C = std::move(nxt);
       }
     } else {

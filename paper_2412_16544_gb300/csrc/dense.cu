@@ -236,17 +236,20 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
                                                       int64_t A, int64_t T, int64_t B, int64_t S, int64_t R2,
                                                       int64_t S_store, double* __restrict__ resid) {
   constexpr int PER = BK * TILE / NT;  // staged X elements per thread
-  __shared__ Acc Ms[BK][TILE + 1];
-  __shared__ Acc Xs[BK][TILE + 1];
+  // rows padded to TILE + 4: 16-byte aligned for the vector reads of the product, and a stage written
+  // along k spreads over the banks
+  __shared__ __align__(16) Acc Ms[BK][TILE + 4];
+  __shared__ __align__(16) Acc Xs[BK][TILE + 4];
   const int64_t c0 = (int64_t)blockIdx.x * TILE;
   const int64_t s0 = (int64_t)blockIdx.y * TILE;
   const int64_t AB = A * B;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool m_along_s = (ms == 1);
   const bool x_along_c = B >= 8;
-  // the column c = a * B + b of every staged X element is fixed across the T stages
-  int xkk[PER], xcc[PER];
-  int64_t xoff[PER];
+  // the column c = a * B + b of every staged X element, and the output index s of every staged M
+  // element, are fixed across the T stages
+  int xkk[PER], xcc[PER], mkk[PER], mss[PER];
+  int64_t xoff[PER], moff[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int e = threadIdx.x + q * NT;
@@ -254,6 +257,9 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
     const int64_t c = c0 + xcc[q];
     const int64_t a = c / B, b = c - a * B;
     xoff[q] = (c < AB) ? a * T * B + b : -1;
+    if (m_along_s) { mss[q] = e % TILE; mkk[q] = e / TILE; } else { mkk[q] = e % BK; mss[q] = e / BK; }
+    const int64_t sidx = s0 + mss[q];
+    moff[q] = (sidx < S) ? sidx * ms : -1;
   }
   Acc acc[4][4];
 #pragma unroll
@@ -261,26 +267,32 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = Acc(0);
 
-  for (int64_t t0 = 0; t0 < T; t0 += BK) {
-    for (int e = threadIdx.x; e < BK * TILE; e += NT) {
-      int kk, ss;
-      if (m_along_s) { ss = e % TILE; kk = e / TILE; } else { kk = e % BK; ss = e / BK; }
-      const int64_t t = t0 + kk, sidx = s0 + ss;
-      Ms[kk][ss] = (t < T && sidx < S) ? static_cast<Acc>(M[sidx * ms + t * mt]) : Acc(0);
-    }
+  // the next stage's operands are loaded into registers while the current one is multiplied
+  Acc xr[PER], mr[PER];
+  auto fetch = [&](int64_t t0) {
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      const int64_t t = t0 + xkk[q];
-      Xs[xkk[q]][xcc[q]] = (t < T && xoff[q] >= 0) ? static_cast<Acc>(X[xoff[q] + t * B]) : Acc(0);
+      const int64_t tx_ = t0 + xkk[q], tm_ = t0 + mkk[q];
+      xr[q] = (tx_ < T && xoff[q] >= 0) ? static_cast<Acc>(X[xoff[q] + tx_ * B]) : Acc(0);
+      mr[q] = (tm_ < T && moff[q] >= 0) ? static_cast<Acc>(M[moff[q] + tm_ * mt]) : Acc(0);
+    }
+  };
+  fetch(0);
+  for (int64_t t0 = 0; t0 < T; t0 += BK) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      Xs[xkk[q]][xcc[q]] = xr[q];
+      Ms[mkk[q]][mss[q]] = mr[q];
     }
     __syncthreads();
+    if (t0 + BK < T) fetch(t0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       Acc a[4], b[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = Ms[kk][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = Ms[kk][4 * ty + u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Xs[kk][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) b[v] = Xs[kk][4 * tx + v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -291,14 +303,14 @@ __global__ void __launch_bounds__(NT) ttm_simt_kernel(const Tin* __restrict__ X,
   double rq = 0.0;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const int64_t c = c0 + tx + 16 * v;
+    const int64_t c = c0 + 4 * tx + v;
     if (c >= AB) continue;
     const int64_t a = c / B, b = c - a * B;
     // B > 1: out[a][s][b]; B == 1: the new axis goes in front of the last R2 rows
     const int64_t o = a / R2, i = a - o * R2;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int64_t sidx = s0 + ty + 16 * u;
+      const int64_t sidx = s0 + 4 * ty + u;
       if (sidx < S_store) {
         const int64_t off = (B > 1) ? (a * S_store + sidx) * B + b : (o * S_store + sidx) * R2 + i;
         out[off] = static_cast<Tout>(acc[u][v]);

@@ -32,7 +32,9 @@ enum KernelClass {
   K_MLP = 13,
   K_PREP = 14,
   K_OTHER = 15,
-  K_NUM_CLASSES = 16
+  K_PAIR_PROJ = 16,  // two-mode projections of small leaves (pair.cu)
+  K_PAIR_GRAM = 17,  // two-mode Gram passes (pair.cu)
+  K_NUM_CLASSES = 18
 };
 const char* kernel_class_name(int cls);
 

@@ -278,20 +278,27 @@ __global__ void __launch_bounds__(PROJ_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Warp-specialised projection for ranks <= 8, na <= 24 and nb <= 32. Lane (g, p) of a warp owns the
-// four columns 4g .. 4g+3 of a tile and two output indices (p and p + 4); the basis columns it needs
-// live in its registers, so one 16-byte shared load of a tile row feeds eight FMAs and no basis is
-// ever re-read from shared memory.
-//   stage 1 (ka warps, warp i = row i of a band of ka rows): Z[i][b][c] = sum_j T[i][j][c] Ub[j][b];
-//   stage 2 (8 warps, warp b): W[a][b][c] = sum_i Ua[i][a] Z[i][b][c] over the na rows of a tile, once
-//   per tile, written with 16-byte stores.
-// Z holds a whole tile, double-buffered by tile parity and handed over through named barriers:
-//   ZFULL[z] (ids 2, 3): stage 1 arrives after the last band of a tile, stage 2 waits;
-//   ZEMPTY[z] (ids 4, 5): stage 2 arrives when it has read Z[z], stage 1 waits before the first band of
-//   the tile after next; S1 (id 1): the stage-1 warps among themselves.
+// Warp-specialised projection for ranks <= 8, na = nb = 24. The basis entries a lane needs live in
+// its registers, so no basis is ever re-read from shared memory.
+//   stage 1 (ka warps, warp i = row i of a band of ka rows): Z[i][b][c] = sum_j T[i][j][c] Ub[j][b].
+//   Lane (g, p) = lane (8 p + g) owns the four columns 4g .. 4g+3 and the six rows j = p, p+4, ...;
+//   a quarter-warp reads one whole 128-byte row, so every 16-byte load is a distinct word of shared
+//   memory and feeds 32 FMAs (all eight outputs b). The four partial sums of an output are then
+//   reduce-scattered over the lanes p = 0..3 with two rounds of shuffles, after which lane p holds
+//   outputs p and p + 4. Lane p keeps its outputs in the order b = slot XOR p (its basis registers
+//   are loaded in that order), so both rounds keep the even / low slots without any select.
+//   stage 2 (4 warps, warp w: b = w and w + 4): W[a][b][c] = sum_i Ua[i][a] Z[i][b][c] over the na
+//   rows of a tile; lane (g, p) owns the four columns 4g .. 4g+3 and a = p, p + 4; once per tile,
+//   written with 16-byte stores.
+// A unit is one band of ka rows of mode a; two bands make a tile. Z holds one band and is
+// double-buffered by unit parity, handed over through named barriers:
+//   ZFULL[z] (ids 2, 3): stage 1 arrives after it has written Z[z] (and read the band's TMA stage),
+//   stage 2 waits; ZEMPTY[z] (ids 4, 5): stage 2 arrives when it has read Z[z], stage 1 waits before
+//   it writes Z[z] again; S1 (id 1): the stage-1 warps among themselves.
 // Thread 0 alone waits on each TMA barrier (bounded) and tells the stage-1 warps through shared memory;
-// a wait that gave up raises an abort flag that stage 2 reads after its next ZFULL wait, so every named
-// barrier still sees matching arrivals on both sides and both roles leave together.
+// the first stage-2 thread issues the loads and refills a stage once ZFULL says stage 1 is done with
+// it. A wait that gave up raises an abort flag that stage 2 reads after its next ZFULL wait, so every
+// named barrier still sees matching arrivals on both sides and both roles leave together.
 // ---------------------------------------------------------------------------------------------
 constexpr int WS_W2 = 4;  // stage-2 warps, two output indices of mode b each
 constexpr int WS_MAX_THREADS = 32 * (12 + WS_W2);
@@ -333,11 +340,11 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wsm) + 1023) & ~(uintptr_t)1023);
   float* Zb = reinterpret_cast<float*>(base + (size_t)pg.nst * pg.stage_bytes);  // [2][KA][8][32]
   __shared__ __align__(8) uint64_t full[PROJ_STAGES_MAX];
-  __shared__ int sflag, abort_flag;
+  __shared__ int sflag[2], abort_flag;
   __shared__ double red[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W1 = pg.ka, NT = (int)blockDim.x;
-  const int gq = lane >> 2, pq = lane & 3;  // columns 4 gq .. 4 gq + 3, output indices pq and pq + 4
+  const int gq = lane >> 2, pq = lane & 3;  // stage 2: columns 4 gq .. 4 gq + 3, outputs a = pq, pq + 4
   const size_t zsize = (size_t)KA * 8 * PCOLS;
   if (tid == 0) {
     for (int st = 0; st < pg.nst; ++st) tma::mbar_init(&full[st], 1);
@@ -347,157 +354,155 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
   __syncthreads();
   // each CTA takes a contiguous run of tiles (consecutive column blocks of the same rows), so that its
   // successive loads continue the DRAM pages of its previous ones
-  const int64_t per = (g.ntiles + gridDim.x - 1) / gridDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * per;
-  const int64_t my_tiles = (g.ntiles > t0) ? min(per, g.ntiles - t0) : 0;
-  const int64_t my_units = my_tiles * pg.nbands;
+  // (the launcher keeps ntiles * nbands below 2^31, so tile and unit counters fit 32 bits)
+  const int per = (int)((g.ntiles + gridDim.x - 1) / gridDim.x);
+  const int t0 = (int)blockIdx.x * per;
+  const int my_tiles = (g.ntiles > t0) ? min(per, (int)g.ntiles - t0) : 0;
+  const int my_units = my_tiles * pg.nbands;
   double sx = 0.0, sy = 0.0;
   if (warp < W1) {
     // ---------------- stage 1 ----------------
-    float u0[NB], u1[NB];  // Ub[j][pq], Ub[j][pq + 4]
+    static_assert(NB % 8 == 0, "rows of a warp start on a swizzle period");
+    constexpr int JR = NB / 4;              // rows j = 4 m + p of lane (g, p), m < JR
+    const int g1 = lane & 7, p1 = lane >> 3;  // stage-1 lane (g1, p1)
+    float2 u[JR][4];  // u[m][h] = (Ub[4 m + p1][2h ^ p1], Ub[4 m + p1][(2h + 1) ^ p1]): slots 2h, 2h + 1
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      u0[j] = (j < g.nb && pq < rb) ? (float)Ub[(int64_t)j * ldb + pq] : 0.f;
-      u1[j] = (j < g.nb && pq + 4 < rb) ? (float)Ub[(int64_t)j * ldb + pq + 4] : 0.f;
-    }
-    int64_t issued = 0, u_t = t0;
-    int u_b = 0;
-    if (tid == 0) {
-      for (; issued < my_units && issued < pg.nst; ++issued) {
-        issue_band(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg, u_t * pg.nbands + u_b);
-        if (++u_b == pg.nbands) {
-          u_b = 0;
-          ++u_t;
-        }
+    for (int m = 0; m < JR; ++m)
+#pragma unroll
+      for (int hh = 0; hh < 4; ++hh) {
+        const int j = 4 * m + p1, b0 = (2 * hh) ^ p1, b1 = (2 * hh + 1) ^ p1;
+        u[m][hh].x = (j < g.nb && b0 < rb) ? (float)Ub[(int64_t)j * ldb + b0] : 0.f;
+        u[m][hh].y = (j < g.nb && b1 < rb) ? (float)Ub[(int64_t)j * ldb + b1] : 0.f;
       }
-    }
-    int64_t k = 0, tk = 0, posted = 0;
-    int s = 0, band = 0;
+    int k = 0, posted = 0;  // units consumed; Z buffers handed to stage 2
+    int s = 0;
     float sx_hi = 0.f, sx_lo = 0.f;
     uint32_t par = 0;
     for (; k < my_units; ++k) {
-      if (tid == 0) sflag = tma::mbar_wait(&full[s], par, status) ? 0 : 1;
+      // the verdict of the wait is double-buffered: thread 0 may run one unit ahead of a slow warp
+      if (tid == 0) sflag[k & 1] = tma::mbar_wait(&full[s], par, status) ? 0 : 1;
       named_sync(1, 32 * W1);
-      const bool abort_now = sflag != 0;
-      const int zb = (int)(tk & 1);
-      if (tk >= 2) named_sync(4 + zb, NT);  // stage 2 has read Z[zb] (unit tk - 2)
+      const bool abort_now = sflag[k & 1] != 0;
+      const int zb = k & 1;
+      if (k >= 2) named_sync(4 + zb, NT);  // stage 2 has read Z[zb] (unit k - 2)
       if (abort_now) {
         if (tid == 0) abort_flag = 1;
-        named_arrive(2 + zb, NT);  // wake stage 2 for unit tk; it sees the flag and leaves
+        named_arrive(2 + zb, NT);  // wake stage 2 for unit k; it sees the flag and leaves
         ++posted;
         break;
       }
       const uint8_t* T = base + (size_t)s * pg.stage_bytes;
       if (warp < KA) {
-        float acc[8];
+        float2 acc[4][4];  // acc[c][h] = slots (2h, 2h + 1) of column c, two FMAs per packed instruction
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-        float2 xx2 = make_float2(0.f, 0.f);  // every lane of a column group squares the same four values
-        // rows r = warp NB + j with NB % 8 == 0: the swizzle of row r is j mod 8, a constant of the unrolled loop
-        const uint8_t* Tw = T + (size_t)warp * NB * 128;
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          const float4 x = *reinterpret_cast<const float4*>(Tw + j * 128 + ((gq ^ (j & 7)) << 4));
+          for (int hh = 0; hh < 4; ++hh) acc[c][hh] = make_float2(0.f, 0.f);
+        float2 xx2 = make_float2(0.f, 0.f);
+        // row r = warp NB + 4 m + p1 has swizzle (4 m + p1) mod 8 = 4 (m mod 2) + p1, so the 16-byte
+        // chunk of columns 4 g1 .. 4 g1 + 3 sits at g1 ^ p1 ^ 4 (m mod 2)
+        const uint8_t* Tw = T + (size_t)(warp * NB + p1) * 128;
+        const int ch = g1 ^ p1;
+#pragma unroll
+        for (int m = 0; m < JR; ++m) {
+          const float4 x = *reinterpret_cast<const float4*>(Tw + m * 512 + ((ch ^ ((m & 1) << 2)) << 4));
           xx2 = ffma2(make_float2(x.x, x.y), make_float2(x.x, x.y), xx2);
           xx2 = ffma2(make_float2(x.z, x.w), make_float2(x.z, x.w), xx2);
-          acc[0] = fmaf(x.x, u0[j], acc[0]);
-          acc[1] = fmaf(x.y, u0[j], acc[1]);
-          acc[2] = fmaf(x.z, u0[j], acc[2]);
-          acc[3] = fmaf(x.w, u0[j], acc[3]);
-          acc[4] = fmaf(x.x, u1[j], acc[4]);
-          acc[5] = fmaf(x.y, u1[j], acc[5]);
-          acc[6] = fmaf(x.z, u1[j], acc[6]);
-          acc[7] = fmaf(x.w, u1[j], acc[7]);
+          const float xc[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 xd = make_float2(xc[c], xc[c]);
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) acc[c][hh] = ffma2(xd, u[m][hh], acc[c][hh]);
+          }
         }
-        float* Z = Zb + (size_t)zb * zsize + (size_t)warp * 8 * PCOLS;
-        *reinterpret_cast<float4*>(Z + pq * PCOLS + 4 * gq) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *reinterpret_cast<float4*>(Z + (pq + 4) * PCOLS + 4 * gq) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        // reduce-scatter over p1: the partner p1 ^ 1 holds in slot 2h + 1 the output that slot 2h
+        // holds here, and p1 ^ 2 in slot 4h' + 2 what slot 4h' holds here
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int hh = 0; hh < 4; ++hh) acc[c][hh].x += __shfl_xor_sync(0xffffffffu, acc[c][hh].y, 8);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[c][0].x += __shfl_xor_sync(0xffffffffu, acc[c][1].x, 16);
+          acc[c][2].x += __shfl_xor_sync(0xffffffffu, acc[c][3].x, 16);
+        }
+        // slots 0 and 4 hold outputs p1 and p1 + 4
+        float* Z = Zb + (size_t)zb * zsize + (size_t)(warp * 8 + p1) * PCOLS + 4 * g1;
+        *reinterpret_cast<float4*>(Z) = make_float4(acc[0][0].x, acc[1][0].x, acc[2][0].x, acc[3][0].x);
+        *reinterpret_cast<float4*>(Z + 4 * PCOLS) = make_float4(acc[0][2].x, acc[1][2].x, acc[2][2].x, acc[3][2].x);
         ds_add(xx2.x + xx2.y, sx_hi, sx_lo);
-      }
-      named_sync(1, 32 * W1);  // every stage-1 read of stage s done
-      if (tid == 0 && issued < my_units) {
-        issue_band(&map, &full[s], base + (size_t)s * pg.stage_bytes, g, pg, u_t * pg.nbands + u_b);
-        ++issued;
-        if (++u_b == pg.nbands) {
-          u_b = 0;
-          ++u_t;
-        }
       }
       if (++s == pg.nst) {
         s = 0;
         par ^= 1u;
       }
-      named_arrive(2 + zb, NT);  // Z[zb] holds this band
+      // Z[zb] holds this band, and every stage-1 read of this band's stage is done: stage 2 refills it
+      named_arrive(2 + zb, NT);
       ++posted;
-      ++tk;
-      if (++band == pg.nbands) band = 0;
     }
     // the Z buffers of the last (up to) two tiles posted: wait until stage 2 has read them
-    for (int64_t q = (posted >= 2 ? posted - 2 : 0); q < posted; ++q) named_sync(4 + (int)(q & 1), NT);
-    if (tid == 0 && sflag != 0) {
-      // drain the loads still in flight after a wait gave up (bounded, ignoring the status word)
-      for (int64_t q = k; q < issued; ++q) {
-        const int sq = (int)(q % pg.nst);
-        const uint32_t pp = (uint32_t)((q / pg.nst) & 1);
-        const uint64_t t0 = tma::gtimer();
-        uint32_t ok = 0;
-        while (!ok && tma::gtimer() - t0 < DRAIN_NS) {
-          asm volatile(
-              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-              : "=r"(ok)
-              : "r"(tma::smem_u32(&full[sq])), "r"(pp)
-              : "memory");
-        }
-        if (!ok) break;
-      }
-    }
-    // each of the four lanes of a column group counted the same squares
-    sx = 0.25 * ((double)sx_hi + (double)sx_lo);
+    for (int q = (posted >= 2 ? posted - 2 : 0); q < posted; ++q) named_sync(4 + (q & 1), NT);
+    // every element of a band was squared by exactly one lane
+    sx = (double)sx_hi + (double)sx_lo;
   } else {
     // ---------------- stage 2 ----------------
     const int b0 = warp - W1, b1 = b0 + WS_W2;  // output indices of mode b of this warp
-    float v0[NA], v1[NA];  // Ua[i][pq], Ua[i][pq + 4]
+    float2 v[NA];  // (Ua[i][pq], Ua[i][pq + 4])
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      v0[i] = (i < g.na && pq < ra) ? (float)Ua[(int64_t)i * lda + pq] : 0.f;
-      v1[i] = (i < g.na && pq + 4 < ra) ? (float)Ua[(int64_t)i * lda + pq + 4] : 0.f;
+      v[i].x = (i < g.na && pq < ra) ? (float)Ua[(int64_t)i * lda + pq] : 0.f;
+      v[i].y = (i < g.na && pq + 4 < ra) ? (float)Ua[(int64_t)i * lda + pq + 4] : 0.f;
     }
-    float acc[16];  // [b0, b1][a = pq, pq + 4][4 columns]
+    float2 acc[2][4];  // acc[b0 or b1][column] = (a = pq, a = pq + 4)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[hb][c] = make_float2(0.f, 0.f);
     float sy_hi = 0.f, sy_lo = 0.f;
-    int64_t t = t0;
-    for (int64_t k = 0; k < my_units; ++k) {
-      const int zb = (int)(k & 1), band = (int)(k & 1);  // two bands per tile
+    // the first stage-2 thread issues the TMA loads: unit u goes to stage u mod nst, refilled once
+    // stage 1 has posted the band that occupied it
+    const bool producer = tid == 32 * W1;
+    int issued = 0;
+    if (producer)
+      for (; issued < my_units && issued < pg.nst; ++issued)
+        issue_band(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg,
+                   (int64_t)t0 * pg.nbands + issued);
+    int t = t0, k = 0;
+    for (; k < my_units; ++k) {
+      const int zb = k & 1, band = k & 1;  // two bands per tile
       named_sync(2 + zb, NT);
       if (abort_flag) {
         named_arrive(4 + zb, NT);
         break;
       }
-      const float* Z = Zb + (size_t)zb * zsize + 4 * gq;
-#pragma unroll
-      for (int i = 0; i < KA; ++i) {
-        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b0) * PCOLS);
-        const float4 zc = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b1) * PCOLS);
-        const float w0 = band ? v0[KA + i] : v0[i];
-        const float w1 = band ? v1[KA + i] : v1[i];
-        acc[0] = fmaf(za.x, w0, acc[0]);
-        acc[1] = fmaf(za.y, w0, acc[1]);
-        acc[2] = fmaf(za.z, w0, acc[2]);
-        acc[3] = fmaf(za.w, w0, acc[3]);
-        acc[4] = fmaf(za.x, w1, acc[4]);
-        acc[5] = fmaf(za.y, w1, acc[5]);
-        acc[6] = fmaf(za.z, w1, acc[6]);
-        acc[7] = fmaf(za.w, w1, acc[7]);
-        acc[8] = fmaf(zc.x, w0, acc[8]);
-        acc[9] = fmaf(zc.y, w0, acc[9]);
-        acc[10] = fmaf(zc.z, w0, acc[10]);
-        acc[11] = fmaf(zc.w, w0, acc[11]);
-        acc[12] = fmaf(zc.x, w1, acc[12]);
-        acc[13] = fmaf(zc.y, w1, acc[13]);
-        acc[14] = fmaf(zc.z, w1, acc[14]);
-        acc[15] = fmaf(zc.w, w1, acc[15]);
+      if (producer && issued < my_units) {
+        const int sq = issued % pg.nst;  // == k mod nst: the stage unit k has just left
+        issue_band(&map, &full[sq], base + (size_t)sq * pg.stage_bytes, g, pg, (int64_t)t0 * pg.nbands + issued);
+        ++issued;
       }
+      const float* Z = Zb + (size_t)zb * zsize + 4 * gq;
+      // one unrolled copy per band, so the basis rows are picked at compile time
+      auto rows = [&](const float2* vb) {
+#pragma unroll
+        for (int i = 0; i < KA; ++i) {
+          const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b0) * PCOLS);
+          const float4 zc = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b1) * PCOLS);
+          const float2 w = vb[i];
+          acc[0][0] = ffma2(make_float2(za.x, za.x), w, acc[0][0]);
+          acc[0][1] = ffma2(make_float2(za.y, za.y), w, acc[0][1]);
+          acc[0][2] = ffma2(make_float2(za.z, za.z), w, acc[0][2]);
+          acc[0][3] = ffma2(make_float2(za.w, za.w), w, acc[0][3]);
+          acc[1][0] = ffma2(make_float2(zc.x, zc.x), w, acc[1][0]);
+          acc[1][1] = ffma2(make_float2(zc.y, zc.y), w, acc[1][1]);
+          acc[1][2] = ffma2(make_float2(zc.z, zc.z), w, acc[1][2]);
+          acc[1][3] = ffma2(make_float2(zc.w, zc.w), w, acc[1][3]);
+        }
+      };
+      if (band)
+        rows(v + KA);
+      else
+        rows(v);
       named_arrive(4 + zb, NT);  // Z[zb] read
       if (band == 1) {
         const int64_t aidx = t / g.ncb, col = (t - aidx * g.ncb) * PCOLS + 4 * gq;
@@ -510,8 +515,9 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
             for (int h = 0; h < 2; ++h) {
               const int a = pq + 4 * h;
               if (b < rb && a < ra) {
-                const float* q4 = acc + 8 * hb + 4 * h;
-                const float4 w = make_float4(q4[0], q4[1], q4[2], q4[3]);
+                const float2* q4 = acc[hb];
+                const float4 w = h ? make_float4(q4[0].y, q4[1].y, q4[2].y, q4[3].y)
+                                   : make_float4(q4[0].x, q4[1].x, q4[2].x, q4[3].x);
                 *reinterpret_cast<float4*>(out + ((aidx * ra + a) * rb + b) * g.B + col) = w;
                 yy = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, yy))));
               }
@@ -520,8 +526,27 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
           ds_add(yy, sy_hi, sy_lo);
         }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+        for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[hb][c] = make_float2(0.f, 0.f);
         ++t;
+      }
+    }
+    if (producer && k < my_units) {
+      // stage 1 gave up on a wait: drain the loads still in flight (bounded, ignoring the status word)
+      for (int q = k; q < issued; ++q) {
+        const int sq = q % pg.nst;
+        const uint32_t pp = (uint32_t)((q / pg.nst) & 1);
+        const uint64_t tw = tma::gtimer();
+        uint32_t ok = 0;
+        while (!ok && tma::gtimer() - tw < DRAIN_NS) {
+          asm volatile(
+              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+              : "=r"(ok)
+              : "r"(tma::smem_u32(&full[sq])), "r"(pp)
+              : "memory");
+        }
+        if (!ok) break;
       }
     }
     sy = (double)sy_hi + (double)sy_lo;
@@ -769,6 +794,7 @@ cudaError_t launch_proj_ws(const float* X, const PairGeom& g, const double* Ua, 
                            cudaStream_t s) {
   // two bands of 12 rows of mode a (na = 24), nb = 24
   if (g.na != 24 || g.nb != 24 || (g.B & 3) != 0) return cudaErrorInvalidValue;
+  if (g.ntiles * 2 > 0x7fffffffll) return cudaErrorInvalidValue;  // 32-bit unit counters in the kernel
   ProjGeom pg;
   pg.ka = 12;
   pg.nbands = 2;
@@ -820,7 +846,7 @@ cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t 
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.ntiles, sm_count());
   const double K = (double)A * (double)B;  // columns per row of either unfolding, over the whole tensor
-  ProfScope prof(K_GRAM_F32, s, (double)na * (na + 1) * K * nb + (double)nb * (nb + 1) * K * na,
+  ProfScope prof(K_PAIR_GRAM, s, (double)na * (na + 1) * K * nb + (double)nb * (nb + 1) * K * na,
                  4.0 * K * na * nb);
   pair_gram_kernel<<<grid, threads, smem, s>>>(m, g, wa, Ga, Gb, status);
   note_launch();
@@ -834,7 +860,7 @@ cudaError_t launch_pair_project(const float* X, int64_t A, int na, int nb, int64
     return cudaErrorInvalidValue;
   const PairGeom g = geom(A, na, nb, B);
   const double elems = (double)A * na * nb * (double)B;
-  ProfScope prof(K_TTM_F32, s, 2.0 * elems * rb + 2.0 * (double)A * na * rb * (double)B * ra,
+  ProfScope prof(K_PAIR_PROJ, s, 2.0 * elems * rb + 2.0 * (double)A * na * rb * (double)B * ra,
                  4.0 * elems + 4.0 * (double)A * ra * rb * (double)B);
   if (ra <= 8 && rb <= 8 && na == 24 && nb == 24) return launch_proj_ws(X, g, Ua, ra, lda, Ub, rb, ldb, out, norm_in, norm_out,
                                                             resid, status, s);
