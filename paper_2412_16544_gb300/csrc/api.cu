@@ -1850,11 +1850,17 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   LTensor Cbar = project_all(st, dY, dtype, N, ar, s, acc.as<double>(), &norm_done, resid);
   if (!norm_done) sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
   if (!ar.mixed) sqnorm_of(Cbar.ptr, Cbar.dtype, Cbar.numel(), acc.as<double>() + 1, s);
+  // the norms and the status word of the bounded waits come back together, after one synchronisation
   double h[3];
+  int hstat = 0;
   ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H norms");
+  ck(cudaMemcpyAsync(&hstat, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
   ck(cudaStreamSynchronize(s), "sync");
+  if (hstat != 0) {
+    cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
+    fail((bht_status)hstat, "a bounded device-side wait gave up");
+  }
   if (!std::isfinite(h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
-  check_status(st, s);
   const double eps_des = eps_rel * std::sqrt(h[0]);
   const double eps_proj = ar.mixed ? std::sqrt(std::max(h[2], 0.0))
                                    : std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold

@@ -111,6 +111,28 @@ __device__ __forceinline__ void issue_band(const CUtensorMap* map, uint64_t* bar
   tma::load_3d(map, bar, buf, (int)(cb * PCOLS), 0, (int)(a * g.na + band * pg.ka));
 }
 
+// The next band a CTA loads, advanced without divisions: (item row block a, column block cb, band).
+struct BandCursor {
+  int a, cb, band;
+  __device__ void start(int64_t tile, const PairGeom& g) {
+    a = (int)(tile / g.ncb);
+    cb = (int)(tile - (int64_t)a * g.ncb);
+    band = 0;
+  }
+  __device__ __forceinline__ void issue(const CUtensorMap* map, uint64_t* bar, uint8_t* buf, const PairGeom& g,
+                                        const ProjGeom& pg) {
+    tma::mbar_expect_tx(bar, pg.unit_bytes);
+    tma::load_3d(map, bar, buf, cb * PCOLS, 0, a * g.na + band * pg.ka);
+    if (++band == pg.nbands) {
+      band = 0;
+      if (++cb == (int)g.ncb) {
+        cb = 0;
+        ++a;
+      }
+    }
+  }
+};
+
 template <int RA, int RB>
 __global__ void __launch_bounds__(PROJ_THREADS, 1)
     pair_project_kernel(const __grid_constant__ CUtensorMap map, const PairGeom g, const ProjGeom pg,
@@ -291,14 +313,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, 1)
 //   rows of a tile; lane (g, p) owns the four columns 4g .. 4g+3 and a = p, p + 4; once per tile,
 //   written with 16-byte stores.
 // A unit is one band of ka rows of mode a; two bands make a tile. Z holds one band and is
-// double-buffered by unit parity, handed over through named barriers:
-//   ZFULL[z] (ids 2, 3): stage 1 arrives after it has written Z[z] (and read the band's TMA stage),
-//   stage 2 waits; ZEMPTY[z] (ids 4, 5): stage 2 arrives when it has read Z[z], stage 1 waits before
-//   it writes Z[z] again; S1 (id 1): the stage-1 warps among themselves.
+// triple-buffered by unit index, handed over through named barriers:
+//   ZFULL[z] (ids 2, 3, 4): stage 1 arrives after it has written Z[z] (and read the band's TMA
+//   stage), stage 2 waits; ZEMPTY[z] (ids 5, 6, 7): stage 2 arrives when it has read Z[z], stage 1
+//   waits before it writes Z[z] again; S1 (id 1): the stage-1 warps among themselves.
 // Thread 0 alone waits on each TMA barrier (bounded) and tells the stage-1 warps through shared memory;
-// the first stage-2 thread issues the loads and refills a stage once ZFULL says stage 1 is done with
-// it. A wait that gave up raises an abort flag that stage 2 reads after its next ZFULL wait, so every
-// named barrier still sees matching arrivals on both sides and both roles leave together.
+// the first stage-2 thread issues the loads, refilling a stage once ZFULL says stage 1 is done with
+// it, and walks the bands with a cursor (no integer division on the way). A wait that gave up raises
+// an abort flag that stage 2 reads after its next ZFULL wait, so every named barrier still sees
+// matching arrivals on both sides and both roles leave together.
 // ---------------------------------------------------------------------------------------------
 constexpr int WS_W2 = 4;  // stage-2 warps, two output indices of mode b each
 constexpr int WS_MAX_THREADS = 32 * (12 + WS_W2);
@@ -336,9 +359,10 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
                            int ldb, float* __restrict__ out, double* norm_in, double* norm_out, double* resid,
                            int* status) {
   constexpr int NA = 2 * KA;  // rows of mode a held in stage 2's registers: two bands of KA rows
+  constexpr int NZ = 3;       // Z buffers
   extern __shared__ __align__(1024) uint8_t wsm[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wsm) + 1023) & ~(uintptr_t)1023);
-  float* Zb = reinterpret_cast<float*>(base + (size_t)pg.nst * pg.stage_bytes);  // [2][KA][8][32]
+  float* Zb = reinterpret_cast<float*>(base + (size_t)pg.nst * pg.stage_bytes);  // [NZ][KA][8][32]
   __shared__ __align__(8) uint64_t full[PROJ_STAGES_MAX];
   __shared__ int sflag[2], abort_flag;
   __shared__ double red[32];
@@ -375,7 +399,7 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
         u[m][hh].y = (j < g.nb && b1 < rb) ? (float)Ub[(int64_t)j * ldb + b1] : 0.f;
       }
     int k = 0, posted = 0;  // units consumed; Z buffers handed to stage 2
-    int s = 0;
+    int s = 0, zb = 0;
     float sx_hi = 0.f, sx_lo = 0.f;
     uint32_t par = 0;
     for (; k < my_units; ++k) {
@@ -383,8 +407,7 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
       if (tid == 0) sflag[k & 1] = tma::mbar_wait(&full[s], par, status) ? 0 : 1;
       named_sync(1, 32 * W1);
       const bool abort_now = sflag[k & 1] != 0;
-      const int zb = k & 1;
-      if (k >= 2) named_sync(4 + zb, NT);  // stage 2 has read Z[zb] (unit k - 2)
+      if (k >= NZ) named_sync(5 + zb, NT);  // stage 2 has read Z[zb] (unit k - NZ)
       if (abort_now) {
         if (tid == 0) abort_flag = 1;
         named_arrive(2 + zb, NT);  // wake stage 2 for unit k; it sees the flag and leaves
@@ -440,9 +463,10 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
       // Z[zb] holds this band, and every stage-1 read of this band's stage is done: stage 2 refills it
       named_arrive(2 + zb, NT);
       ++posted;
+      if (++zb == NZ) zb = 0;
     }
-    // the Z buffers of the last (up to) two tiles posted: wait until stage 2 has read them
-    for (int q = (posted >= 2 ? posted - 2 : 0); q < posted; ++q) named_sync(4 + (q & 1), NT);
+    // the Z buffers of the last (up to) NZ units posted: wait until stage 2 has read them
+    for (int q = (posted >= NZ ? posted - NZ : 0); q < posted; ++q) named_sync(5 + q % NZ, NT);
     // every element of a band was squared by exactly one lane
     sx = (double)sx_hi + (double)sx_lo;
   } else {
@@ -463,23 +487,28 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
     // the first stage-2 thread issues the TMA loads: unit u goes to stage u mod nst, refilled once
     // stage 1 has posted the band that occupied it
     const bool producer = tid == 32 * W1;
-    int issued = 0;
-    if (producer)
+    int issued = 0, sq = 0;  // units issued; the stage of the next one
+    BandCursor cur;
+    if (producer) {
+      cur.start(t0, g);
       for (; issued < my_units && issued < pg.nst; ++issued)
-        issue_band(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg,
-                   (int64_t)t0 * pg.nbands + issued);
-    int t = t0, k = 0;
+        cur.issue(&map, &full[issued], base + (size_t)issued * pg.stage_bytes, g, pg);
+    }
+    // the item row block and column block of the tile being accumulated
+    int oa = (int)(t0 / g.ncb), ocb = (int)(t0 - (int64_t)oa * g.ncb);
+    int k = 0, zb = 0;
     for (; k < my_units; ++k) {
-      const int zb = k & 1, band = k & 1;  // two bands per tile
+      const int band = k & 1;  // two bands per tile
       named_sync(2 + zb, NT);
       if (abort_flag) {
-        named_arrive(4 + zb, NT);
+        named_arrive(5 + zb, NT);
         break;
       }
       if (producer && issued < my_units) {
-        const int sq = issued % pg.nst;  // == k mod nst: the stage unit k has just left
-        issue_band(&map, &full[sq], base + (size_t)sq * pg.stage_bytes, g, pg, (int64_t)t0 * pg.nbands + issued);
+        // sq == issued mod nst == k mod nst: the stage unit k has just left
+        cur.issue(&map, &full[sq], base + (size_t)sq * pg.stage_bytes, g, pg);
         ++issued;
+        if (++sq == pg.nst) sq = 0;
       }
       const float* Z = Zb + (size_t)zb * zsize + 4 * gq;
       // one unrolled copy per band, so the basis rows are picked at compile time
@@ -503,9 +532,11 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
         rows(v + KA);
       else
         rows(v);
-      named_arrive(4 + zb, NT);  // Z[zb] read
+      named_arrive(5 + zb, NT);  // Z[zb] read
+      if (++zb == NZ) zb = 0;
       if (band == 1) {
-        const int64_t aidx = t / g.ncb, col = (t - aidx * g.ncb) * PCOLS + 4 * gq;
+        const int64_t aidx = oa;
+        const int col = ocb * PCOLS + 4 * gq;
         if (col < g.B) {  // B % 4 == 0, so the four columns are all inside
           float yy = 0.f;
 #pragma unroll
@@ -529,7 +560,10 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
         for (int hb = 0; hb < 2; ++hb)
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[hb][c] = make_float2(0.f, 0.f);
-        ++t;
+        if (++ocb == (int)g.ncb) {
+          ocb = 0;
+          ++oa;
+        }
       }
     }
     if (producer && k < my_units) {
@@ -800,7 +834,7 @@ cudaError_t launch_proj_ws(const float* X, const PairGeom& g, const double* Ua, 
   pg.nbands = 2;
   pg.unit_bytes = (uint32_t)pg.ka * (uint32_t)g.nb * 128u;
   pg.stage_bytes = (pg.unit_bytes + 1023u) & ~1023u;
-  const size_t fixed = 1024 + sizeof(float) * 2 * (size_t)pg.ka * 8 * PCOLS;
+  const size_t fixed = 1024 + sizeof(float) * 3 * (size_t)pg.ka * 8 * PCOLS;  // three Z buffers
   const size_t cap = 227 * 1024;
   pg.nst = (int)std::min<size_t>(PROJ_STAGES_MAX, (cap - fixed) / pg.stage_bytes);
   if (pg.nst < 2) return cudaErrorInvalidValue;
