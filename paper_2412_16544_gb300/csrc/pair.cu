@@ -754,6 +754,174 @@ __global__ void __launch_bounds__(384, 1)
   (void)nwarps;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Gram matrices of both modes for na = nb = 24 (the Gram twin of the warp-specialised projection).
+// Same warp roles as the generic kernel (warps 0-5: the upper 8 x 8 blocks of G_a, warps 6-11: those
+// of G_b, lane = column), but with the mode sizes fixed at compile time every shared-memory address
+// is a per-lane base plus an immediate, products go two at a time through packed FMAs, diagonal
+// blocks load one operand, and the CTA walks its contiguous run of tiles with a cursor through a
+// ring of three whole-tile stages: thread 0 waits on the next tile, and after the one CTA barrier of
+// a tile (every warp is then done with the previous tile) refills that tile's stage.
+// ---------------------------------------------------------------------------------------------
+constexpr int G24_STAGES = 3;
+
+template <bool DIAG, uint32_t ROW_STEP, uint32_t OSTEP>
+__device__ __forceinline__ void g24_block(const uint8_t* Tp, const uint8_t* Tq, const uint32_t (&lo)[8],
+                                          float2 (&acc)[8][4]) {
+  // operand u of the block's first rows sits at Tp + u ROW_STEP + o OSTEP + (lane offset of that row's
+  // swizzle), and of its second rows at Tq + ...; the outer index runs in three rounds of eight (one
+  // swizzle period), each unrolled, which keeps the kernel's code within the instruction caches
+#pragma unroll 1
+  for (int ob = 0; ob < 24; ob += 8) {
+#pragma unroll
+    for (int oo = 0; oo < 8; ++oo) {
+      float vp[8], vq[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t off = u * ROW_STEP + oo * OSTEP + lo[(ROW_STEP == 128u) ? u : oo];
+        vp[u] = *reinterpret_cast<const float*>(Tp + off);
+        vq[u] = DIAG ? vp[u] : *reinterpret_cast<const float*>(Tq + off);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float2 d = make_float2(vp[u], vp[u]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)  // a diagonal block needs only the pairs that reach its upper triangle
+          if (!DIAG || 2 * v + 1 >= u) acc[u][v] = ffma2(d, make_float2(vq[2 * v], vq[2 * v + 1]), acc[u][v]);
+      }
+    }
+    Tp += 8 * OSTEP;
+    Tq += 8 * OSTEP;
+  }
+}
+
+__device__ __forceinline__ void g24_fold(float2 (&acc)[8][4], double* blk) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float x = acc[u][v].x, y = acc[u][v].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == ((u * 8 + 2 * v) & 31)) blk[u * 8 + 2 * v] += (double)x;
+      if (lane == ((u * 8 + 2 * v + 1) & 31)) blk[u * 8 + 2 * v + 1] += (double)y;
+      acc[u][v] = make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(384, 1)
+    pair_gram24_kernel(const __grid_constant__ CUtensorMap map, const PairGeom g, double* __restrict__ Ga,
+                       double* __restrict__ Gb, int* status) {
+  extern __shared__ __align__(1024) uint8_t gsm[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~(uintptr_t)1023);
+  double* blocks = reinterpret_cast<double*>(base + G24_STAGES * (size_t)g.stage_bytes);  // [12][64]
+  __shared__ __align__(8) uint64_t full[G24_STAGES];
+  __shared__ int sflag[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool on_a = warp < 6;
+  int p, q;
+  block_of(on_a ? warp : warp - 6, 3, p, q);
+  double* blk = blocks + warp * 64;
+  for (int e = lane; e < 64; e += 32) blk[e] = 0.0;
+  // the CTA's contiguous run of tiles, walked with a cursor (the launcher keeps ntiles below 2^31)
+  const int per = (int)((g.ntiles + gridDim.x - 1) / gridDim.x);
+  const int t0 = (int)blockIdx.x * per;
+  const int my = (g.ntiles > t0) ? min(per, (int)g.ntiles - t0) : 0;
+  int issued = 0, ca = 0, ccb = 0;
+  auto issue = [&](int st) {
+    tma::mbar_expect_tx(&full[st], g.tile_bytes);
+    tma::load_3d(&map, &full[st], base + (size_t)st * g.stage_bytes, ccb * PCOLS, 0, ca * 24);
+    if (++ccb == (int)g.ncb) {
+      ccb = 0;
+      ++ca;
+    }
+  };
+  if (tid == 0) {
+    for (int st = 0; st < G24_STAGES; ++st) tma::mbar_init(&full[st], 1);
+    tma::fence_mbar_init();
+    ca = (int)(t0 / g.ncb);
+    ccb = (int)(t0 - (int64_t)ca * g.ncb);
+    for (; issued < my && issued < G24_STAGES; ++issued) issue(issued);
+  }
+  __syncthreads();
+  // lane offsets within a 128-byte row under the 128-byte swizzle: chunk (lane / 4) ^ (row mod 8)
+  uint32_t lo[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) lo[r] = ((((uint32_t)lane >> 2) ^ (uint32_t)r) << 4) + (((uint32_t)lane & 3u) << 2);
+  // G_a: operand u of block row p is row (8p + u) nb + o, whose swizzle is o mod 8 (nb = 24):
+  //   offset (8p + u) * 3072 + o * 128; G_b: row o nb + 8p + u, swizzle u: offset o * 3072 + (8p + u) * 128
+  const uint32_t row_step = on_a ? 3072u : 128u, ostep = on_a ? 128u : 3072u;
+  float2 acc[8][4];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+  int k = 0, s = 0, since = 0;
+  uint32_t par = 0;
+  for (; k < my; ++k) {
+    if (tid == 0) sflag[k & 1] = tma::mbar_wait(&full[s], par, status) ? 0 : 1;
+    __syncthreads();  // tile k is in (or the wait gave up) and every warp is done with tile k - 1
+    if (sflag[k & 1]) break;
+    if (tid == 0 && k >= 1 && issued < my) {
+      issue(issued % G24_STAGES);  // the stage tile k - 1 has left (issued == k - 1 + stages)
+      ++issued;
+    }
+    const uint8_t* T = base + (size_t)s * g.stage_bytes;
+    const uint8_t* Tp = T + (uint32_t)(8 * p) * row_step;
+    const uint8_t* Tq = T + (uint32_t)(8 * q) * row_step;
+    if (on_a) {
+      if (p == q)
+        g24_block<true, 3072u, 128u>(Tp, Tq, lo, acc);
+      else
+        g24_block<false, 3072u, 128u>(Tp, Tq, lo, acc);
+    } else {
+      if (p == q)
+        g24_block<true, 128u, 3072u>(Tp, Tq, lo, acc);
+      else
+        g24_block<false, 128u, 3072u>(Tp, Tq, lo, acc);
+    }
+    if (++s == G24_STAGES) {
+      s = 0;
+      par ^= 1u;
+    }
+    if (++since == GRAM_FOLD) {
+      since = 0;
+      g24_fold(acc, blk);
+    }
+  }
+  if (tid == 0 && k < my) {
+    // a wait gave up: drain the loads still in flight (bounded, ignoring the status word)
+    for (int qq = k; qq < issued; ++qq) {
+      const int sq = qq % G24_STAGES;
+      const uint32_t pp = (uint32_t)((qq / G24_STAGES) & 1);
+      const uint64_t tw = tma::gtimer();
+      uint32_t okd = 0;
+      while (!okd && tma::gtimer() - tw < DRAIN_NS) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(okd)
+            : "r"(tma::smem_u32(&full[sq])), "r"(pp)
+            : "memory");
+      }
+      if (!okd) break;
+    }
+  }
+  g24_fold(acc, blk);
+  __syncwarp();
+  double* Gm = on_a ? Ga : Gb;
+  for (int e = lane; e < 64; e += 32) {
+    const int u = e >> 3, v = e & 7;
+    const int r = 8 * p + u, c = 8 * q + v;
+    if (p == q && v < u) continue;  // a diagonal block holds its upper triangle
+    atomicAdd(&Gm[r * 24 + c], blk[e]);
+    if (r != c) atomicAdd(&Gm[c * 24 + r], blk[e]);
+  }
+}
+
 // 3-D map of X[A][na][nb][B] as (B, nb, na * A), box (32, nb, rows): a whole tile (rows = na) or one band.
 bool make_map_pair(CUtensorMap* m, const float* X, const PairGeom& g, int rows) {
   auto fn = tensor_map_encoder();
@@ -882,6 +1050,14 @@ cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t 
   const double K = (double)A * (double)B;  // columns per row of either unfolding, over the whole tensor
   ProfScope prof(K_PAIR_GRAM, s, (double)na * (na + 1) * K * nb + (double)nb * (nb + 1) * K * na,
                  4.0 * K * na * nb);
+  if (na == 24 && nb == 24 && g.ntiles <= 0x7fffffffll) {
+    const size_t smem24 = 1024 + G24_STAGES * (size_t)g.stage_bytes + sizeof(double) * 64 * 12;
+    e = allow_max_smem(reinterpret_cast<const void*>(pair_gram24_kernel));
+    if (e != cudaSuccess) return e;
+    pair_gram24_kernel<<<grid, 384, smem24, s>>>(m, g, Ga, Gb, status);
+    note_launch();
+    return cudaGetLastError();
+  }
   pair_gram_kernel<<<grid, threads, smem, s>>>(m, g, wa, Ga, Gb, status);
   note_launch();
   return cudaGetLastError();
