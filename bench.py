@@ -53,6 +53,8 @@ def parse(argv=None):
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-second", action="store_true", help="skip the 64^3 spectral-field second record")
     ap.add_argument("--roofline-steps", type=int, default=2)
+    ap.add_argument("--per-batch", action="store_true",
+                    help="one htrise_update call per increment instead of one htrise_update_stream call")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", choices=["sensor", "spectral", "bumps", "multivar"], default="sensor",
                     help="sensor: 24^5 Chebyshev sensor responses drawn on the device (the headline); spectral: the "
@@ -312,15 +314,35 @@ def measured_peaks(B):
     return hbm, src, f64, f32
 
 
+PER_BATCH = False  # --per-batch: one htrise_update call per increment instead of htrise_update_stream
+
+
+def consecutive(incs):
+    """incs[1:] as one [count][items]... view when they lie back to back in memory, else None."""
+    import torch
+    rest = incs[1:]
+    if not rest or not all(isinstance(x, torch.Tensor) and x.is_contiguous() for x in rest):
+        return None
+    first = rest[0]
+    for k, x in enumerate(rest):
+        if x.shape != first.shape or x.data_ptr() != first.data_ptr() + k * first.numel() * first.element_size():
+            return None
+    return torch.as_strided(first, (len(rest),) + tuple(first.shape), (first.numel(),) + tuple(first.stride()))
+
+
 def one_pass(B, tree, incs, eps, prec, infos=None):
+    """BHT-l2r on the first increment, HT-RISE on the rest: one htrise_update_stream call over the rest
+    (the library overlaps each increment's projection with the previous one's skip test), or one
+    htrise_update call per increment."""
     st = B.bht_l2r(tree, incs[0], eps, precision=prec)
-    skips = 0
-    for k in range(1, len(incs)):
-        info = B.htrise_update(st, incs[k], eps, precision=prec)
-        skips += int(info.skipped)
-        if infos is not None:
-            infos.append(info)
-    return st, skips
+    rest = None if PER_BATCH else consecutive(incs)
+    if rest is not None:
+        got = B.htrise_update_stream(st, rest, eps, precision=prec)
+    else:
+        got = [B.htrise_update(st, incs[k], eps, precision=prec) for k in range(1, len(incs))]
+    if infos is not None:
+        infos.extend(got)
+    return st, sum(int(i.skipped) for i in got)
 
 
 def run_timed(B, torch, tree, incs, eps, prec, steps, warmup, dist, dev, local_rank, profile_mask=0, flush=None,
@@ -536,6 +558,8 @@ def run_ours(a, rank, world, local_rank):
         "dtype": "f32" if a.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "precision": a.precision, "items_per_step": a.increments * a.items,
                    "bytes_per_step": S.nbytes, "parallelism": f"{world} independent streams", "inputs": S.where,
+                   "api": ("bht_l2r + one htrise_update call per increment" if PER_BATCH else
+                           "bht_l2r + one htrise_update_stream call over the other increments"),
                    "l2": (f"inputs ({S.nbytes / 1e9:.1f} GB per stream) larger than L2 (129 MB); no flush"
                           if flush is None else
                           f"inputs ({S.nbytes / 1e6:.1f} MB) smaller than L2: a 258 MB write flushes L2 "
@@ -715,7 +739,9 @@ def job_rate_gbs(bytes_per_rank, world, seconds_max):
 
 
 def main():
+    global PER_BATCH
     a = parse()
+    PER_BATCH = a.per_batch
     rank, world, local_rank = rank_env()
     if a.impl == "reference":
         run_reference(a, rank)

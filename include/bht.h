@@ -179,6 +179,24 @@ bht_status htrise_update(bht_state* state, const void* Y, int32_t dtype, int64_t
                          double eps_rel, const bht_opts* opts, void* stream,
                          bht_update_info* info);
 
+/* HT-RISE (Algorithm 2) over a stream of `count` batches of N items each, in order: the same result
+ * as `count` calls of htrise_update on consecutive batches, with the GPU kept busy between them.
+ *   Y      : [count][N][n_1]..[n_d] item-major, element type `dtype`, device or host. Host batches
+ *            are copied into two device buffers on a copy stream of the call while the previous
+ *            batch computes (pinned host memory lets the copies overlap; pageable memory works but
+ *            serialises them).
+ *   infos  : NULL or [count] outcomes, one per batch, as htrise_update reports them.
+ *   done   : NULL or the number of batches committed when the call returns (count on success).
+ *   Step 1 of batch k + 1 (its projection onto the current cores) is enqueued before the skip test
+ * of batch k is read back: when batch k is skipped the cores do not change and that projection is the
+ * one Algorithm 2 makes; when batch k expands them, it is dropped and made again on the new cores.
+ * On an error the state holds every batch before the failing one (*done of them) and none after.
+ * opts as for htrise_update; its per-node outputs describe the last batch that expanded the cores.
+ * Synchronises `stream` before it returns. */
+bht_status htrise_update_stream(bht_state* state, const void* Y, int32_t dtype, int64_t N, int64_t count,
+                                double eps_rel, const bht_opts* opts, void* stream, bht_update_info* infos,
+                                int64_t* done);
+
 /* Root-to-leaves reconstruction (eq. htucker_reconstruction) of stored items
  * first .. first+count-1 into `out` ([count][n_1]..[n_d], element type `dtype`,
  * device or host). Never modifies the state. */

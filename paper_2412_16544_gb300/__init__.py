@@ -59,6 +59,7 @@ def _load():
         "bht_tree_info": [vp, P(i32), P(i32)],
         "bht_l2r": [vp, vp, i32, i64, dbl, P(_Opts), vp, P(vp)],
         "htrise_update": [vp, vp, i32, i64, dbl, P(_Opts), vp, P(_Info)],
+        "htrise_update_stream": [vp, vp, i32, i64, i64, dbl, P(_Opts), vp, P(_Info), P(i64)],
         "ht_reconstruct": [vp, i64, i64, vp, i32, vp],
         "ht_encode": [vp, vp, i32, i64, vp, vp],
         "bht_get_ranks": [vp, P(i64), i64],
@@ -109,6 +110,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bht_l2r", "htrise_update",
+            "htrise_update_stream",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
             "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
@@ -259,6 +261,24 @@ def htrise_update(state, Y, eps_rel: float, precision=None, stream=None, predict
     del keep
     return UpdateInfo(bool(info.skipped), info.eps_proj, info.eps_des, info.norm_y, info.n_items_total,
                       info.pred_nodes, info.pred_skipped, info.pred_fallback, info.pred_missed, info.batch_reads)
+
+
+def htrise_update_stream(state, Y, eps_rel: float, precision=None, stream=None, budget=None):
+    """HT-RISE over the batches Y[0], Y[1], ... ([count][N][n_1]..[n_d], device or host, host ideally
+    pinned) in one call, the next batch's projection overlapping the current batch's skip test.
+    Returns the list of UpdateInfo, one per batch."""
+    ptr, code, shape, keep = _buffer(Y)
+    if len(shape) < 3:
+        raise ValueError("Y must be [count][N][n_1]..[n_d]")
+    count, n = int(shape[0]), int(shape[1])
+    infos = (_Info * max(count, 1))()
+    done = ctypes.c_int64()
+    _check(_lib.htrise_update_stream(state, ptr, code, n, count, float(eps_rel),
+                                     _opts(precision, None, None, None, budget), _stream(stream), infos,
+                                     ctypes.byref(done)), "htrise_update_stream")
+    del keep
+    return [UpdateInfo(bool(i.skipped), i.eps_proj, i.eps_des, i.norm_y, i.n_items_total, i.pred_nodes,
+                       i.pred_skipped, i.pred_fallback, i.pred_missed, i.batch_reads) for i in infos[:count]]
 
 
 def bht_get_dims(state):

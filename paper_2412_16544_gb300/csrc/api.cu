@@ -10,6 +10,7 @@
 // a C-order reshape and moves no data.
 #include <algorithm>
 #include <exception>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -361,6 +362,9 @@ struct bht_state {
   };
   mutable std::vector<TcWeights> wcache;
   mutable std::mutex wmu;
+  // pinned host slots the skip test of Algorithm 2 reads back into (two, for the pipelined stream of
+  // batches): ||Y||^2, ||C||^2, the projection error and the status word of the bounded waits
+  double* pinned = nullptr;
 
   int64_t rows(int id) const {  // alpha of eq. compute_residual; n for a leaf
     const TNode& nd = tree.nodes[id];
@@ -1821,62 +1825,95 @@ bht_status ht_l2r(int32_t d, const int64_t* dims, const void* Y, int32_t dtype, 
   BHT_API_END
 }
 
-bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N, double eps_rel,
-                         const bht_opts* opts, void* stream, bht_update_info* info) {
-  BHT_API_BEGIN
-  if (!st || !Y) fail(BHT_EINVAL, "null argument");
-  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
-  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
-  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
-  validate_opts(opts);
-  if (st->plain) fail(BHT_EINVAL, "HT-RISE appends items along the root; this state holds a plain HT tensor");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bht_tree& t = st->tree;
-  int64_t item = 1;
-  for (auto v : t.dims) item *= v;
-  DBuf staging;
-  const void* dY = stage_input(Y, dtype, N * item, staging, s);
-  BatchScope batch_scope(dY);
-  const int64_t reads0 = g_batch_reads;
+namespace {
+// Step 1 of Algorithm 2 for one batch, enqueued on s: the projection Cbar onto the current cores,
+// ||Y||^2 and the projection error of eq. relative_error_threshold (FP64 form: ||Y||^2 - ||C||^2;
+// mixed form: the sum of the energies each node's complement removes), copied with the status word of
+// the bounded waits into the pinned slot hp, followed by the event ev. Nothing here waits for the GPU.
+struct Step1 {
+  LTensor Cbar;
+  DBuf acc;
+  int64_t reads = 0;     // reads of the batch by the enqueued work
+  double* hp = nullptr;  // pinned: ||Y||^2, ||C||^2, projection error, status word (int) in slot 3
+  cudaEvent_t ev = nullptr;
+  Step1() = default;
+  Step1(const Step1&) = delete;
+  Step1& operator=(const Step1&) = delete;
+  ~Step1() {
+    if (ev) cudaEventDestroy(ev);
+  }
+};
 
-  // Step 1: project onto the existing cores. ||Y||^2 in FP64; the projection error of
-  // eq. relative_error_threshold in FP64 as ||Y||^2 - ||C||^2 (FP64 form), or in the mixed form as the
-  // sum of the energies the projection removes at each node, measured on the node's complement.
-  const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
-  DBuf acc(sizeof(double) * 3, s);
-  ck(cudaMemsetAsync(acc.p, 0, sizeof(double) * 3, s), "memset");
+double* pinned_slot(bht_state* st, int k) {
+  if (!st->pinned) ck(cudaMallocHost(reinterpret_cast<void**>(&st->pinned), sizeof(double) * 8), "pinned slots");
+  return st->pinned + 4 * (k & 1);
+}
+
+void step1_enqueue(bht_state* st, const void* dY, int32_t dtype, int64_t N, const Arith& ar, cudaStream_t s,
+                   double* hp, Step1& o) {
+  int64_t item = 1;
+  for (auto v : st->tree.dims) item *= v;
+  BatchScope scope(dY);
+  const int64_t r0 = g_batch_reads;
+  o.acc = DBuf(sizeof(double) * 3, s);
+  ck(cudaMemsetAsync(o.acc.p, 0, sizeof(double) * 3, s), "memset");
   bool norm_done = false;
-  double* resid = ar.mixed ? acc.as<double>() + 2 : nullptr;
-  LTensor Cbar = project_all(st, dY, dtype, N, ar, s, acc.as<double>(), &norm_done, resid);
-  if (!norm_done) sqnorm_of(dY, dtype, N * item, acc.as<double>(), s);
-  if (!ar.mixed) sqnorm_of(Cbar.ptr, Cbar.dtype, Cbar.numel(), acc.as<double>() + 1, s);
-  // the norms and the status word of the bounded waits come back together, after one synchronisation
+  double* resid = ar.mixed ? o.acc.as<double>() + 2 : nullptr;
+  o.Cbar = project_all(st, dY, dtype, N, ar, s, o.acc.as<double>(), &norm_done, resid);
+  if (!norm_done) sqnorm_of(dY, dtype, N * item, o.acc.as<double>(), s);
+  if (!ar.mixed) sqnorm_of(o.Cbar.ptr, o.Cbar.dtype, o.Cbar.numel(), o.acc.as<double>() + 1, s);
+  ck(cudaMemcpyAsync(hp, o.acc.p, sizeof(double) * 3, cudaMemcpyDeviceToHost, s), "D2H norms");
+  ck(cudaMemcpyAsync(hp + 3, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
+  ck(cudaEventCreateWithFlags(&o.ev, cudaEventDisableTiming), "event");
+  ck(cudaEventRecord(o.ev, s), "event");
+  o.hp = hp;
+  o.reads = g_batch_reads - r0;
+}
+
+// The skip test of Algorithm 2 on an enqueued Step 1 (waits for its event only).
+struct Verdict {
   double h[3];
+  double eps_proj, eps_des;
+  bool skip;
+};
+
+Verdict step1_verdict(bht_state* st, Step1& o, double eps_rel, const Arith& ar, cudaStream_t s) {
+  ck(cudaEventSynchronize(o.ev), "sync");
   int hstat = 0;
-  ck(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H norms");
-  ck(cudaMemcpyAsync(&hstat, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status readback");
-  ck(cudaStreamSynchronize(s), "sync");
+  std::memcpy(&hstat, o.hp + 3, sizeof(int));
   if (hstat != 0) {
     cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
     fail((bht_status)hstat, "a bounded device-side wait gave up");
   }
-  if (!std::isfinite(h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
-  const double eps_des = eps_rel * std::sqrt(h[0]);
-  const double eps_proj = ar.mixed ? std::sqrt(std::max(h[2], 0.0))
-                                   : std::sqrt(std::max(h[0] - h[1], 0.0));  // eq. relative_error_threshold
-  const int64_t r11_old = st->r11(), r12_old = st->r12();
-  if (eps_proj <= eps_des) {
-    grow_root(st, r11_old, r12_old, r11_old, r12_old, st->n_items + N, s);
-    copy_convert(Cbar, st->root + st->n_items * r11_old * r12_old, BHT_F64, s);
-    st->n_items += N;
-    ck(cudaStreamSynchronize(s), "sync");
-    if (info)
-      *info = bht_update_info{1, (int32_t)(g_batch_reads - reads0), eps_proj, eps_des, std::sqrt(h[0]), st->n_items,
-                              0, 0, 0, 0};
-    return BHT_OK;
-  }
-  Cbar = LTensor();
+  Verdict v;
+  std::memcpy(v.h, o.hp, sizeof(v.h));
+  if (!std::isfinite(v.h[0])) fail(BHT_ENUMERIC, "the batch holds non-finite values");
+  v.eps_des = eps_rel * std::sqrt(v.h[0]);
+  v.eps_proj = ar.mixed ? std::sqrt(std::max(v.h[2], 0.0))
+                        : std::sqrt(std::max(v.h[0] - v.h[1], 0.0));  // eq. relative_error_threshold
+  v.skip = v.eps_proj <= v.eps_des;
+  return v;
+}
 
+// A skipped batch: only the root grows (eq. incremental_root_concatenate), enqueued on s.
+void append_root(bht_state* st, const LTensor& Cbar, int64_t N, cudaStream_t s) {
+  const int64_t r11 = st->r11(), r12 = st->r12();
+  grow_root(st, r11, r12, r11, r12, st->n_items + N, s);
+  copy_convert(Cbar, st->root + st->n_items * r11 * r12, BHT_F64, s);
+  st->n_items += N;
+}
+
+// Steps 2-3 of Algorithm 2 for a batch whose projection error exceeds eps_des: residuals truncated
+// node by node, bases expanded, parents zero padded, the batch re-projected; the new cores live in a
+// shadow copy until the commit at the end. reads0: reads of the batch before this call.
+void update_expand(bht_state* st, const void* dY, int32_t dtype, int64_t N, double eps_rel, const bht_opts* opts,
+                   const Arith& ar, const Verdict& v, int64_t reads0, cudaStream_t s, bht_update_info* info) {
+  const bht_tree& t = st->tree;
+  BatchScope batch_scope(dY);
+  const int64_t reads_in = g_batch_reads;
+  const double* h = v.h;
+  const double eps_des = v.eps_des, eps_proj = v.eps_proj;
+  const int64_t r11_old = st->r11(), r12_old = st->r12();
   // Steps 2-3 layer by layer; the new cores live in a shadow copy until commit
   double eps_nw2 = eps_des * eps_des / (2.0 * t.d - 2.0);
   const int budget = (opts && opts->budget >= 0) ? opts->budget : st->budget;
@@ -2137,8 +2174,151 @@ bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N,
   st->n_items += N;
   ck(cudaStreamSynchronize(s), "sync");
   if (info)
-    *info = bht_update_info{0, (int32_t)(g_batch_reads - reads0), eps_proj, eps_des, std::sqrt(h[0]), st->n_items, pstat.nodes, pstat.skipped,
-                            pstat.fallback, pstat.missed};
+    *info = bht_update_info{0, (int32_t)(reads0 + g_batch_reads - reads_in), eps_proj, eps_des, std::sqrt(h[0]),
+                            st->n_items, pstat.nodes, pstat.skipped, pstat.fallback, pstat.missed};
+}
+}  // namespace
+
+bht_status htrise_update(bht_state* st, const void* Y, int32_t dtype, int64_t N, double eps_rel,
+                         const bht_opts* opts, void* stream, bht_update_info* info) {
+  BHT_API_BEGIN
+  if (!st || !Y) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  if (st->plain) fail(BHT_EINVAL, "HT-RISE appends items along the root; this state holds a plain HT tensor");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t item = 1;
+  for (auto v : st->tree.dims) item *= v;
+  DBuf staging;
+  const void* dY = stage_input(Y, dtype, N * item, staging, s);
+  const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
+  // Step 1: project onto the existing cores; the skip test after one synchronisation
+  Step1 o;
+  step1_enqueue(st, dY, dtype, N, ar, s, pinned_slot(st, 0), o);
+  const Verdict v = step1_verdict(st, o, eps_rel, ar, s);
+  if (v.skip) {
+    append_root(st, o.Cbar, N, s);
+    ck(cudaStreamSynchronize(s), "sync");
+    if (info)
+      *info = bht_update_info{1, (int32_t)o.reads, v.eps_proj, v.eps_des, std::sqrt(v.h[0]), st->n_items, 0, 0, 0, 0};
+    return BHT_OK;
+  }
+  o.Cbar = LTensor();
+  update_expand(st, dY, dtype, N, eps_rel, opts, ar, v, o.reads, s, info);
+  BHT_API_END
+}
+
+bht_status htrise_update_stream(bht_state* st, const void* Y, int32_t dtype, int64_t N, int64_t count,
+                                double eps_rel, const bht_opts* opts, void* stream, bht_update_info* infos,
+                                int64_t* done) {
+  if (done) *done = 0;
+  BHT_API_BEGIN
+  if (!st || !Y) fail(BHT_EINVAL, "null argument");
+  if (dtype != BHT_F32 && dtype != BHT_F64) fail(BHT_EINVAL, "dtype must be BHT_F32 or BHT_F64");
+  if (N < 1) fail(BHT_EINVAL, "N must be >= 1");
+  if (count < 0) fail(BHT_EINVAL, "count must be >= 0");
+  if (!(eps_rel > 0.0) || !std::isfinite(eps_rel)) fail(BHT_EINVAL, "eps_rel must be positive and finite");
+  validate_opts(opts);
+  if (st->plain) fail(BHT_EINVAL, "HT-RISE appends items along the root; this state holds a plain HT tensor");
+  if (count == 0) return BHT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t item = 1;
+  for (auto v : st->tree.dims) item *= v;
+  const size_t bytes = dtype_size(dtype) * (size_t)(N * item);
+  const char* Yc = static_cast<const char*>(Y);
+  const bool host = !is_device_ptr(Y);
+  const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
+  // host batches: two device buffers, filled on a copy stream while the previous batch computes
+  DBuf buf[2];
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  struct Cleanup {
+    cudaStream_t* cs;
+    cudaEvent_t* ev;
+    cudaStream_t s;
+    ~Cleanup() {
+      if (*cs) {
+        cudaStreamSynchronize(*cs);
+        cudaStreamDestroy(*cs);
+      }
+      cudaStreamSynchronize(s);
+      for (int i = 0; i < 4; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    }
+  };
+  cudaEvent_t evs[4] = {nullptr, nullptr, nullptr, nullptr};
+  Cleanup cleanup{&cs, evs, s};
+  if (host) {
+    for (int b = 0; b < 2 && b < count; ++b) buf[b] = DBuf(bytes, s);
+    ck(cudaStreamSynchronize(s), "sync");
+    ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 4; ++i) ck(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming), "event");
+    copied[0] = evs[0];
+    copied[1] = evs[1];
+    freed[0] = evs[2];
+    freed[1] = evs[3];
+  }
+  // batch k into buffer k mod 2, after `left` (the batch two back is done with that buffer)
+  auto h2d = [&](int64_t k, cudaEvent_t left) {
+    const int b = (int)(k & 1);
+    if (left) ck(cudaStreamWaitEvent(cs, left, 0), "wait");
+    ck(cudaMemcpyAsync(buf[b].p, Yc + (size_t)k * bytes, bytes, cudaMemcpyHostToDevice, cs), "H2D batch");
+    ck(cudaEventRecord(copied[b], cs), "event");
+  };
+  auto batch = [&](int64_t k) -> const void* {
+    if (!host) return Yc + (size_t)k * bytes;
+    ck(cudaStreamWaitEvent(s, copied[k & 1], 0), "wait");
+    return buf[k & 1].p;
+  };
+  if (host) {
+    h2d(0, nullptr);
+    if (count > 1) h2d(1, nullptr);
+  }
+  // Step 1 of batch k + 1 is enqueued before the skip test of batch k is read: the cores it projects
+  // onto are those batch k leaves whenever batch k is skipped; otherwise it is dropped and redone
+  std::unique_ptr<Step1> cur(new Step1), nxt;
+  const void* dcur = batch(0);
+  step1_enqueue(st, dcur, dtype, N, ar, s, pinned_slot(st, 0), *cur);
+  for (int64_t k = 0; k < count; ++k) {
+    const void* dnext = nullptr;
+    cudaEvent_t left = nullptr;  // the point on s after which batch k no longer reads its input
+    if (k + 1 < count) {
+      dnext = batch(k + 1);
+      nxt.reset(new Step1);
+      step1_enqueue(st, dnext, dtype, N, ar, s, pinned_slot(st, k + 1), *nxt);
+    }
+    const Verdict v = step1_verdict(st, *cur, eps_rel, ar, s);
+    if (v.skip) {
+      append_root(st, cur->Cbar, N, s);
+      if (infos)
+        infos[k] = bht_update_info{1, (int32_t)cur->reads, v.eps_proj, v.eps_des, std::sqrt(v.h[0]), st->n_items,
+                                   0, 0, 0, 0};
+      left = cur->ev;  // a skipped batch read its input in Step 1 only
+    } else {
+      // the speculative Step 1 of batch k + 1 projected onto cores that are about to change
+      if (nxt) {
+        ck(cudaEventSynchronize(nxt->ev), "sync");
+        nxt.reset();
+      }
+      cur->Cbar = LTensor();
+      update_expand(st, dcur, dtype, N, eps_rel, opts, ar, v, cur->reads, s, infos ? infos + k : nullptr);
+      if (host) {
+        ck(cudaEventRecord(freed[k & 1], s), "event");
+        left = freed[k & 1];
+      }
+      if (k + 1 < count) {
+        nxt.reset(new Step1);
+        step1_enqueue(st, dnext, dtype, N, ar, s, pinned_slot(st, k + 1), *nxt);
+      }
+    }
+    if (done) *done = k + 1;
+    if (host && k + 2 < count) h2d(k + 2, left);
+    cur = std::move(nxt);
+    dcur = dnext;
+  }
+  ck(cudaStreamSynchronize(s), "sync");
   BHT_API_END
 }
 
@@ -2589,6 +2769,7 @@ bht_status bht_state_destroy(bht_state* st) {
   st->wcache.clear();
   cudaDeviceSynchronize();
   if (st->d_status) cudaFree(st->d_status);
+  if (st->pinned) cudaFreeHost(st->pinned);
   delete st;
   return BHT_OK;
 }
