@@ -472,17 +472,21 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
   } else {
     // ---------------- stage 2 ----------------
     const int b0 = warp - W1, b1 = b0 + WS_W2;  // output indices of mode b of this warp
-    float2 v[NA];  // (Ua[i][pq], Ua[i][pq + 4])
+    float4 v[NA];  // (Ua[i][pq], Ua[i][pq], Ua[i][pq + 4], Ua[i][pq + 4]): each basis entry twice, so a
+                   // packed FMA takes two columns of Z against it without any register copy
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      v[i].x = (i < g.na && pq < ra) ? (float)Ua[(int64_t)i * lda + pq] : 0.f;
-      v[i].y = (i < g.na && pq + 4 < ra) ? (float)Ua[(int64_t)i * lda + pq + 4] : 0.f;
+      const float x0 = (i < g.na && pq < ra) ? (float)Ua[(int64_t)i * lda + pq] : 0.f;
+      const float x1 = (i < g.na && pq + 4 < ra) ? (float)Ua[(int64_t)i * lda + pq + 4] : 0.f;
+      v[i] = make_float4(x0, x0, x1, x1);
     }
-    float2 acc[2][4];  // acc[b0 or b1][column] = (a = pq, a = pq + 4)
+    float2 acc[2][2][2];  // acc[b0 or b1][a = pq or pq + 4][columns (0, 1) or (2, 3)]
 #pragma unroll
     for (int hb = 0; hb < 2; ++hb)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[hb][c] = make_float2(0.f, 0.f);
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp) acc[hb][h][cp] = make_float2(0.f, 0.f);
     float sy_hi = 0.f, sy_lo = 0.f;
     // the first stage-2 thread issues the TMA loads: unit u goes to stage u mod nst, refilled once
     // stage 1 has posted the band that occupied it
@@ -512,20 +516,20 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
       }
       const float* Z = Zb + (size_t)zb * zsize + 4 * gq;
       // one unrolled copy per band, so the basis rows are picked at compile time
-      auto rows = [&](const float2* vb) {
+      auto rows = [&](const float4* vb) {
 #pragma unroll
         for (int i = 0; i < KA; ++i) {
           const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b0) * PCOLS);
           const float4 zc = *reinterpret_cast<const float4*>(Z + (size_t)(i * 8 + b1) * PCOLS);
-          const float2 w = vb[i];
-          acc[0][0] = ffma2(make_float2(za.x, za.x), w, acc[0][0]);
-          acc[0][1] = ffma2(make_float2(za.y, za.y), w, acc[0][1]);
-          acc[0][2] = ffma2(make_float2(za.z, za.z), w, acc[0][2]);
-          acc[0][3] = ffma2(make_float2(za.w, za.w), w, acc[0][3]);
-          acc[1][0] = ffma2(make_float2(zc.x, zc.x), w, acc[1][0]);
-          acc[1][1] = ffma2(make_float2(zc.y, zc.y), w, acc[1][1]);
-          acc[1][2] = ffma2(make_float2(zc.z, zc.z), w, acc[1][2]);
-          acc[1][3] = ffma2(make_float2(zc.w, zc.w), w, acc[1][3]);
+          const float2 w0 = make_float2(vb[i].x, vb[i].y), w1 = make_float2(vb[i].z, vb[i].w);
+          acc[0][0][0] = ffma2(make_float2(za.x, za.y), w0, acc[0][0][0]);
+          acc[0][0][1] = ffma2(make_float2(za.z, za.w), w0, acc[0][0][1]);
+          acc[0][1][0] = ffma2(make_float2(za.x, za.y), w1, acc[0][1][0]);
+          acc[0][1][1] = ffma2(make_float2(za.z, za.w), w1, acc[0][1][1]);
+          acc[1][0][0] = ffma2(make_float2(zc.x, zc.y), w0, acc[1][0][0]);
+          acc[1][0][1] = ffma2(make_float2(zc.z, zc.w), w0, acc[1][0][1]);
+          acc[1][1][0] = ffma2(make_float2(zc.x, zc.y), w1, acc[1][1][0]);
+          acc[1][1][1] = ffma2(make_float2(zc.z, zc.w), w1, acc[1][1][1]);
         }
       };
       if (band)
@@ -546,9 +550,7 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
             for (int h = 0; h < 2; ++h) {
               const int a = pq + 4 * h;
               if (b < rb && a < ra) {
-                const float2* q4 = acc[hb];
-                const float4 w = h ? make_float4(q4[0].y, q4[1].y, q4[2].y, q4[3].y)
-                                   : make_float4(q4[0].x, q4[1].x, q4[2].x, q4[3].x);
+                const float4 w = make_float4(acc[hb][h][0].x, acc[hb][h][0].y, acc[hb][h][1].x, acc[hb][h][1].y);
                 *reinterpret_cast<float4*>(out + ((aidx * ra + a) * rb + b) * g.B + col) = w;
                 yy = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, yy))));
               }
@@ -559,7 +561,9 @@ __global__ void __launch_bounds__(WS_MAX_THREADS, 1)
 #pragma unroll
         for (int hb = 0; hb < 2; ++hb)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[hb][c] = make_float2(0.f, 0.f);
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int cp = 0; cp < 2; ++cp) acc[hb][h][cp] = make_float2(0.f, 0.f);
         if (++ocb == (int)g.ncb) {
           ocb = 0;
           ++oa;
