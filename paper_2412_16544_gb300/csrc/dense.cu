@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict
     const int64_t na_here = min(na, A - a0), nb_here = min(nb, B - b0);
     const int ncol = (int)(na_here * nb_here);
     __syncthreads();
+    // 32-bit index arithmetic in the staging loops (a chunk holds CHC x Ip entries)
     if (B == 1) {
       const float* src = X + a0 * I;
       for (int e = tid; e < CHC * Ip; e += blockDim.x) {
@@ -168,12 +169,14 @@ __global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict
         Xs[c * Ip + i] = (c < ncol && i < I) ? src[(int64_t)c * I + i] : 0.f;
       }
     } else {
+      const int nbi = (int)nb, nai = (int)na, nbh = (int)nb_here, nah = (int)na_here;
+      const float* src = X + (a0 * I) * B + b0;
       for (int e = tid; e < CHC * Ip; e += blockDim.x) {
-        const int b = (int)(e % nb), t = (int)(e / nb);
-        const int al = t % (int)na, i = t / (int)na;
+        const int t = e / nbi, b = e - t * nbi;
+        const int i = t / nai, al = t - i * nai;
         float v = 0.f;
-        if (i < I && al < na_here && b < nb_here) v = X[((a0 + al) * I + i) * B + b0 + b];
-        if (i < Ip) Xs[(al * (int)nb + b) * Ip + i] = v;
+        if (i < I && al < nah && b < nbh) v = src[((int64_t)al * I + i) * B + b];
+        if (i < Ip) Xs[(al * nbi + b) * Ip + i] = v;
       }
     }
     __syncthreads();
