@@ -253,7 +253,7 @@ KERNEL_SOURCES = {
                         ["paper_2412_16544_gb300/csrc/sync.cuh"]),
     "pair_proj": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_project_ws_kernel", "ds_add", "ffma2"],
                   ["paper_2412_16544_gb300/csrc/tma.cuh"]),
-    "pair_gram": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_gram_kernel", "fold_block"],
+    "pair_gram": ("paper_2412_16544_gb300/csrc/pair.cu", ["pair_gram24_kernel", "g24_block", "g24_fold"],
                   ["paper_2412_16544_gb300/csrc/tma.cuh"]),
 }
 
