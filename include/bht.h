@@ -286,14 +286,18 @@ bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const doubl
  * fp32 device data viewed as [A][na][nb][B] (B contiguous, B % 4 == 0, X 16-byte aligned), read once,
  * tile by tile, through TMA.
  * bht_pair_gram: Ga (na x na) and Gb (nb x nb), FP64 device, receive the Gram matrices of the two
- *   mode unfoldings, G_a = X_(a) X_(a)^T and G_b = X_(b) X_(b)^T (FP32 products and partial sums
- *   folded into FP64). na, nb <= 24.
+ *   mode unfoldings, G_a = X_(a) X_(a)^T and G_b = X_(b) X_(b)^T. na, nb <= 24. tensor_cores != 0 and
+ *   na = nb = 24: tcgen05 MMAs in split TF32 (x = h + l, G = H H^T + L H^T + (L H^T)^T; the missing
+ *   L L^T is below 2^-22 of each product), one tile summed in FP32 in tensor memory (96 MMA results
+ *   per entry: within 1.2e-5 of the largest entry) and folded into FP64; otherwise, and in BHT-l2r
+ *   (where it is 2.7 times faster at 24 x 24), FP32 products with per-lane FP32 partial sums folded
+ *   into FP64 (within 2e-6).
  * bht_pair_project: out[A][ra][rb][B] (fp32 device) = X x_a Ua^T x_b Ub^T with Ua [na][ra] and
  *   Ub [nb][rb] FP64 device bases (row-major); norms (nullable, 3 FP64 device values) receives
  *   ||X||^2, ||out||^2 and their difference added in FP64. na, nb <= 32, ra, rb <= 16.
  * Shapes outside these limits give BHT_EUNSUPPORTED. Both synchronise `stream`. */
 bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, double* Ga, double* Gb,
-                         void* stream);
+                         int32_t tensor_cores, void* stream);
 bht_status bht_pair_project(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, const double* Ua,
                             int64_t ra, const double* Ub, int64_t rb, float* out, double* norms, void* stream);
 

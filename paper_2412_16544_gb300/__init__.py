@@ -92,7 +92,7 @@ def _load():
         "bht_sketch_features": [vp, i64, dbl, dbl, ctypes.c_uint64, vp, vp],
         "bht_synth_chebyshev": [vp, i64, i32, i32, i32, i32, dbl, ctypes.c_uint64, i64, vp, vp],
         "bht_probe_fma_rate": [i32, P(dbl), vp],
-        "bht_pair_gram": [vp, i64, i64, i64, i64, vp, vp, vp],
+        "bht_pair_gram": [vp, i64, i64, i64, i64, vp, vp, i32, vp],
         "bht_pair_project": [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -498,14 +498,16 @@ def bht_mode_product_noalloc(X, U, S: int, R2: int = 1, out=None, norms=None, st
     return out
 
 
-def bht_pair_gram(X, stream=None):
-    """Gram matrices of modes 1 and 2 of a contiguous fp32 CUDA tensor X [A, na, nb, B] (one read of X)."""
+def bht_pair_gram(X, tensor_cores=False, stream=None):
+    """Gram matrices of modes 1 and 2 of a contiguous fp32 CUDA tensor X [A, na, nb, B] (one read of X);
+    tensor_cores: the split-TF32 tensor-core pass where the shape has one (24 x 24), else FP32 SIMT."""
     torch = _torch()
     A, na, nb, B = X.shape
     Ga = torch.empty((na, na), dtype=torch.float64, device=X.device)
     Gb = torch.empty((nb, nb), dtype=torch.float64, device=X.device)
     _check(_lib.bht_pair_gram(ctypes.c_void_p(X.data_ptr()), A, na, nb, B, ctypes.c_void_p(Ga.data_ptr()),
-                              ctypes.c_void_p(Gb.data_ptr()), _stream(stream)), "bht_pair_gram")
+                              ctypes.c_void_p(Gb.data_ptr()), 1 if tensor_cores else 0, _stream(stream)),
+           "bht_pair_gram")
     return Ga, Gb
 
 

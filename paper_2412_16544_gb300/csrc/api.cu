@@ -1616,8 +1616,10 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         ck(cudaMemsetAsync(lp.Ga.p, 0, sizeof(double) * na * na, s), "memset");
         ck(cudaMemsetAsync(lp.Gb.p, 0, sizeof(double) * nb * nb, s), "memset");
         note_read(Cl.ptr);
+        // the FP32 SIMT pass: the tensor-core one costs 2.7 times as much on 24 x 24 pairs (an MMA carries
+        // 24 useful rows of its 128 and costs as much as a full one)
         ck(launch_pair_gram(static_cast<const float*>(Cl.ptr), A, (int)na, (int)nb, B, lp.Ga.as<double>(),
-                            lp.Gb.as<double>(), st->d_status, s),
+                            lp.Gb.as<double>(), st->d_status, s, false),
            "two-mode Gram pass");
         out.push_back(std::move(lp));
         ++m;
@@ -2477,7 +2479,7 @@ bht_status ht_encode(const bht_state* st, const void* Y, int32_t dtype, int64_t 
 }
 
 bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, double* Ga, double* Gb,
-                         void* stream) {
+                         int32_t tensor_cores, void* stream) {
   BHT_API_BEGIN
   if (!X || !Ga || !Gb) fail(BHT_EINVAL, "null argument");
   if (!pair_gram_supported(A, na, nb, B)) fail(BHT_EUNSUPPORTED, "shape outside the two-mode Gram pass");
@@ -2488,7 +2490,8 @@ bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int6
   ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
   ck(cudaMemsetAsync(Ga, 0, sizeof(double) * na * na, s), "memset");
   ck(cudaMemsetAsync(Gb, 0, sizeof(double) * nb * nb, s), "memset");
-  ck(launch_pair_gram(X, A, (int)na, (int)nb, B, Ga, Gb, status.as<int>(), s), "two-mode Gram pass");
+  ck(launch_pair_gram(X, A, (int)na, (int)nb, B, Ga, Gb, status.as<int>(), s, tensor_cores != 0),
+     "two-mode Gram pass");
   check_status_word(status.as<int>(), s);
   BHT_API_END
 }

@@ -255,13 +255,15 @@ cudaError_t launch_ttm_tc_resid(const float* X, int64_t rows, int64_t K, const f
                                 int* status, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// Two-mode passes over X[A][na][nb][B] (pair.cu): TMA-staged tiles, FP32 SIMT, one read of X.
+// Two-mode passes over X[A][na][nb][B] (pair.cu): TMA-staged tiles, FP32 SIMT or tensor cores, one read
+// of X (the tensor-core Gram reads each tile a second time, from L2).
 // ---------------------------------------------------------------------------
 bool pair_gram_supported(int64_t A, int64_t na, int64_t nb, int64_t B);
 bool pair_project_supported(int64_t A, int64_t na, int64_t nb, int64_t B, int64_t ra, int64_t rb);
 // G_a (na x na) and G_b (nb x nb) += the Gram matrices of the two mode unfoldings (zeroed by the caller).
+// tensor_cores: the split-TF32 tcgen05 pass where the shape has one (na = nb = 24), else FP32 SIMT.
 cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t B, double* Ga, double* Gb,
-                             int* status, cudaStream_t s);
+                             int* status, cudaStream_t s, bool tensor_cores);
 // out[A][ra][rb][B] = X x_a Ua^T x_b Ub^T (Ua [na][ra] with leading dimension lda, Ub likewise);
 // norm_in += ||X||^2, norm_out += ||out||^2, resid += their difference (each nullable).
 cudaError_t launch_pair_project(const float* X, int64_t A, int na, int nb, int64_t B, const double* Ua, int ra,

@@ -21,6 +21,7 @@
 
 #include "bht.h"
 #include "internal.cuh"
+#include "tcgen.cuh"
 #include "tma.cuh"
 
 namespace bht {
@@ -926,6 +927,261 @@ __global__ void __launch_bounds__(384, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Both Grams of a 24 x 24 pair on the tensor cores (tcgen05, split TF32, FP32 accumulation in TMEM,
+// FP64 sums per CTA). A tile (24 x 24 rows of 32 columns) arrives as twelve bands of four rows of the
+// contracted mode, each in its own ring slot:
+//   * six bands of i (rows (i, j), the map of the projection): for each i, the 24 rows j form a K-major
+//     operand (K = the 32 columns), and G_b += X_i X_i^T is one MMA per 8 columns;
+//   * six bands of j through a second map that takes i before j (rows (j, i); the same bytes, mostly from
+//     L2): for each j, G_a += X_j X_j^T.
+// An MMA is M = 128 rows by N = 32 from the start of a 24-row group; rows and columns beyond 24 read the
+// next group (ignored in the result; the ring is followed by a pad they may reach). Split TF32: the MMA
+// reads x as its TF32 part h, a converter warp pair writes l = x - h beside it, and
+// G = H H^T + L H^T + (L H^T)^T. Two TMEM sets take turns: while one accumulates a tile, one warp
+// moves the other's D = H H^T and E = L H^T into FP64 registers as F = D + 2E (the symmetric part of
+// the sum of the F is G, D being symmetric).
+// Warps: 0 TMA producer, 1 TMEM allocation and MMA issue, 2-3 the l planes, 4 the FP64 sums.
+// Every wait is bounded (1 s): a wait that gives up sets the status word and the roles wind down,
+// the producer waiting for its loads in flight.
+// ---------------------------------------------------------------------------------------------
+constexpr int GTC_THREADS = 160;
+constexpr int GTC_BAND = 4;                                  // rows of the contracted mode per band
+constexpr int GTC_UNIT_BYTES = GTC_BAND * 24 * 128;          // 12 KB: one band of a tile
+constexpr int GTC_SLOT_BYTES = 2 * GTC_UNIT_BYTES;           // the band and its l plane
+constexpr int GTC_SLOTS = 8;
+constexpr int GTC_PAD = 14 * 1024;                           // reach of the last MMA past the ring
+constexpr int GTC_UNITS_PER_TILE = 2 * 24 / GTC_BAND;        // 6 bands of i, then 6 bands of j
+constexpr int GTC_DRAIN_TILES = 1;                           // tiles per TMEM set before it is drained
+constexpr size_t GTC_SMEM = 1024 + (size_t)GTC_SLOTS * GTC_SLOT_BYTES + GTC_PAD;
+
+__device__ __forceinline__ void load_4d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
+                                        int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(tma::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(tma::smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(GTC_THREADS, 1)
+    pair_gram_tc_kernel(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
+                        const PairGeom g, double* __restrict__ Ga, double* __restrict__ Gb, int* status) {
+  extern __shared__ __align__(1024) uint8_t gtc_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gtc_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[GTC_SLOTS], ready[GTC_SLOTS], empty[GTC_SLOTS], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (int)((g.ntiles + gridDim.x - 1) / gridDim.x);
+  const int t0 = (int)blockIdx.x * per;
+  const int my_tiles = (g.ntiles > t0) ? min(per, (int)g.ntiles - t0) : 0;
+  const int my_units = my_tiles * GTC_UNITS_PER_TILE;
+  const int nsets = (my_tiles + GTC_DRAIN_TILES - 1) / GTC_DRAIN_TILES;  // TMEM set uses
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < GTC_SLOTS; ++i) {
+      tma::mbar_init(&full[i], 1);
+      tma::mbar_init(&ready[i], 2);
+      tma::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tma::mbar_init(&tfull[i], 1);
+      tma::mbar_init(&tempty[i], 1);
+    }
+    tma::fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tma::smem_u32(&tmem_base)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  const uint32_t tmem = tmem_base;  // set s at column 128 s: D_b, E_b, D_a, E_a at +0, +32, +64, +96
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int ca = (int)(t0 / g.ncb), ccb = (int)(t0 - (int64_t)ca * g.ncb), ub = 0;
+      int issued = 0;
+      bool ok = true;
+      for (; ok && issued < my_units; ++issued) {
+        const int slot = issued % GTC_SLOTS;
+        const uint32_t ph = (uint32_t)((issued / GTC_SLOTS) & 1);
+        if (issued >= GTC_SLOTS && !tma::mbar_wait(&empty[slot], ph ^ 1u, status)) {
+          ok = false;
+          break;
+        }
+        uint8_t* dst = base + (size_t)slot * GTC_SLOT_BYTES;
+        tma::mbar_expect_tx(&full[slot], GTC_UNIT_BYTES);
+        if (ub < 6)
+          tma::load_3d(&map_i, &full[slot], dst, ccb * PCOLS, 0, ca * 24 + GTC_BAND * ub);
+        else
+          load_4d(&map_j, &full[slot], dst, ccb * PCOLS, 0, GTC_BAND * (ub - 6), ca);
+        if (++ub == GTC_UNITS_PER_TILE) {
+          ub = 0;
+          if (++ccb == (int)g.ncb) {
+            ccb = 0;
+            ++ca;
+          }
+        }
+      }
+      if (!ok) {
+        // let the loads in flight land before the CTA leaves (bounded, ignoring the status word)
+        for (int q = max(issued - GTC_SLOTS, 0); q < issued; ++q) {
+          const int sq = q % GTC_SLOTS;
+          const uint32_t pp = (uint32_t)((q / GTC_SLOTS) & 1);
+          const uint64_t tw = tma::gtimer();
+          uint32_t okd = 0;
+          while (!okd && tma::gtimer() - tw < DRAIN_NS) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(okd)
+                : "r"(tma::smem_u32(&full[sq])), "r"(pp)
+                : "memory");
+          }
+          if (!okd) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tcg::idesc_tf32(128, 32);
+      bool ok = true;
+      int u = 0;
+      for (int set = 0; ok && set < nsets; ++set) {
+        const uint32_t acc = (uint32_t)(set & 1), aph = (uint32_t)((set >> 1) & 1);
+        if (set >= 2 && !tma::mbar_wait(&tempty[acc], aph ^ 1u, status)) break;
+        tcg::fence_after();
+        const uint32_t dt = tmem + acc * 128u;
+        const int uend = min(my_units, (set + 1) * GTC_DRAIN_TILES * GTC_UNITS_PER_TILE);
+        bool first_b = true, first_a = true;
+        for (; u < uend; ++u) {
+          const int slot = u % GTC_SLOTS;
+          const uint32_t ph = (uint32_t)((u / GTC_SLOTS) & 1);
+          if (!tma::mbar_wait(&full[slot], ph, status) || !tma::mbar_wait(&ready[slot], ph, status)) {
+            ok = false;
+            break;
+          }
+          tcg::fence_after();
+          const bool on_b = (u % GTC_UNITS_PER_TILE) < 6;
+          const uint32_t hi = tma::smem_u32(base + (size_t)slot * GTC_SLOT_BYTES), lo = hi + GTC_UNIT_BYTES;
+          const uint32_t dD = dt + (on_b ? 0u : 64u), dE = dD + 32u;
+          bool& first = on_b ? first_b : first_a;
+#pragma unroll
+          for (int gr = 0; gr < GTC_BAND; ++gr)
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t off = (uint32_t)(gr * 3072 + 32 * k4);
+              const uint64_t bh = tcg::sw128_desc(hi + off);
+              const uint32_t accum = first ? 0u : 1u;
+              tcg::mma_tf32(dD, tcg::sw128_desc(hi + off), bh, idesc, accum);
+              tcg::mma_tf32(dE, tcg::sw128_desc(lo + off), bh, idesc, accum);
+              first = false;
+            }
+          tcg::mma_commit(&empty[slot]);
+        }
+        if (!ok) break;
+        tcg::mma_commit(&tfull[acc]);
+      }
+    }
+  } else if (warp < 4) {
+    // ---------------- l = x - (x with its 13 low mantissa bits cleared) ----------------
+    const int t = (int)threadIdx.x - 64;  // 0..63
+    for (int u = 0; u < my_units; ++u) {
+      const int slot = u % GTC_SLOTS;
+      const uint32_t ph = (uint32_t)((u / GTC_SLOTS) & 1);
+      if (!tma::mbar_wait(&full[slot], ph, status)) break;
+      const float4* src = reinterpret_cast<const float4*>(base + (size_t)slot * GTC_SLOT_BYTES);
+      float4* dst = reinterpret_cast<float4*>(base + (size_t)slot * GTC_SLOT_BYTES + GTC_UNIT_BYTES);
+      for (int q = t; q < GTC_UNIT_BYTES / 16; q += 64) {
+        const float4 x = src[q];
+        float4 l;
+        l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+        l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+        l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+        l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+        dst[q] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) tcg::mbar_arrive(&ready[slot]);
+    }
+  } else {
+    // ---------------- FP64 sums of the TMEM sets (TMEM lanes 0..31 = rows 0..31) ----------------
+    double fb[24], fa[24];
+#pragma unroll
+    for (int c = 0; c < 24; ++c) fb[c] = fa[c] = 0.0;
+    for (int set = 0; set < nsets; ++set) {
+      const uint32_t acc = (uint32_t)(set & 1), aph = (uint32_t)((set >> 1) & 1);
+      if (!tma::mbar_wait(&tfull[acc], aph, status)) break;
+      tcg::fence_after();
+      const uint32_t dt = tmem + acc * 128u;
+      float d[16], e[16];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        // columns 0..15 and 16..23 (16..31 loaded, the rest ignored) of D and E, for each Gram
+        tcg::tmem_ld16(dt + 16u * half, d);
+        tcg::tmem_ld16(dt + 32u + 16u * half, e);
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (16 * half + c < 24) fb[16 * half + c] += (double)d[c] + 2.0 * (double)e[c];
+        tcg::tmem_ld16(dt + 64u + 16u * half, d);
+        tcg::tmem_ld16(dt + 96u + 16u * half, e);
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (16 * half + c < 24) fa[16 * half + c] += (double)d[c] + 2.0 * (double)e[c];
+      }
+      tcg::fence_before();
+      __syncwarp();
+      if (lane == 0) tcg::mbar_arrive(&tempty[acc]);
+    }
+    // G = (F + F^T) / 2 through shared memory (the ring is idle once every set is summed)
+    double* Fs = reinterpret_cast<double*>(base);  // [2][24][24]
+    if (lane < 24)
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        Fs[lane * 24 + c] = fb[c];
+        Fs[576 + lane * 24 + c] = fa[c];
+      }
+    __syncwarp();
+    if (lane < 24)
+      for (int c = lane; c < 24; ++c) {
+        const double vb = 0.5 * (Fs[lane * 24 + c] + Fs[c * 24 + lane]);
+        const double va = 0.5 * (Fs[576 + lane * 24 + c] + Fs[576 + c * 24 + lane]);
+        atomicAdd(&Gb[lane * 24 + c], vb);
+        atomicAdd(&Ga[lane * 24 + c], va);
+        if (c != lane) {
+          atomicAdd(&Gb[c * 24 + lane], vb);
+          atomicAdd(&Ga[c * 24 + lane], va);
+        }
+      }
+  }
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+}
+
+// 4-D map of X[A][na][nb][B] that takes mode a before mode b: dims (B, na, nb, A), box (32, na, rows, 1);
+// a tile band lands as rows (j, i).
+bool make_map_pair_ji(CUtensorMap* m, const float* X, const PairGeom& g, int rows) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)g.B, (cuuint64_t)g.na, (cuuint64_t)g.nb, (cuuint64_t)g.A};
+  cuuint64_t strides[3] = {(cuuint64_t)g.nb * (cuuint64_t)g.B * 4, (cuuint64_t)g.B * 4,
+                           (cuuint64_t)g.na * (cuuint64_t)g.nb * (cuuint64_t)g.B * 4};
+  cuuint32_t box[4] = {(cuuint32_t)PCOLS, (cuuint32_t)g.na, (cuuint32_t)rows, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(X), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // 3-D map of X[A][na][nb][B] as (B, nb, na * A), box (32, nb, rows): a whole tile (rows = na) or one band.
 bool make_map_pair(CUtensorMap* m, const float* X, const PairGeom& g, int rows) {
   auto fn = tensor_map_encoder();
@@ -1038,7 +1294,7 @@ bool pair_project_supported(int64_t A, int64_t na, int64_t nb, int64_t B, int64_
 }
 
 cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t B, double* Ga, double* Gb,
-                             int* status, cudaStream_t s) {
+                             int* status, cudaStream_t s, bool tensor_cores) {
   if (!pair_gram_supported(A, na, nb, B) || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
   const PairGeom g = geom(A, na, nb, B);
   CUtensorMap m;
@@ -1054,6 +1310,16 @@ cudaError_t launch_pair_gram(const float* X, int64_t A, int na, int nb, int64_t 
   const double K = (double)A * (double)B;  // columns per row of either unfolding, over the whole tensor
   ProfScope prof(K_PAIR_GRAM, s, (double)na * (na + 1) * K * nb + (double)nb * (nb + 1) * K * na,
                  4.0 * K * na * nb);
+  if (tensor_cores && na == 24 && nb == 24 && g.ntiles <= 0x7fffffffll) {
+    CUtensorMap mi, mj;
+    if (make_map_pair(&mi, X, g, GTC_BAND) && make_map_pair_ji(&mj, X, g, GTC_BAND)) {
+      e = allow_max_smem(reinterpret_cast<const void*>(pair_gram_tc_kernel));
+      if (e != cudaSuccess) return e;
+      pair_gram_tc_kernel<<<grid, GTC_THREADS, GTC_SMEM, s>>>(mi, mj, g, Ga, Gb, status);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   if (na == 24 && nb == 24 && g.ntiles <= 0x7fffffffll) {
     const size_t smem24 = 1024 + G24_STAGES * (size_t)g.stage_bytes + sizeof(double) * 64 * 12;
     e = allow_max_smem(reinterpret_cast<const void*>(pair_gram24_kernel));
