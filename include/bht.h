@@ -326,6 +326,18 @@ bht_status bht_mode_product_noalloc(const float* X, int64_t rows, int64_t K, con
  * ones. n <= 4096. Synchronises `stream`. */
 bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, void* stream);
 
+/* Full-rank certificate of a truncation (eq. ht_leaf_svd, Algorithm 1): the tail rule keeps all n
+ * directions of a node exactly when the smallest eigenvalue of its Gram matrix exceeds the node's
+ * budget eps_nw^2. G: n x n symmetric FP64, device, row-major (its lower triangle is read; G itself
+ * is not written). *above (host) = 1 when the Cholesky factorisation of G - (tau + delta) I runs to
+ * completion in FP64, delta = 2 (n + 4) 2^-53 trace(G): then every eigenvalue of G exceeds tau (delta
+ * covers the factorisation's backward error, gamma_{n+1} |L||L^T|, bounded through the trace).
+ * *above = 0 when a pivot is <= 0 or not a number: no certificate, which does not prove the converse
+ * (an eigenvalue within delta of tau). BHT-l2r gives a certified interior node the identity as its
+ * basis and skips its products. n <= 4096 (BHT_ECAPACITY), tau finite and >= 0 (else BHT_EINVAL).
+ * Synchronises `stream`. */
+bht_status bht_eig_min_above(const double* G, int64_t n, double tau, int32_t* above, void* stream);
+
 /* Getters. Ranks: ranks[0] = items in the accumulation, ranks[i] = rank of
  * node i (breadth-first) for i = 1 .. 2d-2; `cap` is the length of `ranks`. */
 bht_status bht_get_ranks(const bht_state* state, int64_t* ranks, int64_t cap);
@@ -367,7 +379,7 @@ bht_status bht_probe_fma_rate(int32_t dtype, double* tflops, void* stream);
 /* Optional kernel timing. With bit c of class_mask set, every launch of
  * kernel class c made by the calling thread is bracketed by a CUDA event pair
  * recorded on its launch stream. bht_profile_read() waits for the recorded
- * events and returns, per class c < n (n >= 18), the summed durations in ms,
+ * events and returns, per class c < n (n >= 19), the summed durations in ms,
  * the launch counts and the algorithmic work of the timed launches (flops and
  * bytes the mathematics of each launch requires); reset != 0 clears them.
  * Any output pointer may be NULL. Class names come from bht_kernel_class_name(c). */

@@ -94,6 +94,7 @@ def _load():
         "bht_probe_fma_rate": [i32, P(dbl), vp],
         "bht_pair_gram": [vp, i64, i64, i64, i64, vp, vp, i32, vp],
         "bht_pair_project": [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp],
+        "bht_eig_min_above": [vp, i64, ctypes.c_double, ctypes.POINTER(i32), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -113,13 +114,14 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "htrise_update_stream",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
-            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_mode_product_noalloc",
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_eig_min_above",
+            "bht_mode_product_noalloc",
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
             "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode", "ht_l2r",
             "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items",
             "bht_synth_chebyshev", "bht_probe_fma_rate", "bht_pair_gram", "bht_pair_project", "bht_batch_reads",
             "bht_debug_withhold_barrier"]
-KERNEL_CLASSES = 18
+KERNEL_CLASSES = 19
 
 
 def _check(status: int, where: str):
@@ -533,6 +535,19 @@ def bht_sym_eig(G, r: int, stream=None):
     _check(_lib.bht_sym_eig(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
                             ctypes.c_void_p(U.data_ptr()), int(r), _stream(stream)), "bht_sym_eig")
     return lam, U[:, :r]
+
+
+def bht_eig_min_above(G, tau: float, stream=None) -> bool:
+    """True when a Cholesky factorisation certifies that every eigenvalue of the symmetric fp64 CUDA
+    tensor G exceeds tau (G is not written)."""
+    torch = _torch()
+    if G.dtype != torch.float64 or not G.is_cuda or G.dim() != 2 or G.shape[0] != G.shape[1]:
+        raise ValueError("G must be a square float64 CUDA tensor")
+    G = G.contiguous()
+    v = ctypes.c_int32(0)
+    _check(_lib.bht_eig_min_above(ctypes.c_void_p(G.data_ptr()), G.shape[0], float(tau), ctypes.byref(v),
+                                  _stream(stream)), "bht_eig_min_above")
+    return v.value == 1
 
 
 def bht_probe_fma_rate(dtype: str = "float64", stream=None) -> float:

@@ -170,7 +170,7 @@ const char* kernel_class_name(int cls) {
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
                                              "house_f64",      "mlp",            "prep",            "other",
-                                             "pair_proj",      "pair_gram"};
+                                             "pair_proj",      "pair_gram",      "spd_test_f64"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -343,6 +343,10 @@ struct bht_state {
   std::vector<int64_t> rank;    // per node id; rank[0] unused
   std::vector<double*> U;       // per node id: orthonormal matrix form [rows][rank], FP64, device
   std::vector<double*> Q;       // per node id: orthonormal complement of U in R^rows, [rows][rows - rank]
+  // per node id: the basis U[id] when it is the identity of R^rows (a node whose truncation keeps every
+  // direction), else null. A product with it leaves the tensor as it is and is not launched. Cleared
+  // when the node's basis is replaced (a padded or expanded core is no longer the identity).
+  std::vector<const double*> ident;
   double* root = nullptr;       // [root_cap][r11][r12], FP64, device
   int64_t root_cap = 0;
   int64_t n_items = 0;
@@ -1022,6 +1026,20 @@ void check_status_word(int* d_status, cudaStream_t s) {
 
 void check_status(bht_state* st, cudaStream_t s) { check_status_word(st->d_status, s); }
 
+// Whether every eigenvalue of the n x n Gram matrix G (device) exceeds eps_nw2, certified by a Cholesky
+// factorisation of G less a shift that covers its rounding (chol.cu). Then the tail rule of
+// eq. ht_leaf_svd keeps all n directions: the energy discarded with n - 1 kept is the smallest
+// eigenvalue. No certificate (a pivot <= 0) says nothing either way.
+bool certify_full_rank(const double* G, int64_t n, double eps_nw2, int* d_status, cudaStream_t s) {
+  DBuf work(spd_test_workspace_bytes(n), s), v(sizeof(int), s);
+  ck(launch_spd_test(G, n, eps_nw2, work.p, v.as<int>(), d_status, s), "full-rank certificate");
+  check_status_word(d_status, s);
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, v.p, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H verdict");
+  ck(cudaStreamSynchronize(s), "sync");
+  return h == 1;
+}
+
 int num_sms() {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -1210,10 +1228,12 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
     std::vector<int64_t> rs;
     for (int id : t.layers[layer]) {
       if (t.nodes[id].leaf()) continue;  // already contracted
+      if (st->ident[id]) continue;       // the identity: nothing to apply, nothing removed
       ids.push_back(id);
       Us.push_back(st->U[id]);
       rs.push_back(st->rank[id]);
     }
+    if (ids.empty()) continue;
     // small products in place on the FP32 SIMT kernel (the rule of project_layer)
     const bool small = ar.mixed && small_products(C, rs);
     if (ar.mixed && !ar.tight && !small && resid && C.dtype == BHT_F32) {
@@ -1584,6 +1604,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
   st->rank.assign(t.nodes.size(), 0);
   st->U.assign(t.nodes.size(), nullptr);
   st->Q.assign(t.nodes.size(), nullptr);
+  st->ident.assign(t.nodes.size(), nullptr);
   try {
     ck(cudaMalloc(&st->d_status, sizeof(int)), "cudaMalloc status");
     ck(cudaMemsetAsync(st->d_status, 0, sizeof(int), s), "memset status");
@@ -1696,6 +1717,19 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
             ck(cudaMemcpyAsync(G.p, pg->p, sizeof(double) * I * I, cudaMemcpyDeviceToDevice, sk), "pair Gram");
           else
             gram_any(C, ax, G.as<double>(), ark, sk);
+          // an interior node that keeps every direction (eq. ht_leaf_svd with r = I) takes the identity
+          // as its basis: U U^T = I is all the truncation states, and the layer's products skip the node.
+          // Only possible when the unfolding has at least I columns.
+          if (!t.nodes[id].leaf() && I >= 2 && C.numel() / I >= I &&
+              certify_full_rank(G.as<double>(), I, eps_nw2, status.as<int>(), sk)) {
+            double* U = static_cast<double*>(dalloc(sizeof(double) * I * I, sk));
+            ck(launch_fill_identity(U, I, sk), "identity basis");
+            st->U[id] = U;
+            st->rank[id] = I;
+            st->Q[id] = complement_of(U, I, I, complement_seed(id, 0), status.as<int>(), sk);  // empty
+            st->ident[id] = U;
+            return;
+          }
           eig_tridiag64(G.as<double>(), I, eo, status.as<int>(), sk);
           check_status_word(status.as<int>(), sk);
         }
@@ -1708,7 +1742,10 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
       });
       std::vector<const double*> Us;
       std::vector<int64_t> rs;
+      std::vector<int> pids;  // the nodes whose product changes the intermediate (not the identity)
       for (int id : ids) {
+        if (st->ident[id]) continue;
+        pids.push_back(id);
         Us.push_back(st->U[id]);
         rs.push_back(st->rank[id]);
       }
@@ -1716,6 +1753,8 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
         std::vector<int64_t> rows(t.nodes.size(), 0);
         for (int id : ids) rows[id] = st->rows(id);
         C = project_layer_removed(std::move(C), ids, st->U, st->Q, st->rank, t, rows, ar, s, removed.as<double>());
+      } else if (pids.empty()) {
+        // every node of the layer keeps its whole space: the intermediate is the layer's result
       } else {
         // the pairs two axes at a time (pairs later in the axis order first, so that the views of the
         // earlier ones keep their sizes), then any other node of the layer
@@ -1752,7 +1791,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
           for (size_t k = 0; k < ids.size(); ++k) {
             bool paired = false;
             for (const LeafPair& lp : pairs) paired = paired || lp.ida == ids[k] || lp.idb == ids[k];
-            if (!paired) rest_ids.push_back(ids[k]);
+            if (!paired && !st->ident[ids[k]]) rest_ids.push_back(ids[k]);
           }
           for (int id : rest_ids) {
             rest_Us.push_back(st->U[id]);
@@ -1760,7 +1799,7 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
           }
           if (!rest_ids.empty()) C = project_layer(std::move(C), rest_ids, rest_Us, rest_rs, ar, s);
         } else {
-          C = project_layer(std::move(C), ids, Us, rs, ar, s);
+          C = project_layer(std::move(C), pids, Us, rs, ar, s);
         }
       }
       if (adaptive && layer > 1) {
@@ -2115,10 +2154,14 @@ void update_expand(bht_state* st, const void* dY, int32_t dtype, int64_t N, doub
         ck(launch_unit_cols(Pq, q1, q0, ra0, rb0, ra, rb, s), "complement of new coordinates");
         Q[par] = Pq;
       }
-      // Step 1 revisited: project onto the updated cores of the layer
+      // Step 1 revisited: project onto the updated cores of the layer (a basis that is still the
+      // identity leaves the intermediate as it is)
+      std::vector<int> pids;
       std::vector<const double*> Us;
       std::vector<int64_t> rs;
       for (int id : ids) {
+        if (st->ident[id] && U[id] == st->ident[id]) continue;
+        pids.push_back(id);
         Us.push_back(U[id]);
         rs.push_back(rank[id]);
       }
@@ -2127,8 +2170,8 @@ void update_expand(bht_state* st, const void* dY, int32_t dtype, int64_t N, doub
         std::vector<int64_t> rows(t.nodes.size(), 0);
         for (int k = 0; k < nn; ++k) rows[ids[k]] = alpha[k];
         C = project_layer_removed(std::move(C), ids, U, Q, rank, t, rows, ar, s, removed.as<double>());
-      } else {
-        C = project_layer(std::move(C), ids, Us, rs, ar, s);
+      } else if (!pids.empty()) {
+        C = project_layer(std::move(C), pids, Us, rs, ar, s);
       }
       if (adaptive) {
         // App. C on the update: the error spent by the projection onto the updated cores so far
@@ -2160,6 +2203,7 @@ void update_expand(bht_state* st, const void* dY, int32_t dtype, int64_t N, doub
   // commit: release the replaced cores and any intermediate core superseded within this call
   for (size_t id = 1; id < U.size(); ++id) {
     if (U[id] != st->U[id]) {
+      st->ident[id] = nullptr;
       purge_weights(st, st->U[id], s);
       dfree(st->U[id], s);
     }
@@ -2570,6 +2614,20 @@ bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, 
   ck(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   ck(cudaStreamSynchronize(s), "sync");
   if (h) fail((bht_status)h, "a bounded device-side wait gave up (eigensolver)");
+  BHT_API_END
+}
+
+bht_status bht_eig_min_above(const double* G, int64_t n, double tau, int32_t* above, void* stream) {
+  BHT_API_BEGIN
+  if (!G || !above) fail(BHT_EINVAL, "null argument");
+  if (n < 1) fail(BHT_EINVAL, "need n >= 1");
+  if (n > 4096) fail(BHT_ECAPACITY, "n > 4096");
+  if (!(tau >= 0.0) || !std::isfinite(tau)) fail(BHT_EINVAL, "tau must be finite and >= 0");
+  if (!is_device_ptr(G)) fail(BHT_EINVAL, "bht_eig_min_above takes a device matrix");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  *above = certify_full_rank(G, n, tau, status.as<int>(), s) ? 1 : 0;
   BHT_API_END
 }
 

@@ -34,7 +34,8 @@ enum KernelClass {
   K_OTHER = 15,
   K_PAIR_PROJ = 16,  // two-mode projections of small leaves (pair.cu)
   K_PAIR_GRAM = 17,  // two-mode Gram passes (pair.cu)
-  K_NUM_CLASSES = 18
+  K_SPD = 18,        // full-rank certificates by Cholesky factorisation (chol.cu)
+  K_NUM_CLASSES = 19
 };
 const char* kernel_class_name(int cls);
 
@@ -271,6 +272,13 @@ cudaError_t launch_pair_project(const float* X, int64_t A, int na, int nb, int64
                                 double* norm_out, double* resid, int* status, cudaStream_t s);
 
 // A (n x n) += alpha I
+// Certificate that every eigenvalue of the symmetric n x n FP64 matrix G (device, row-major; lower
+// triangle read) exceeds tau >= 0: *verdict (device int) = 1 when the Cholesky factorisation of
+// G - (tau + 2 (n + 4) 2^-53 trace(G)) I completes in FP64, 0 otherwise (chol.cu). n <= 4096; work holds
+// spd_test_workspace_bytes(n); status: device word of the bounded grid barrier.
+size_t spd_test_workspace_bytes(int64_t n);
+cudaError_t launch_spd_test(const double* G, int64_t n, double tau, void* work, int* verdict, int* status,
+                            cudaStream_t s);
 cudaError_t launch_add_diag(double* A, int64_t n, double alpha, cudaStream_t s);
 
 }  // namespace bht
