@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GB/s of tensor stream compressed (BHT-l2r+HT-RISE) at rel err<=eps, fast vs plain FP64"
 L2_BYTES = 129 * 1024 * 1024
-FP64_LA = ("eig_tridiag_f64", "eig_bisect_f64", "gemm_f64", "eig_vec_f64", "eig_back_f64", "house_f64", "spd_test_f64")
+FP64_LA = ("eig_tridiag_f64", "eig_bisect_f64", "gemm_f64", "eig_vec_f64", "eig_back_f64", "house_f64", "spd_test_f64", "ritz_small")
 
 
 def parse(argv=None):

@@ -301,6 +301,17 @@ bht_status bht_pair_gram(const float* X, int64_t A, int64_t na, int64_t nb, int6
 bht_status bht_pair_project(const float* X, int64_t A, int64_t na, int64_t nb, int64_t B, const double* Ua,
                             int64_t ra, const double* Ub, int64_t rb, float* out, double* norms, void* stream);
 
+/* Three-mode pass (eq. ht_leaf_contraction for three leaves, Step 1 of Algorithm 2): X fp32 device
+ * data viewed as [A][n1][n2][n3] (16-byte aligned; the slabs of n1 n2 n3 values contiguous), read once
+ * slab by slab. out[A][r1][r2][r3] (fp32 device) = X x_1 U1^T x_2 U2^T x_3 U3^T with U_m [n_m][r_m] FP64
+ * device bases (row-major); norms (nullable, 3 FP64 device values) receives ||X||^2, ||out||^2 and their
+ * difference added in FP64. Products and sums in FP32. n_m <= 32, r_m <= 8, n2 n3 % 4 == 0 and
+ * n1 n2 n3 <= 13824 with the ring of three slabs and the work areas within 220 KB of shared memory;
+ * other shapes give BHT_EUNSUPPORTED. Synchronises `stream`. */
+bht_status bht_tri_project(const float* X, int64_t A, int64_t n1, int64_t n2, int64_t n3, const double* U1,
+                           int64_t r1, const double* U2, int64_t r2, const double* U3, int64_t r3, float* out,
+                           double* norms, void* stream);
+
 /* bht_mode_product without any device allocation (the paper has no
  * counterpart: this is an interface for callers that may not allocate device
  * memory during the call, e.g. when another allocator owns the GPU's memory or
@@ -325,6 +336,16 @@ bht_status bht_mode_product_noalloc(const float* X, int64_t rows, int64_t K, con
  * U ([n][r] row-major, device) the orthonormal eigenvectors of the r largest
  * ones. n <= 4096. Synchronises `stream`. */
 bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, void* stream);
+
+/* Eigenpairs for the mixed-precision truncation of a small node (eq. ht_leaf_svd, n <= 32, else
+ * BHT_EINVAL): cyclic Jacobi in FP32 on G (n x n symmetric FP64, device, row-major; not written), its
+ * vectors made orthonormal in FP64 by two Newton-Schulz steps, and their Ritz values v_i^T G v_i in FP64.
+ * lam (device, n) receives the Ritz values in decreasing order and V (device, [n][n] row-major) the
+ * vectors as columns in the same order. Keeping the first r columns discards exactly the energy
+ * sum_{i>=r} lam_i, the quantity the tail rule bounds; lam differs from the eigenvalues of G by the square
+ * of the vectors' FP32-level angles. BHT-l2r uses it in the mixed path for nodes of at most 32 rows.
+ * Synchronises `stream`. */
+bht_status bht_sym_eig_small(const double* G, int64_t n, double* lam, double* V, void* stream);
 
 /* Full-rank certificate of a truncation (eq. ht_leaf_svd, Algorithm 1): the tail rule keeps all n
  * directions of a node exactly when the smallest eigenvalue of its Gram matrix exceeds the node's
@@ -379,7 +400,7 @@ bht_status bht_probe_fma_rate(int32_t dtype, double* tflops, void* stream);
 /* Optional kernel timing. With bit c of class_mask set, every launch of
  * kernel class c made by the calling thread is bracketed by a CUDA event pair
  * recorded on its launch stream. bht_profile_read() waits for the recorded
- * events and returns, per class c < n (n >= 19), the summed durations in ms,
+ * events and returns, per class c < n (n >= 21), the summed durations in ms,
  * the launch counts and the algorithmic work of the timed launches (flops and
  * bytes the mathematics of each launch requires); reset != 0 clears them.
  * Any output pointer may be NULL. Class names come from bht_kernel_class_name(c). */

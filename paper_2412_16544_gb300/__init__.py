@@ -95,6 +95,8 @@ def _load():
         "bht_pair_gram": [vp, i64, i64, i64, i64, vp, vp, i32, vp],
         "bht_pair_project": [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp],
         "bht_eig_min_above": [vp, i64, ctypes.c_double, ctypes.POINTER(i32), vp],
+        "bht_sym_eig_small": [vp, i64, vp, vp, vp],
+        "bht_tri_project": [vp, i64, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -114,14 +116,15 @@ EXPORTED = ["bht_tree_create_balanced", "bht_tree_destroy", "bht_tree_info", "bh
             "htrise_update_stream",
             "ht_reconstruct", "ht_encode", "bht_get_ranks", "bht_get_dims", "bht_get_core", "bht_get_root",
             "bht_num_elements", "bht_state_destroy", "bht_launch_count", "bht_last_error", "bht_version",
-            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_eig_min_above",
+            "bht_profile_enable", "bht_profile_read", "bht_kernel_class_name", "bht_mode_product", "bht_sym_eig", "bht_sym_eig_small", "bht_eig_min_above",
             "bht_mode_product_noalloc",
             "bht_mlp_create", "bht_mlp_destroy", "bht_mlp_num_params", "bht_mlp_get_params", "bht_mlp_forward",
             "bht_mlp_loss_grad", "bht_mlp_adam_step", "bht_sketch_features", "ht_decode", "ht_l2r",
             "ht_relative_test_error", "bht_normalize", "bht_denormalize", "bht_permute_items",
-            "bht_synth_chebyshev", "bht_probe_fma_rate", "bht_pair_gram", "bht_pair_project", "bht_batch_reads",
+            "bht_synth_chebyshev", "bht_probe_fma_rate", "bht_pair_gram", "bht_pair_project", "bht_tri_project",
+            "bht_batch_reads",
             "bht_debug_withhold_barrier"]
-KERNEL_CLASSES = 19
+KERNEL_CLASSES = 21
 
 
 def _check(status: int, where: str):
@@ -526,6 +529,19 @@ def bht_pair_project(X, Ua, Ub, norms=None, stream=None):
     return out
 
 
+def bht_tri_project(X, U1, U2, U3, norms=None, stream=None):
+    """X [A, n1, n2, n3] x_1 U1^T x_2 U2^T x_3 U3^T -> [A, r1, r2, r3] (fp32 CUDA X, FP64 CUDA bases)."""
+    torch = _torch()
+    A, n1, n2, n3 = X.shape
+    r1, r2, r3 = U1.shape[1], U2.shape[1], U3.shape[1]
+    out = torch.empty((A, r1, r2, r3), dtype=torch.float32, device=X.device)
+    nptr = ctypes.c_void_p(norms.data_ptr()) if norms is not None else None
+    _check(_lib.bht_tri_project(ctypes.c_void_p(X.data_ptr()), A, n1, n2, n3, ctypes.c_void_p(U1.data_ptr()), r1,
+                                ctypes.c_void_p(U2.data_ptr()), r2, ctypes.c_void_p(U3.data_ptr()), r3,
+                                ctypes.c_void_p(out.data_ptr()), nptr, _stream(stream)), "bht_tri_project")
+    return out
+
+
 def bht_sym_eig(G, r: int, stream=None):
     """Eigenvalues (descending) and the r leading eigenvectors of a symmetric fp64 CUDA tensor G (overwritten)."""
     torch = _torch()
@@ -535,6 +551,21 @@ def bht_sym_eig(G, r: int, stream=None):
     _check(_lib.bht_sym_eig(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
                             ctypes.c_void_p(U.data_ptr()), int(r), _stream(stream)), "bht_sym_eig")
     return lam, U[:, :r]
+
+
+def bht_sym_eig_small(G, stream=None):
+    """Ritz values (decreasing) and orthonormal vectors of a symmetric fp64 CUDA tensor G, n <= 32
+    (FP32 Jacobi, FP64 Newton-Schulz and Ritz values; G is not written)."""
+    torch = _torch()
+    if G.dtype != torch.float64 or not G.is_cuda or G.dim() != 2 or G.shape[0] != G.shape[1]:
+        raise ValueError("G must be a square float64 CUDA tensor")
+    G = G.contiguous()
+    n = G.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=G.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=G.device)
+    _check(_lib.bht_sym_eig_small(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
+                                  ctypes.c_void_p(V.data_ptr()), _stream(stream)), "bht_sym_eig_small")
+    return lam, V
 
 
 def bht_eig_min_above(G, tau: float, stream=None) -> bool:

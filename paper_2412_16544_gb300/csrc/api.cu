@@ -170,7 +170,7 @@ const char* kernel_class_name(int cls) {
                                              "gemm_f64",       "norm",           "copy",            "ttm_tc",
                                              "gram_f32",       "eig_vec_f64",    "eig_back_f64",    "ttm_f32",
                                              "house_f64",      "mlp",            "prep",            "other",
-                                             "pair_proj",      "pair_gram",      "spd_test_f64"};
+                                             "pair_proj",      "pair_gram",      "spd_test_f64",   "tri_proj",       "ritz_small"};
   return (cls >= 0 && cls < K_NUM_CLASSES) ? names[cls] : "?";
 }
 
@@ -877,6 +877,22 @@ void eig_values64(double* G, int64_t n, EigOut& out, int* d_status, cudaStream_t
   out.computed = n;
 }
 
+// The tail rule of eq. ht_leaf_svd / eq. svd_on_residual on all n eigenvalues lam (decreasing) of a
+// Gram matrix of trace tr: the smallest r >= rmin whose discarded energy tr - sum_{i<r} lam_i is at most
+// eps_nw2 (r = n discards nothing), capped at rmax.
+int64_t tail_rank(const double* lam, int64_t n, double tr, double eps_nw2, int64_t rmin, int64_t rmax) {
+  rmax = std::min(rmax, n);
+  double kept = 0.0;
+  for (int64_t r = 0; r <= n; ++r) {
+    if (r >= rmin) {
+      const double tail = (r == n) ? 0.0 : std::max(tr - kept, 0.0);
+      if (tail <= eps_nw2 || r >= rmax) return std::min(r, rmax);
+    }
+    if (r < n) kept += std::max(lam[r], 0.0);
+  }
+  return rmax;
+}
+
 // Truncation rank of eq. ht_leaf_svd / eq. svd_on_residual from the largest eigenvalues only: the
 // discarded energy after r kept values is trace - sum_{i<r} lam_i, so eigenvalues are bisected from the
 // top, in chunks that double, until some r >= rmin meets tail <= eps_nw2 (or all are known).
@@ -931,9 +947,21 @@ void newton_schulz(double* X, int64_t rows, int64_t r, cudaStream_t s, int iters
 double sqnorm_of(const void* x, int dtype, int64_t n, double* d_acc, cudaStream_t s);
 
 // Estimate of ||X^T X - I||_2 for X (rows x r): four power steps on E = X^T X - I from a
-// pseudo-random start, each two matrix-vector products (the ratio of the last two iterates).
+// pseudo-random start, each two matrix-vector products (the ratio of the last two iterates). For
+// r <= 64, ||E||_F itself (an upper bound of ||E||_2) from E formed in one product: three launches
+// instead of a dozen.
 double orth_error(const double* X, int64_t rows, int64_t r, cudaStream_t s) {
   if (r <= 0) return 0.0;
+  if (r <= 64) {
+    DBuf E(sizeof(double) * r * r, s), acc(sizeof(double), s);
+    ck(launch_gemm_f64(r, r, rows, 1.0, X, 1, r, X, r, 1, 0.0, E.as<double>(), r, 1, s), "X^T X");
+    ck(launch_add_diag(E.as<double>(), r, -1.0, s), "- I");
+    sqnorm_of(E.p, BHT_F64, r * r, acc.as<double>(), s);
+    double h = 0.0;
+    ck(cudaMemcpyAsync(&h, acc.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H probe");
+    ck(cudaStreamSynchronize(s), "sync");
+    return std::sqrt(h);
+  }
   DBuf v(sizeof(double) * 2 * r, s), y(sizeof(double) * rows, s), acc(sizeof(double) * 2, s);
   double* x = v.as<double>();
   double* z = x + r;
@@ -1166,6 +1194,34 @@ LTensor project_all(const bht_state* st, const void* Y, int dtype, int64_t N, co
     // two); the energy each pass removes, ||in||^2 - ||out||^2, goes to the skip test's sum
     int m0 = 0;
     while (ar.pairs && m0 + 1 < t.d && C.dtype == BHT_F32 && (reinterpret_cast<uintptr_t>(C.ptr) & 15) == 0) {
+      if (m0 > 0 && m0 + 3 == t.d) {
+        // the last three leaves in one read of the (small) intermediate
+        const int id1 = t.leaf_of_mode[m0], id2 = t.leaf_of_mode[m0 + 1], id3 = t.leaf_of_mode[m0 + 2];
+        int64_t A = N;
+        for (int k = 0; k < m0; ++k) A *= C.dims[k];
+        const int64_t n1 = C.dims[m0], n2 = C.dims[m0 + 1], n3 = C.dims[m0 + 2];
+        const int64_t r1 = st->rank[id1], r2 = st->rank[id2], r3 = st->rank[id3];
+        if (tri_project_supported(A, n1, n2, n3, r1, r2, r3)) {
+          LTensor nxt;
+          nxt.dtype = BHT_F32;
+          nxt.N = C.N;
+          nxt.dims = C.dims;
+          nxt.node = C.node;
+          nxt.dims[m0] = r1;
+          nxt.dims[m0 + 1] = r2;
+          nxt.dims[m0 + 2] = r3;
+          nxt.own = DBuf(sizeof(float) * (size_t)std::max<int64_t>(nxt.numel(), 1), s);
+          nxt.ptr = nxt.own.p;
+          note_read(C.ptr);
+          ck(launch_tri_project(static_cast<const float*>(C.ptr), A, (int)n1, (int)n2, (int)n3, st->U[id1], (int)r1,
+                                (int)r1, st->U[id2], (int)r2, (int)r2, st->U[id3], (int)r3, (int)r3,
+                                nxt.own.as<float>(), nullptr, nullptr, resid, ar.d_status, s),
+             "three-mode projection");
+          C = std::move(nxt);
+          m0 = t.d;
+          break;
+        }
+      }
       const int ida = t.leaf_of_mode[m0], idb = t.leaf_of_mode[m0 + 1];
       int64_t A = N, B = 1;
       for (int k = 0; k < m0; ++k) A *= C.dims[k];
@@ -1420,10 +1476,13 @@ void grow_root(bht_state* st, int64_t r11_old, int64_t r12_old, int64_t r11, int
   int64_t cap = std::max<int64_t>(st->root_cap, 16);
   while (cap < need) cap *= 2;
   DBuf nr(sizeof(double) * cap * r11 * r12, s);
-  if (st->n_items > 0)
+  if (st->n_items > 0 && reshape)
     ck(launch_copy_pad3<double, double>(st->root, st->n_items, r11_old, r12_old, nr.as<double>(), st->n_items, r11,
                                         r12, s),
        "root re-layout");
+  else if (st->n_items > 0)  // the same layout: one contiguous copy
+    ck(cudaMemcpyAsync(nr.p, st->root, sizeof(double) * st->n_items * r11 * r12, cudaMemcpyDeviceToDevice, s),
+       "root copy");
   dfree(st->root, s);
   st->root = static_cast<double*>(nr.release());
   st->root_cap = cap;
@@ -1728,6 +1787,27 @@ bht_state* l2r_build(const bht_tree& t, const void* Y, int dtype, int64_t N, dou
             st->rank[id] = I;
             st->Q[id] = complement_of(U, I, I, complement_seed(id, 0), status.as<int>(), sk);  // empty
             st->ident[id] = U;
+            return;
+          }
+          if (ar.mixed && I <= 32) {
+            // a small node of the mixed path: FP32 Jacobi vectors, FP64 Ritz values (ritz.cu); the tail rule
+            // on the Ritz values bounds the energy that the kept vectors discard, and the other vectors are
+            // their orthonormal complement
+            DBuf lam(sizeof(double) * I, sk), V(sizeof(double) * I * I, sk);
+            ck(launch_small_ritz(G.as<double>(), I, lam.as<double>(), V.as<double>(), sk), "small eigensolve");
+            std::vector<double> hl(I);
+            ck(cudaMemcpyAsync(hl.data(), lam.p, sizeof(double) * I, cudaMemcpyDeviceToHost, sk), "D2H Ritz values");
+            ck(cudaStreamSynchronize(sk), "sync");
+            double tr = 0.0;
+            for (double v : hl) tr += v;
+            const int64_t r = tail_rank(hl.data(), I, tr, eps_nw2, 1, I);  // eq. ht_leaf_svd, r >= 1
+            double* U = static_cast<double*>(dalloc(sizeof(double) * I * r, sk));
+            ck(launch_copy_cols(V.as<double>(), I, I, r, U, r, sk), "kept vectors");
+            double* Qc = static_cast<double*>(dalloc(sizeof(double) * (size_t)std::max<int64_t>(I * (I - r), 1), sk));
+            if (r < I) ck(launch_copy_cols(V.as<double>() + r, I, I, I - r, Qc, I - r, sk), "complement");
+            st->U[id] = U;
+            st->rank[id] = r;
+            st->Q[id] = Qc;
             return;
           }
           eig_tridiag64(G.as<double>(), I, eo, status.as<int>(), sk);
@@ -2276,6 +2356,9 @@ bht_status htrise_update_stream(bht_state* st, const void* Y, int32_t dtype, int
   const char* Yc = static_cast<const char*>(Y);
   const bool host = !is_device_ptr(Y);
   const Arith ar = make_arith(opts ? opts->precision : st->precision, eps_rel, st->d_status);
+  // room in the root for every item of the stream at the current ranks, so that the appends of skipped
+  // updates copy nothing (an expansion re-lays the root out as in htrise_update)
+  grow_root(st, st->r11(), st->r12(), st->r11(), st->r12(), st->n_items + count * N, s);
   // host batches: two device buffers, filled on a copy stream while the previous batch computes
   DBuf buf[2];
   cudaStream_t cs = nullptr;
@@ -2559,6 +2642,27 @@ bht_status bht_pair_project(const float* X, int64_t A, int64_t na, int64_t nb, i
   BHT_API_END
 }
 
+bht_status bht_tri_project(const float* X, int64_t A, int64_t n1, int64_t n2, int64_t n3, const double* U1,
+                           int64_t r1, const double* U2, int64_t r2, const double* U3, int64_t r3, float* out,
+                           double* norms, void* stream) {
+  BHT_API_BEGIN
+  if (!X || !U1 || !U2 || !U3 || !out) fail(BHT_EINVAL, "null argument");
+  if (!tri_project_supported(A, n1, n2, n3, r1, r2, r3)) fail(BHT_EUNSUPPORTED, "shape outside the three-mode projection");
+  if (!is_device_ptr(X) || !is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(U3) || !is_device_ptr(out) ||
+      (norms && !is_device_ptr(norms)))
+    fail(BHT_EINVAL, "device pointers required");
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) fail(BHT_EINVAL, "X must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBuf status(sizeof(int), s);
+  ck(cudaMemsetAsync(status.p, 0, sizeof(int), s), "memset");
+  ck(launch_tri_project(X, A, (int)n1, (int)n2, (int)n3, U1, (int)r1, (int)r1, U2, (int)r2, (int)r2, U3, (int)r3,
+                        (int)r3, out, norms, norms ? norms + 1 : nullptr, norms ? norms + 2 : nullptr,
+                        status.as<int>(), s),
+     "three-mode projection");
+  check_status_word(status.as<int>(), s);
+  BHT_API_END
+}
+
 bht_status bht_mode_product(const float* X, int64_t rows, int64_t K, const double* U, int64_t S, int32_t precision,
                             float* out, int64_t R2, double* norms, void* stream) {
   BHT_API_BEGIN
@@ -2614,6 +2718,17 @@ bht_status bht_sym_eig(double* G, int64_t n, double* lam, double* U, int64_t r, 
   ck(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   ck(cudaStreamSynchronize(s), "sync");
   if (h) fail((bht_status)h, "a bounded device-side wait gave up (eigensolver)");
+  BHT_API_END
+}
+
+bht_status bht_sym_eig_small(const double* G, int64_t n, double* lam, double* V, void* stream) {
+  BHT_API_BEGIN
+  if (!G || !lam || !V) fail(BHT_EINVAL, "null argument");
+  if (n < 1 || n > 32) fail(BHT_EINVAL, "need 1 <= n <= 32");
+  if (!is_device_ptr(G) || !is_device_ptr(lam) || !is_device_ptr(V)) fail(BHT_EINVAL, "device pointers required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ck(launch_small_ritz(G, n, lam, V, s), "small eigensolve");
+  ck(cudaStreamSynchronize(s), "sync");
   BHT_API_END
 }
 

@@ -12,7 +12,9 @@
 // M = fl(G - sigma I) that completes has L L^T = M + dM positive definite and
 // ||dM||_2 <= ||dM||_F <= gamma_{n+1} ||L||_F^2 <= gamma_{n+1} trace(M) / (1 - gamma_{n+1}), so
 // lambda_min(G) > sigma - ((n + 1) u (1 + O(n u)) + 2 u) trace(G). delta = 2 (n + 4) u trace(G), u = 2^-53,
-// with the trace as computed, covers this with room for the rounding of the trace and of sigma itself.
+// with the trace as computed, covers this with room for the rounding of the trace and of sigma itself
+// (and for the pivots' reciprocal square roots, within one ulp, taken in place of a square root and
+// divisions: a few more roundings per entry of L).
 // A pivot <= 0 (or not a number) stops the factorisation: then no certificate is given.
 #include <cmath>
 #include <cstdint>
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(PT_THREADS) spd_test_kernel(const double* __re
   __shared__ double D[PT][PT + 1];  // diagonal tile; its strictly lower part becomes L_kk
   __shared__ double P[PT][PT + 1];  // panel tile (phase 1), row block i of the panel (phase 2)
   __shared__ double R[PT][PT + 1];  // row block j of the panel (phase 2)
-  __shared__ double Ld[PT], Li[PT];  // diagonal of L_kk and its reciprocals
+  __shared__ double Li[PT];          // reciprocals of the diagonal of L_kk
   __shared__ int bad;
   __shared__ double red[33];
   const int tr = threadIdx.x / PT, tc = threadIdx.x % PT;
@@ -75,24 +77,33 @@ __global__ void __launch_bounds__(PT_THREADS) spd_test_kernel(const double* __re
       D[tr][tc] = (tr < kw && tc <= tr) ? A[(size_t)(k0 + tr) * n + k0 + tc] : 0.0;
       if (c > 0) P[tr][tc] = (tr < iw && tc < kw) ? A[(size_t)(i0 + tr) * n + k0 + tc] : 0.0;
       __syncthreads();
+      if (threadIdx.x == 0) {
+        const double d = D[0][0];
+        bad = !(d > 0.0);
+        if (!bad) Li[0] = rsqrt(d);
+      }
+      __syncthreads();
+      // Column j of the diagonal tile and of the panel tile (X L_kk^T = P) in two phases: the column
+      // scaled by 1/L_jj; then the trailing updates, while thread 0 updates the next pivot and takes its
+      // reciprocal square root, so that its scalar chain overlaps the other threads' updates.
       bool ok = true;
       for (int j = 0; j < kw; ++j) {
-        if (threadIdx.x == 0) {
-          const double d = D[j][j];
-          bad = !(d > 0.0);
-          if (!bad) {
-            Ld[j] = sqrt(d);
-            Li[j] = 1.0 / Ld[j];
-          }
-        }
-        __syncthreads();
-        if (bad) {  // read by every thread after the barrier: the branch is uniform
+        if (bad) {  // written by thread 0 before the last barrier: the branch is uniform
           ok = false;
           break;
         }
-        if (tc == j && tr > j && tr < kw) D[tr][j] *= Li[j];
+        const double li = Li[j];
+        if (tc == j && tr > j && tr < kw) D[tr][j] *= li;
+        if (c > 0 && tc == j && tr < iw) P[tr][j] *= li;
         __syncthreads();
-        if (tc > j && tr >= tc && tr < kw) D[tr][tc] -= D[tr][j] * D[tc][j];
+        if (tc > j && tr >= tc && tr < kw && !(tr == j + 1 && tc == j + 1)) D[tr][tc] -= D[tr][j] * D[tc][j];
+        if (c > 0 && tc > j && tc < kw && tr < iw) P[tr][tc] -= P[tr][j] * D[tc][j];
+        if (threadIdx.x == 0 && j + 1 < kw) {
+          const double dn = D[j + 1][j + 1] - D[j + 1][j] * D[j + 1][j];
+          D[j + 1][j + 1] = dn;
+          bad = !(dn > 0.0);
+          if (!bad) Li[j + 1] = rsqrt(dn);
+        }
         __syncthreads();
       }
       if (!ok) {
@@ -100,13 +111,6 @@ __global__ void __launch_bounds__(PT_THREADS) spd_test_kernel(const double* __re
         break;  // c is uniform in the CTA; a failed factor has nothing to solve against
       }
       if (c == 0) continue;
-      // X L_kk^T = P, column by column
-      for (int j = 0; j < kw; ++j) {
-        if (tc == j && tr < iw) P[tr][j] *= Li[j];
-        __syncthreads();
-        if (tc > j && tc < kw && tr < iw) P[tr][tc] -= P[tr][j] * D[tc][j];
-        __syncthreads();
-      }
       if (tr < iw && tc < kw) A[(size_t)(i0 + tr) * n + k0 + tc] = P[tr][tc];
       __syncthreads();
     }
@@ -171,8 +175,9 @@ cudaError_t launch_spd_test(const double* G, int64_t n, double tau, void* work, 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spd_test_kernel, PT_THREADS, 0);
   if (e != cudaSuccess) return e;
-  // at most two CTAs per SM: more only lengthen the barriers once every trailing tile has a CTA
-  const int cap = std::max(1, std::min(per_sm, 2)) * nsm;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // one CTA per SM: more CTAs would only lengthen every grid barrier
+  const int cap = nsm;
   const int grid = std::min(want, cap);
   void* args[] = {&G, &ni, &tau, &A, &bar, &fail, &verdict, &status};
   e = cudaLaunchCooperativeKernel((void*)spd_test_kernel, dim3(grid), dim3(PT_THREADS), args, 0, s);

@@ -117,20 +117,45 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const T* __restrict__ X, 
 // CHC consecutive columns k = a * B + b: CHC values of b inside one a when
 // B >= CHC, CHC / B whole slabs when B < CHC, CHC consecutive a when B == 1. It
 // is staged transposed, Xs[c][i], so four consecutive i are one 16-byte
-// shared load. Thread (tile, group) accumulates the 4 x 4 block (ti, tj),
-// ti <= tj, of G over the chunk columns of its group in FP32; the FP32 partials
-// are added to FP64 registers every GRAM_FOLD chunks, summed over the groups
-// at the end and added to G with FP64 atomics (both triangles).
+// shared load, by 4-byte asynchronous copies into one of two buffers while the
+// other is read (each thread walks its elements of a chunk with a
+// mixed-radix counter: no division per element). Thread (tile, group)
+// accumulates the 4 x 4 block (ti, tj), ti <= tj, of G over the chunk columns
+// of its group in FP32; the FP32 partials are added to FP64 registers every
+// GRAM_FOLD chunks, summed over the groups at the end and added to G with FP64
+// atomics (both triangles).
 // ---------------------------------------------------------------------------
 constexpr int CHC = 128;
 constexpr int GRAM_FOLD = 2;
+constexpr int GRAM_SMALL_THREADS = 256;
 
-__global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict__ X, int64_t A, int I, int64_t B,
-                                                        double* __restrict__ G) {
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// The elements of one chunk a thread copies: (al, i, b) of the chunk's slab al, row i, column b,
+// visited as e = tid, tid + 256, ... of e = (al * I + i) * nb + b, advanced without division.
+struct ChunkWalk {
+  int b0, i0, al0;      // decomposition of tid
+  int db, di, dal;      // of the step 256 (b carries into i, i into al)
+  __device__ void init(int tid, int nb, int I) {
+    b0 = tid % nb;
+    const int t = tid / nb;
+    i0 = t % I;
+    al0 = t / I;
+    db = GRAM_SMALL_THREADS % nb;
+    const int tq = GRAM_SMALL_THREADS / nb;
+    di = tq % I;
+    dal = tq / I;
+  }
+};
+
+__global__ void __launch_bounds__(GRAM_SMALL_THREADS) gram_small_kernel(const float* __restrict__ X, int64_t A,
+                                                                        int I, int64_t B, double* __restrict__ G) {
   const int Ip = (I + 3) & ~3, T4 = Ip / 4, ntiles = T4 * (T4 + 1) / 2;
   const int groups = max(1, (int)blockDim.x / ntiles);
-  extern __shared__ __align__(16) float gs[];  // Xs[CHC][Ip], then the FP64 reduction area
-  float* Xs = gs;
+  extern __shared__ __align__(16) float gs[];  // Xs[2][CHC][Ip], then the FP64 reduction area
   const int tid = threadIdx.x;
   const int tile = tid % ntiles, grp = tid / ntiles;
   const bool active = grp < groups;
@@ -148,6 +173,31 @@ __global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict
   const int64_t chunks_b = (B == 1) ? 1 : (B + nb - 1) / nb;      // chunks along b in one slab group
   const int64_t groups_a = (A + na - 1) / na;
   const int64_t nchunks = groups_a * chunks_b;
+  // zero both buffers once: the copies never write rows i >= I
+  for (int e = tid; e < 2 * CHC * Ip; e += blockDim.x) gs[e] = 0.f;
+  __syncthreads();
+  ChunkWalk w;
+  w.init(tid, (int)nb, I);
+  const int nbi = (int)nb;
+  auto stage = [&](int64_t ch, float* Xs) {
+    if (ch < nchunks) {
+      const int64_t ga = ch / chunks_b, gb = ch - ga * chunks_b;
+      const int64_t a0 = ga * na, b0 = gb * nb;
+      const int nah = (int)min(na, A - a0), nbh = (int)min(nb, B - b0);
+      const float* src = X + (a0 * I) * B + b0;
+      int b = w.b0, i = w.i0, al = w.al0;
+      while (al < nah) {
+        if (b < nbh) cp_async_f32(Xs + (al * nbi + b) * Ip + i, src + ((int64_t)al * I + i) * B + b);
+        b += w.db;
+        int carry = 0;
+        if (b >= nbi) { b -= nbi; carry = 1; }
+        i += w.di + carry;
+        al += w.dal;
+        if (i >= I) { i -= I; ++al; }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   double acc64[4][4];
   float acc[4][4];
 #pragma unroll
@@ -155,31 +205,16 @@ __global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict
 #pragma unroll
     for (int v = 0; v < 4; ++v) { acc64[u][v] = 0.0; acc[u][v] = 0.f; }
   int since = 0;
+  int buf = 0;
+  stage(blockIdx.x, gs);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    stage(ch + gridDim.x, gs + (buf ^ 1) * CHC * Ip);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
+    const float* Xs = gs + buf * CHC * Ip;
     const int64_t ga = ch / chunks_b, gb = ch - ga * chunks_b;
     const int64_t a0 = ga * na, b0 = gb * nb;
-    const int64_t na_here = min(na, A - a0), nb_here = min(nb, B - b0);
-    const int ncol = (int)(na_here * nb_here);
-    __syncthreads();
-    // 32-bit index arithmetic in the staging loops (a chunk holds CHC x Ip entries)
-    if (B == 1) {
-      const float* src = X + a0 * I;
-      for (int e = tid; e < CHC * Ip; e += blockDim.x) {
-        const int c = e / Ip, i = e - c * Ip;
-        Xs[c * Ip + i] = (c < ncol && i < I) ? src[(int64_t)c * I + i] : 0.f;
-      }
-    } else {
-      const int nbi = (int)nb, nai = (int)na, nbh = (int)nb_here, nah = (int)na_here;
-      const float* src = X + (a0 * I) * B + b0;
-      for (int e = tid; e < CHC * Ip; e += blockDim.x) {
-        const int t = e / nbi, b = e - t * nbi;
-        const int i = t / nai, al = t - i * nai;
-        float v = 0.f;
-        if (i < I && al < nah && b < nbh) v = src[((int64_t)al * I + i) * B + b];
-        if (i < Ip) Xs[(al * nbi + b) * Ip + i] = v;
-      }
-    }
-    __syncthreads();
+    const int ncol = (int)(min(na, A - a0) * min(nb, B - b0));
     if (active) {
       for (int c = grp; c < ncol; c += groups) {
         const float4 x = *reinterpret_cast<const float4*>(Xs + c * Ip + 4 * ti);
@@ -198,7 +233,10 @@ __global__ void __launch_bounds__(256) gram_small_kernel(const float* __restrict
           for (int v = 0; v < 4; ++v) { acc64[u][v] += (double)acc[u][v]; acc[u][v] = 0.f; }
       }
     }
+    __syncthreads();  // this buffer is refilled by the next iteration's copies
+    buf ^= 1;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -655,17 +693,22 @@ cudaError_t launch_gram_f32(const float* X, double* G, int64_t A, int64_t I, int
     // short index: the streaming kernel (the caller zeroed G)
     const int Ip = (int)((I + 3) & ~3);
     const int T4 = Ip / 4, ntiles = T4 * (T4 + 1) / 2;
-    const size_t sm = std::max(sizeof(float) * CHC * Ip, sizeof(double) * 16 * (size_t)ntiles);
+    const size_t sm = std::max(sizeof(float) * 2 * CHC * Ip, sizeof(double) * 16 * (size_t)ntiles);
     int64_t nb = (B == 1) ? 1 : (B >= CHC ? CHC : B), na = (B == 1) ? CHC : (B >= CHC ? 1 : CHC / B);
     const int64_t nchunks = ((A + na - 1) / na) * ((B == 1) ? 1 : (B + nb - 1) / nb);
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::min<int64_t>(nchunks, 4 * (int64_t)nsm);
+    cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(gram_small_kernel));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_small_kernel, GRAM_SMALL_THREADS, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = (int)std::min<int64_t>(nchunks, (int64_t)std::min(per_sm, 4) * nsm);
     const int64_t K = A * B;
     ProfScope prof(K_GRAM_F32, s, (double)I * (double)(I + 1) * (double)K,
                    4.0 * (double)K * (double)I + 8.0 * (double)I * (double)I);
-    gram_small_kernel<<<grid, 256, sm, s>>>(X, A, (int)I, B, G);
+    gram_small_kernel<<<grid, GRAM_SMALL_THREADS, sm, s>>>(X, A, (int)I, B, G);
     note_launch();
     return cudaGetLastError();
   }

@@ -13,7 +13,7 @@
 //            orthogonalises its members), then the back-transformation U = Q Z.
 // GB300 has few FP64 units (about 2 FMA per clock per SM), so every stage is
 // spread over the whole GPU: the tridiagonalisation keeps the matrix rows in
-// the shared memory of one cooperative grid (one CTA for n <= 16) with one
+// the shared memory of one cooperative grid (one CTA for n <= 64) with one
 // bounded grid barrier per column; matrices too large for that fall back to a
 // global-memory form with two barriers per column.
 #include <algorithm>
@@ -34,6 +34,8 @@ namespace {
 
 constexpr int EIG_THREADS = 256;
 constexpr int SMALL_N = 16;
+constexpr int ONE_CTA_N = 64;  // the row-resident tridiagonalisation runs in one CTA up to this size: its
+                               // per-column FP64 work (2 n^2 FMAs) stays below a grid barrier's latency
 
 // ---------------------------------------------------------------------------
 // Householder tridiagonalisation of the symmetric matrix A (n x n, both
@@ -852,7 +854,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (n > SMALL_N && autotune_on()) {
+  if (n > ONE_CTA_N && autotune_on()) {
     const int64_t key = (int64_t)dev * 4096 + (n + 31) / 32;
     int rpb = tuned_rows(key);
     if (rpb < 0) {
@@ -872,7 +874,7 @@ cudaError_t launch_eig_tridiag(double* G, int64_t n, void* work, int* status, cu
     // rows resident in shared memory: one CTA for a small matrix, else about one warp per row
     // (at least ceil(n / #SM) rows per CTA, at most one CTA per SM)
     const int warps = EIG_THREADS / 32;
-    const int rpb = n <= SMALL_N ? (int)n : (int)std::max<int64_t>(warps, (n + nsm - 1) / nsm);
+    const int rpb = n <= ONE_CTA_N ? (int)n : (int)std::max<int64_t>(warps, (n + nsm - 1) / nsm);
     const int nbk = (int)((n + rpb - 1) / rpb);
     const size_t smr = sizeof(double) * (size_t)(rpb + 4) * (size_t)n;
     if (smr <= 200 * 1024) {

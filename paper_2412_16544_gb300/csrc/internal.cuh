@@ -35,7 +35,9 @@ enum KernelClass {
   K_PAIR_PROJ = 16,  // two-mode projections of small leaves (pair.cu)
   K_PAIR_GRAM = 17,  // two-mode Gram passes (pair.cu)
   K_SPD = 18,        // full-rank certificates by Cholesky factorisation (chol.cu)
-  K_NUM_CLASSES = 19
+  K_TRI_PROJ = 19,   // three-mode projections (tri.cu)
+  K_RITZ = 20,       // small eigenproblems by FP32 Jacobi and FP64 Ritz values (ritz.cu)
+  K_NUM_CLASSES = 21
 };
 const char* kernel_class_name(int cls);
 
@@ -272,6 +274,19 @@ cudaError_t launch_pair_project(const float* X, int64_t A, int na, int nb, int64
                                 double* norm_out, double* resid, int* status, cudaStream_t s);
 
 // A (n x n) += alpha I
+// out[A][r1][r2][r3] (fp32) = X x_1 U1^T x_2 U2^T x_3 U3^T for X fp32 [A][n1][n2][n3] (16-byte aligned,
+// slabs contiguous) and FP64 bases U_m [n_m][r_m] (row stride ld_m); norm_in, norm_out, resid (nullable
+// FP64 device accumulators) receive ||X||^2, ||out||^2 and their difference added (tri.cu).
+bool tri_project_supported(int64_t A, int64_t n1, int64_t n2, int64_t n3, int64_t r1, int64_t r2, int64_t r3);
+cudaError_t launch_tri_project(const float* X, int64_t A, int n1, int n2, int n3, const double* U1, int r1, int ld1,
+                               const double* U2, int r2, int ld2, const double* U3, int r3, int ld3, float* out,
+                               double* norm_in, double* norm_out, double* resid, int* status, cudaStream_t s);
+
+// Eigenpairs of the symmetric n x n FP64 matrix G (device, n <= 32) for a mixed-precision truncation:
+// lam[n] the Ritz values of FP32 Jacobi vectors made orthonormal in FP64, in decreasing order, and
+// V[n][n] (row-major) those vectors in the same order (ritz.cu).
+cudaError_t launch_small_ritz(const double* G, int64_t n, double* lam, double* V, cudaStream_t s);
+
 // Certificate that every eigenvalue of the symmetric n x n FP64 matrix G (device, row-major; lower
 // triangle read) exceeds tau >= 0: *verdict (device int) = 1 when the Cholesky factorisation of
 // G - (tau + 2 (n + 4) 2^-53 trace(G)) I completes in FP64, 0 otherwise (chol.cu). n <= 4096; work holds

@@ -1,6 +1,8 @@
 """Kernel-level GPU checks through the C ABI: the node eigensolver against
 LAPACK (numpy.linalg.eigh) and the tensor-core mode product against an FP64
 matrix product, on shapes that span several tiles and ragged tails."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -157,3 +159,80 @@ def test_pair_project_matches_fp64(B, A, na, nb, Bc, ra, rb):
     assert abs(n[0] - x2) <= 1e-6 * x2
     assert abs(n[1] - o2) <= 2e-6 * o2
     assert abs(n[2] - (n[0] - n[1])) <= 1e-9 * x2
+
+
+TRI_SHAPES = [
+    (50, 24, 24, 24, 7, 7, 7),    # the 24^5 stream's last three leaves (one slab per item and column pair)
+    (7, 24, 24, 24, 8, 1, 5),     # fewer slabs than SMs
+    (300, 12, 20, 8, 3, 8, 2),    # ragged sizes, 300 slabs over the ring's three stages
+    (5, 32, 16, 24, 8, 8, 8),     # a large slab (12288 values), ranks 8
+    (1000, 1, 4, 1, 1, 2, 1),     # degenerate modes
+]
+
+
+@pytest.mark.parametrize("A,n1,n2,n3,r1,r2,r3", TRI_SHAPES)
+def test_tri_project_matches_fp64(B, A, n1, n2, n3, r1, r2, r3):
+    r1, r2, r3 = min(r1, n1), min(r2, n2), min(r3, n3)
+    rng = np.random.default_rng(A + n1 + n2 + n3)
+    X = (rng.normal(size=(A, n1, n2, n3)) * np.linspace(1.0, 0.1, n1)[None, :, None, None]).astype(np.float32)
+    U = [np.linalg.qr(rng.normal(size=(n, n)))[0][:, :r].copy() for n, r in ((n1, r1), (n2, r2), (n3, r3))]
+    norms = torch.zeros(3, dtype=torch.float64, device="cuda")
+    out = B.bht_tri_project(torch.from_numpy(X).cuda(), *[torch.from_numpy(u).cuda() for u in U],
+                            norms=norms).cpu().numpy().astype(np.float64)
+    ref = np.einsum("xijk,ia,jb,kc->xabc", X.astype(np.float64), *U)
+    # FP32 products on FP32-rounded bases, three contractions: about 2^-24 sqrt(n1 n2 n3) relative
+    assert np.linalg.norm(out - ref) <= 4e-6 * np.linalg.norm(ref)
+    n = norms.cpu().numpy()
+    x2, o2 = float(np.sum(X.astype(np.float64) ** 2)), float(np.sum(ref ** 2))
+    assert abs(n[0] - x2) <= 1e-6 * x2
+    assert abs(n[1] - o2) <= 4e-6 * o2
+    assert abs(n[2] - (n[0] - n[1])) <= 1e-9 * x2
+
+
+def test_tri_project_arguments(B):
+    X = torch.zeros((2, 24, 24, 24), dtype=torch.float32, device="cuda")
+    U = torch.zeros((24, 7), dtype=torch.float64, device="cuda")
+    for bad in [(2, 24, 24, 33, 7, 7, 7), (2, 24, 24, 24, 7, 9, 7), (2, 24, 3, 5, 7, 3, 5), (2, 32, 32, 32, 7, 7, 7)]:
+        A, n1, n2, n3, r1, r2, r3 = bad
+        st = B._lib.bht_tri_project(ctypes.c_void_p(X.data_ptr()), A, n1, n2, n3, ctypes.c_void_p(U.data_ptr()), r1,
+                                    ctypes.c_void_p(U.data_ptr()), r2, ctypes.c_void_p(U.data_ptr()), r3,
+                                    ctypes.c_void_p(X.data_ptr()), None, None)
+        assert st == B.BHT_EUNSUPPORTED
+    host = np.zeros(4, dtype=np.float32)
+    st = B._lib.bht_tri_project(ctypes.c_void_p(host.ctypes.data), 1, 1, 4, 1, ctypes.c_void_p(U.data_ptr()), 1,
+                                ctypes.c_void_p(U.data_ptr()), 1, ctypes.c_void_p(U.data_ptr()), 1,
+                                ctypes.c_void_p(X.data_ptr()), None, None)
+    assert st == B.BHT_EINVAL
+
+
+def _small_gram(kind, n, rng):
+    if kind == "graded":
+        X = rng.normal(size=(n, n + 5)) * np.logspace(0, -4, n)[:, None]
+    elif kind == "lowrank":
+        X = rng.normal(size=(n, 3)) @ rng.normal(size=(3, 60)) + 1e-3 * rng.normal(size=(n, 60))
+    elif kind == "random":
+        X = rng.normal(size=(n, 2 * n))
+    else:
+        return np.zeros((n, n))
+    return X @ X.T
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 17, 24, 31, 32])
+@pytest.mark.parametrize("kind", ["graded", "lowrank", "random", "zero"])
+def test_sym_eig_small_ritz_values(B, n, kind):
+    """FP32 Jacobi vectors made orthonormal in FP64 and their FP64 Ritz values: V is orthonormal to
+    rounding, lam_i = v_i^T G v_i, and keeping the first r vectors discards sum_{i>=r} lam_i, which exceeds
+    the optimal tail (the sum of the smallest eigenvalues) by at most the square of the vectors' FP32-level
+    angles: 2e-7 of the trace allows for clusters inside the FP32 rounding of G (measured up to 5e-8)."""
+    rng = np.random.default_rng(n * 7 + len(kind))
+    G = _small_gram(kind, n, rng)
+    lam, V = B.bht_sym_eig_small(torch.from_numpy(G).cuda())
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    tr = max(np.trace(G), 1e-300)
+    assert np.all(np.diff(lam) <= 0)
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13
+    assert np.abs(np.diag(V.T @ G @ V) - lam).max() <= 1e-12 * tr
+    w = np.linalg.eigvalsh(G)[::-1]
+    for r in range(n):
+        excess = lam[r:].sum() - w[r:].sum()
+        assert -1e-12 * tr <= excess <= 2e-7 * tr
