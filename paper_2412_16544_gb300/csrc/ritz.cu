@@ -1,8 +1,8 @@
 // ritz.cu — eigenpairs of a small symmetric FP64 matrix (n <= 32) for the mixed-precision truncation of
 // eq. ht_leaf_svd, in one CTA:
-//   1. cyclic Jacobi in FP32 (round-robin ordering: n/2 disjoint rotations per round, applied to the rows,
-//      then to the columns and to V), a rotation only where |a_pq| > 2^-23 sqrt(|a_pp a_qq|), until a sweep
-//      rotates nothing or after 8 sweeps;
+//   1. cyclic Jacobi in FP32 (round-robin ordering: n/2 disjoint rotations per round, applied as 2 x 2
+//      blocks of J^T A J and columns of V J), a rotation only where |a_pq| > 2^-23 sqrt(|a_pp a_qq|), until a
+//      sweep rotates nothing or after 8 sweeps;
 //   2. V to FP64, made orthonormal by two Newton-Schulz steps V <- V (3I - V^T V) / 2 (an orthonormality
 //      error e becomes about 3e^2/4 per step);
 //   3. the Ritz values h_i = v_i^T G v_i in FP64, sorted in decreasing order with their vectors.
@@ -32,14 +32,13 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
                                                                 double* __restrict__ lam, double* __restrict__ Vout) {
   __shared__ float A[RZ_MAX][RZ_MAX + 1];
   __shared__ float V[RZ_MAX][RZ_MAX + 1];
-  __shared__ float cs[RZ_MAX / 2][2];
-  __shared__ int pq[RZ_MAX / 2][2];
+  __shared__ float4 rot[RZ_MAX / 2];  // (p, q as bits, c, s) of the round's rotations
+  __shared__ int done;
   __shared__ double W[RZ_MAX][RZ_MAX + 1];   // FP64 V
   __shared__ double S[RZ_MAX][RZ_MAX + 1];   // V^T V, then G V
   __shared__ double Gs[RZ_MAX][RZ_MAX + 1];
   __shared__ double h[RZ_MAX];
   __shared__ double gmax[RZ_THREADS / 32];
-  __shared__ int done;
   const int tid = threadIdx.x;
   const int m = n + (n & 1);  // an even number of players; index n (odd n) is a zero row and column
   double mx = 0.0;
@@ -65,20 +64,31 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
   __syncthreads();
 
   // 1. FP32 cyclic Jacobi. A rotation is skipped when |a_pq| <= 2^-23 sqrt(|a_pp a_qq|) (the relative
-  // criterion that keeps graded matrices accurate); the sweeps end when one skipped them all.
+  // criterion that keeps graded matrices accurate); the sweeps end when one skipped them all. A round
+  // applies its m/2 disjoint rotations in one phase: thread (x, y) owns the 2 x 2 block of rows of pair x
+  // and columns of pair y and forms (J^T A J) there from the old entries; the columns of V likewise. The
+  // tasks of a thread are the same in every round, so their indices are taken once.
+  const int hp = m / 2;
+  const bool blk = tid < hp * hp;
+  const int kx = blk ? tid / hp : 0, ky = blk ? tid - (tid / hp) * hp : 0;
+  int vi[2], vk[2];
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * RZ_THREADS;
+    vi[u] = e < m * hp ? e / hp : -1;
+    vk[u] = e < m * hp ? e - (e / hp) * hp : 0;
+  }
   for (int sweep = 0; sweep < RZ_SWEEPS; ++sweep) {
     if (tid == 0) done = 1;
     __syncthreads();
     for (int round = 0; round < m - 1; ++round) {
       // pairs of this round (circle method: player m-1 fixed, the others rotate)
-      if (tid < m / 2) {
-        int p, q;
-        if (tid == 0) {
-          p = round;
-          q = m - 1;
-        } else {
-          p = (round + tid) % (m - 1);
-          q = (round - tid + (m - 1)) % (m - 1);
+      if (tid < hp) {
+        int p = round, q = m - 1;
+        if (tid > 0) {
+          p = round + tid;
+          if (p >= m - 1) p -= m - 1;
+          q = round - tid;
+          if (q < 0) q += m - 1;
         }
         if (p > q) {
           const int t = p;
@@ -89,38 +99,41 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
         const float apq = A[p][q];
         if (q < n && apq != 0.f && fabsf(apq) > 0x1p-23f * sqrtf(fabsf(A[p][p] * A[q][q]))) {
           done = 0;
-          const float tau = (A[q][q] - A[p][p]) / (2.f * apq);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = 1.f / sqrtf(1.f + t * t);
+          const float tau = __fdividef(A[q][q] - A[p][p], 2.f * apq);
+          float t;
+          if (fabsf(tau) > 1e15f) {
+            t = __fdividef(0.5f, tau);
+          } else {
+            const float hh = 1.f + tau * tau;
+            t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + hh * rsqrtf(hh));
+          }
+          c = rsqrtf(1.f + t * t);
           sn = t * c;
         }
-        pq[tid][0] = p;
-        pq[tid][1] = q;
-        cs[tid][0] = c;
-        cs[tid][1] = sn;
+        rot[tid] = make_float4(__int_as_float(p), __int_as_float(q), c, sn);
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < (m / 2) * m; e += blockDim.x) {
-        const int k = e / m, j = e % m;
-        const int p = pq[k][0], q = pq[k][1];
-        const float c = cs[k][0], sn = cs[k][1];
-        const float ap = A[p][j], aq = A[q][j];
-        A[p][j] = c * ap - sn * aq;
-        A[q][j] = sn * ap + c * aq;
+      if (blk) {
+        const float4 rx = rot[kx], ry = rot[ky];
+        const int px = __float_as_int(rx.x), qx = __float_as_int(rx.y);
+        const int py = __float_as_int(ry.x), qy = __float_as_int(ry.y);
+        const float cx = rx.z, sx = rx.w, cy = ry.z, sy = ry.w;
+        const float a = A[px][py], b = A[px][qy], c = A[qx][py], d = A[qx][qy];
+        const float rp0 = cx * a - sx * c, rp1 = cx * b - sx * d;  // row p of J^T A
+        const float rq0 = sx * a + cx * c, rq1 = sx * b + cx * d;  // row q
+        A[px][py] = cy * rp0 - sy * rp1;
+        A[px][qy] = sy * rp0 + cy * rp1;
+        A[qx][py] = cy * rq0 - sy * rq1;
+        A[qx][qy] = sy * rq0 + cy * rq1;
       }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = tid; e < (m / 2) * m; e += blockDim.x) {
-        const int k = e / m, i = e % m;
-        const int p = pq[k][0], q = pq[k][1];
-        const float c = cs[k][0], sn = cs[k][1];
-        const float ap = A[i][p], aq = A[i][q];
-        A[i][p] = c * ap - sn * aq;
-        A[i][q] = sn * ap + c * aq;
-        const float vp = V[i][p], vq = V[i][q];
-        V[i][p] = c * vp - sn * vq;
-        V[i][q] = sn * vp + c * vq;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (vi[u] < 0) continue;
+        const float4 ry = rot[vk[u]];
+        const int py = __float_as_int(ry.x), qy = __float_as_int(ry.y);
+        const float vp = V[vi[u]][py], vq = V[vi[u]][qy];
+        V[vi[u]][py] = ry.z * vp - ry.w * vq;
+        V[vi[u]][qy] = ry.w * vp + ry.z * vq;
       }
       __syncthreads();
     }
@@ -135,21 +148,31 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
     W[i][j] = (double)V[i][j];
   }
   __syncthreads();
+  // products with four partial sums per entry: dependency chains a quarter as long
+  auto dot4 = [&](const double* a, int sa, const double* b, int sb) {
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+      c0 = fma(a[k * sa], b[k * sb], c0);
+      c1 = fma(a[(k + 1) * sa], b[(k + 1) * sb], c1);
+      c2 = fma(a[(k + 2) * sa], b[(k + 2) * sb], c2);
+      c3 = fma(a[(k + 3) * sa], b[(k + 3) * sb], c3);
+    }
+    for (; k < n; ++k) c0 = fma(a[k * sa], b[k * sb], c0);
+    return (c0 + c1) + (c2 + c3);
+  };
+  constexpr int LD = RZ_MAX + 1;
   for (int step = 0; step < 2; ++step) {
-    for (int e = tid; e < n * n; e += blockDim.x) {  // S = V^T V
+    for (int e = tid; e < n * n; e += blockDim.x) {  // S = (3I - V^T V) / 2
       const int i = e / n, j = e % n;
-      double acc = 0.0;
-      for (int k = 0; k < n; ++k) acc = fma(W[k][i], W[k][j], acc);
-      S[i][j] = acc;
+      S[i][j] = (i == j ? 1.5 : 0.0) - 0.5 * dot4(&W[0][i], LD, &W[0][j], LD);
     }
     __syncthreads();
     double nv[4];
     int cnt = 0;
-    for (int e = tid; e < n * n; e += blockDim.x, ++cnt) {  // V (3I - S) / 2, at most four entries a thread
+    for (int e = tid; e < n * n; e += blockDim.x, ++cnt) {  // V S, at most four entries a thread
       const int i = e / n, j = e % n;
-      double acc = 0.0;
-      for (int k = 0; k < n; ++k) acc = fma(W[i][k], (k == j ? 3.0 : 0.0) - S[k][j], acc);
-      nv[cnt] = 0.5 * acc;
+      nv[cnt] = dot4(&W[i][0], 1, &S[0][j], LD);
     }
     __syncthreads();
     cnt = 0;
@@ -159,9 +182,7 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
   // 3. Ritz values: S = G V, h_j = v_j^T (G v_j)
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc = fma(Gs[i][k], W[k][j], acc);
-    S[i][j] = acc;
+    S[i][j] = dot4(&Gs[i][0], 1, &W[0][j], LD);
   }
   __syncthreads();
   if (tid < n) {
