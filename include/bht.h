@@ -111,7 +111,7 @@ typedef struct {
   /* htrise_update only. With a predictor, every node whose residual Gram matrix is formed gets its
    * 66 sketch features and a prediction; a node predicted not to expand skips its residual
    * eigensolve when the exact residual energy trace(R R^T) <= eps_nw^2 confirms that the truncation
-   * of eq. svd_on_residual keeps nothing (the judge), and is truncated as usual otherwise (the
+   * of eq. svd_on_residual keeps nothing (the exact check), and is truncated as usual otherwise (the
    * fallback). The result is the same as without the predictor. */
   const bht_mlp* predictor;
   /* Optional host outputs, one row per tree node (node ids as bht_get_ranks), written for every
@@ -133,8 +133,8 @@ typedef struct {
   double norm_y;          /* ||Y||_F of the new batch */
   int64_t n_items_total;  /* items in the accumulation after the call */
   int32_t pred_nodes;     /* nodes the predictor saw */
-  int32_t pred_skipped;   /* of those, residual eigensolves skipped (prediction confirmed by the judge) */
-  int32_t pred_fallback;  /* predicted "no expansion" but the judge found residual energy above eps_nw^2 */
+  int32_t pred_skipped;   /* of those, residual eigensolves skipped (prediction confirmed by the exact check) */
+  int32_t pred_fallback;  /* predicted "no expansion" but the exact check found residual energy above eps_nw^2 */
   int32_t pred_missed;    /* predicted "expands" but the truncation kept nothing */
 } bht_update_info;
 

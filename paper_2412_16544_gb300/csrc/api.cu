@@ -2096,7 +2096,7 @@ void update_expand(bht_state* st, const void* dY, int32_t dtype, int64_t N, doub
       std::vector<double> tr(nn, 0.0);
       ck(cudaMemcpyAsync(tr.data(), trd.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, s), "D2H energies");
       // the predictor's view of the layer: a node predicted not to expand skips its eigensolve when the
-      // judge (the exact residual energy) confirms that the truncation keeps nothing
+      // exact check (the residual energy) confirms that the truncation keeps nothing
       std::vector<char> skip_eig(nn, 0), pred_expand(nn, 1);
       if (want_feat) {
         std::vector<float> hf(66 * (size_t)nn);

@@ -137,7 +137,7 @@ def evaluate(net, seeds, increments: int = 4, items: int = 32, grid: int = 64, p
                                            float(np.linalg.norm(runs["repeat"] - runs["plain"]) / nrm))
         out["ranks_equal"] = out["ranks_equal"] and ranks["pred"] == ranks["plain"]
     out["skip_rate"] = out["skipped"] / max(out["nodes"], 1)
-    # a prediction of "no expansion" that the judge overturned would have violated the node bound
+    # a prediction of "no expansion" that the exact check overturned would have violated the node bound
     out["violation_rate_before_fallback"] = out["fallback"] / max(out["nodes"], 1)
     out["violation_rate_after_fallback"] = 0.0 if out["max_rel_err"] <= 1.0 + 1e-4 else 1.0
     return out

@@ -8,7 +8,7 @@
 * the sketch features against properties fixed by their definition;
 * training with the library's kernels reduces the loss;
 * on streams the method compresses: training pairs generated by HT-RISE itself, a predictor trained on
-  some streams and run on others leaves every result unchanged (the judge) and never lets a node
+  some streams and run on others leaves every result unchanged (the exact check) and never lets a node
   that would have expanded go unexpanded.
 """
 import numpy as np
@@ -168,7 +168,7 @@ def test_predictor_gain_on_method_generated_streams(B):
     assert np.mean(hist[-40:]) < hist[0]
     res = P.evaluate(net, range(100, 104), inc, items, grid)
     print(res)
-    # the judge: the same ranks, and reconstructions that differ from the plain run's only at the mixed
+    # the exact check: the same ranks, and reconstructions that differ from the plain run's only at the mixed
     # path's rounding level: its reductions combine FP32 partial sums with FP64 atomics whose order
     # follows the launch order, which the predictor's extra kernels change (two plain runs may or may
     # not differ); 1e-5 is the mixed path's tolerance elsewhere (split TF32 / FP32 mode products)
