@@ -5,7 +5,8 @@
 //      sweep rotates nothing or after 8 sweeps;
 //   2. V to FP64, made orthonormal by two Newton-Schulz steps V <- V (3I - V^T V) / 2 (an orthonormality
 //      error e becomes about 3e^2/4 per step);
-//   3. the Ritz values h_i = v_i^T G v_i in FP64, sorted in decreasing order with their vectors.
+//   3. one FP64 refinement of the vectors (first-order eigenvectors of V^T G V, then Newton-Schulz);
+//   4. the Ritz values h_i = v_i^T G v_i in FP64, sorted in decreasing order with their vectors.
 // On GB300 the FP64 units issue at 1/64 of the FP32 rate, so the FP64 eigensolver's sequential chains
 // (tridiagonalisation, bisection, inverse iteration) cost about 0.4 ms even at n = 24; here the iterative
 // part runs in FP32 and FP64 only forms products.
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
   __shared__ double W[RZ_MAX][RZ_MAX + 1];   // FP64 V
   __shared__ double S[RZ_MAX][RZ_MAX + 1];   // V^T V, then G V
   __shared__ double Gs[RZ_MAX][RZ_MAX + 1];
+  __shared__ double Hm[RZ_MAX][RZ_MAX + 1];  // V^T G V in the refinement
   __shared__ double h[RZ_MAX];
   __shared__ double gmax[RZ_THREADS / 32];
   const int tid = threadIdx.x;
@@ -178,6 +180,61 @@ __global__ void __launch_bounds__(RZ_THREADS) small_ritz_kernel(const double* __
     cnt = 0;
     for (int e = tid; e < n * n; e += blockDim.x, ++cnt) W[e / n][e % n] = nv[cnt];
     __syncthreads();
+  }
+  // 2b. One FP64 refinement of the vectors. The FP32 vectors are eigenvectors of G rounded to FP32, so the
+  // subspace they span is off by up to u32 ||G|| / gap (1e-5 .. 1e-4 rad for gaps of 1e-3 of the trace).
+  // With H = V^T G V = D + E (E off the diagonal, of that size), the eigenvectors of H are I + Z to first
+  // order, Z_ij = E_ij / (D_jj - D_ii): V (I + Z) leaves an error of order (E / gap)^2, and two
+  // Newton-Schulz steps restore orthonormality (Z is antisymmetric). Pairs whose gap is below a thousand
+  // times their coupling (a cluster) keep their vectors: rotations inside a cluster leave the split between
+  // kept and discarded directions alone unless the split falls inside it, a tie either way.
+  for (int e = tid; e < n * n; e += blockDim.x) {  // S = G V
+    const int i = e / n, j = e % n;
+    S[i][j] = dot4(&Gs[i][0], 1, &W[0][j], LD);
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {  // H = V^T S
+    const int i = e / n, j = e % n;
+    Hm[i][j] = dot4(&W[0][i], LD, &S[0][j], LD);
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {  // Z (into S), with I added: S = I + Z
+    const int i = e / n, j = e % n;
+    double z = (i == j) ? 1.0 : 0.0;
+    if (i != j) {
+      const double eij = 0.5 * (Hm[i][j] + Hm[j][i]), d = Hm[j][j] - Hm[i][i];
+      if (d != 0.0 && fabs(eij) <= 1e-3 * fabs(d)) z = eij / d;
+    }
+    S[i][j] = z;
+  }
+  __syncthreads();
+  {
+    double nv[4];
+    int cnt = 0;
+    for (int e = tid; e < n * n; e += blockDim.x, ++cnt) {  // V (I + Z)
+      const int i = e / n, j = e % n;
+      nv[cnt] = dot4(&W[i][0], 1, &S[0][j], LD);
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int e = tid; e < n * n; e += blockDim.x, ++cnt) W[e / n][e % n] = nv[cnt];
+    __syncthreads();
+    for (int step = 0; step < 2; ++step) {
+      for (int e = tid; e < n * n; e += blockDim.x) {  // S = (3I - V^T V) / 2
+        const int i = e / n, j = e % n;
+        S[i][j] = (i == j ? 1.5 : 0.0) - 0.5 * dot4(&W[0][i], LD, &W[0][j], LD);
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int e = tid; e < n * n; e += blockDim.x, ++cnt) {  // V S
+        const int i = e / n, j = e % n;
+        nv[cnt] = dot4(&W[i][0], 1, &S[0][j], LD);
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int e = tid; e < n * n; e += blockDim.x, ++cnt) W[e / n][e % n] = nv[cnt];
+      __syncthreads();
+    }
   }
   // 3. Ritz values: S = G V, h_j = v_j^T (G v_j)
   for (int e = tid; e < n * n; e += blockDim.x) {

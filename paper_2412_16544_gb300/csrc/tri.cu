@@ -31,7 +31,10 @@ struct TriGeom {
   int64_t A;
   int n1, n2, n3, r1, r2, r3;
   int n23, slab;          // n2 n3 and n1 n2 n3 (floats)
-  int n3p;                // row stride of T2: n3 made odd (conflict-free column reads in step 3)
+  int t1s;                // row stride of T1: n2 n3 padded to 24 mod 32 (the rows a and a + 1 of step 2's warps
+                          // fall on disjoint banks)
+  int n3p;                // row stride of T2: n3 padded to 3 mod 4 (odd for step 3's column reads; rows 8 apart
+                          // on disjoint banks for step 2's writes)
   uint32_t slab_bytes;    // 4 slab
   uint32_t stage_bytes;   // slab_bytes rounded up to 128
 };
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(2 * TRI_GROUP, 1)
                        const double* __restrict__ U2, int ld2, const double* __restrict__ U3, int ld3,
                        float* __restrict__ out, double* norm_in, double* norm_out, double* resid, int* status) {
   extern __shared__ __align__(128) uint8_t tsm[];
-  const int t12 = TRI_MAX_R * g.n23 + ((TRI_MAX_R * TRI_MAX_R * g.n3p + 3) & ~3);  // T1 and T2 of one group
+  const int t12 = TRI_MAX_R * g.t1s + ((TRI_MAX_R * TRI_MAX_R * g.n3p + 3) & ~3);  // T1 and T2 of one group
   float* work = reinterpret_cast<float*>(tsm + (size_t)TRI_STAGES * g.stage_bytes);
   float* B1 = work + 2 * t12;            // [n1][8][2]: each entry twice, for packed FMAs
   float* B2 = B1 + 2 * TRI_MAX_R * g.n1;  // [n2][8]
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(2 * TRI_GROUP, 1)
   const int tid = threadIdx.x;
   const int grp = tid / TRI_GROUP, gt = tid - grp * TRI_GROUP;
   float* T1 = work + grp * t12;                  // [8][n23]
-  float* T2 = T1 + TRI_MAX_R * g.n23;            // [8][8][n3p]
+  float* T2 = T1 + TRI_MAX_R * g.t1s;            // [8][8][n3p]
   for (int e = tid; e < TRI_MAX_R * g.n1; e += blockDim.x) {
     const int i = e / TRI_MAX_R, a = e - i * TRI_MAX_R;
     const float u = a < g.r1 ? (float)U1[(int64_t)i * ld1 + a] : 0.f;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(2 * TRI_GROUP, 1)
       }
 #pragma unroll
       for (int a = 0; a < TRI_MAX_R; ++a)
-        *reinterpret_cast<float4*>(T1 + a * n23 + 4 * qd) = make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
+        *reinterpret_cast<float4*>(T1 + a * g.t1s + 4 * qd) = make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
     }
     two_sum(xxp.x + xxp.y, xh, xl);
     group_sync(grp);  // T1 complete; the stage is free
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(2 * TRI_GROUP, 1)
       float acc[TRI_MAX_R];
 #pragma unroll
       for (int b = 0; b < TRI_MAX_R; ++b) acc[b] = 0.f;
-      const float* t1 = T1 + a * n23 + kk;
+      const float* t1 = T1 + a * g.t1s + kk;
 #pragma unroll 8
       for (int j = 0; j < n2; ++j) {
         const float t = t1[j * n3];
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(2 * TRI_GROUP, 1)
 }
 
 size_t tri_smem(const TriGeom& g) {
-  const size_t t12 = (size_t)TRI_MAX_R * g.n23 + (((size_t)TRI_MAX_R * TRI_MAX_R * g.n3p + 3) & ~(size_t)3);
+  const size_t t12 = (size_t)TRI_MAX_R * g.t1s + (((size_t)TRI_MAX_R * TRI_MAX_R * g.n3p + 3) & ~(size_t)3);
   return (size_t)TRI_STAGES * g.stage_bytes +
          sizeof(float) * (2 * t12 + (size_t)TRI_MAX_R * (2 * g.n1 + g.n2 + g.n3));
 }
@@ -299,7 +302,8 @@ bool tri_project_supported(int64_t A, int64_t n1, int64_t n2, int64_t n3, int64_
   if ((n2 * n3) % 4 != 0 || slab > TRI_MAX_SLAB || A > ((int64_t)1 << 40) / slab) return false;
   // shared memory: the ring, both groups' T1 and T2, the bases (the opt-in maximum less static use)
   const int64_t stage = (4 * slab + 127) & ~(int64_t)127;
-  const int64_t t12 = TRI_MAX_R * n2 * n3 + ((TRI_MAX_R * TRI_MAX_R * (n3 | 1) + 3) & ~(int64_t)3);
+  const int64_t t1s = n2 * n3 + ((24 - (n2 * n3) % 32 + 32) % 32), n3p = n3 + ((3 - n3 % 4 + 4) % 4);
+  const int64_t t12 = TRI_MAX_R * t1s + ((TRI_MAX_R * TRI_MAX_R * n3p + 3) & ~(int64_t)3);
   return TRI_STAGES * stage + 4 * (2 * t12 + TRI_MAX_R * (2 * n1 + n2 + n3)) <= 220 * 1024;
 }
 
@@ -317,7 +321,8 @@ cudaError_t launch_tri_project(const float* X, int64_t A, int n1, int n2, int n3
   g.r2 = r2;
   g.r3 = r3;
   g.n23 = n2 * n3;
-  g.n3p = n3 | 1;
+  g.t1s = g.n23 + ((24 - g.n23 % 32 + 32) % 32);
+  g.n3p = n3 + ((3 - n3 % 4 + 4) % 4);
   g.slab = n1 * n2 * n3;
   g.slab_bytes = (uint32_t)(sizeof(float) * g.slab);
   g.stage_bytes = (g.slab_bytes + 127u) & ~127u;
